@@ -1,0 +1,514 @@
+"""SpMV throughput of the selected beta(r,c) format vs plain CSR on one GB300.
+
+Workload: the four synthetic matrices shaped like the paper's benchmark set
+(Table 1 stand-ins), values N(0,1) seed 1, x uniform[-1,1] seed 0:
+  * 27-point 3D stencil on a 128^3 grid      n = 2,097,152   nnz = 55,742,968
+  * FEM-like 3x3 dense blocks, 9-27 per block row, bandwidth 5%   n = 3,000,000
+  * R-MAT scale 22, a/b/c = 0.57/0.19/0.19, 16 draws per vertex, relabelled
+  * uniform random, n = 1,000,000, 8 entries per row
+One step = one y = A x per matrix, each in the block shape picked for it by
+exhaustive timing (the paper's "best kernel"), with the L2 cache flushed
+before every product. value = sum(2 nnz) / sum(kernel time) in GFLOP/s
+(the paper's 2 N_nnz / T).
+
+Also reported on the same line: the plain CSR kernel on the same GPU, the
+float32 form, an end-to-end figure with host buffers, the roofline of the
+dominant kernel and the CPU oracle timed on the host cores.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SpMV GFLOP/s & HBM GB/s (% of peak), selected β(r,c) vs CSR, 1 GB300"
+L2_FLUSH_BYTES = 512 << 20
+FP64_PEAK_GFLOPS = 1250.0  # nominal GB300 float64 rate (2 FMA lanes/clk/SM x 152 SMs x 2.07 GHz x 2)
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=400)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--small", action="store_true", help="small matrices (quick functional run)")
+    p.add_argument("--shapes", default="all", help="'all' or comma list like 1x8,2x4")
+    p.add_argument("--profile", default=None,
+                   help="profiling run: matrix name prefix (stencil27, fem3x3, rmat, uniform); runs --reps SpMVs")
+    p.add_argument("--shape", default="4x8", help="block shape of the profiling run, e.g. 4x8, or csr")
+    p.add_argument("--dtype", default="f64", choices=["f64", "f32", "bf16"], help="profiling run value type")
+    p.add_argument("--reps", type=int, default=3)
+    return p.parse_args()
+
+
+def workload(small: bool):
+    from paper_1801_01134_gb300 import inputs
+
+    if small:
+        specs = [("stencil27_32^3", lambda: inputs.stencil3d(32, 32, 32, points=27, seed=1)),
+                 ("fem3x3_n30k", lambda: inputs.block_fem(10000, seed=1)),
+                 ("rmat_s14", lambda: inputs.rmat(14, seed=1)),
+                 ("uniform_n100k", lambda: inputs.uniform(100000, 100000, 8, seed=1))]
+    else:
+        specs = [("stencil27_128^3", lambda: inputs.stencil3d(128, 128, 128, points=27, seed=1)),
+                 ("fem3x3_n3M", lambda: inputs.block_fem(1000000, bs=3, bmin=9, bmax=27, band_frac=0.05, seed=1)),
+                 ("rmat_s22", lambda: inputs.rmat(22, 16, 0.57, 0.19, 0.19, relabel=True, seed=1)),
+                 ("uniform_n1M", lambda: inputs.uniform(1000000, 1000000, 8, seed=1))]
+    return specs
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1801_01134_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profile_traffic(kernel: str, workload_name: str):
+    """DRAM bytes per launch from a committed ncu summary, if its source hash matches."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        rec = json.load(open(path))
+    except Exception:
+        return None
+    ent = rec.get(f"{kernel}|{workload_name}")
+    if not ent or ent.get("source_hash") != kernel_source_hash():
+        return None
+    return ent.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [v.strip() for v in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx = max(mx, float(f[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_init(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if args.impl == "ours" else "gloo")
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(v: float, ws: int, device=None) -> float:
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ reference
+
+def run_reference(args):
+    """The CPU oracle (plain float64 CSR loop, OpenMP rows) on the same workload."""
+    import oracle
+
+    ws, rank, _ = dist_init(args)
+    if rank != 0:
+        return 0
+    from paper_1801_01134_gb300 import inputs
+
+    mats = [(name, gen()) for name, gen in workload(args.small)]
+    xs = [inputs.vec_uniform(A.m, seed=0) for _, A in mats]
+    flops = sum(2.0 * A.nnz for _, A in mats)
+    for _ in range(args.warmup):
+        for (_, A), x in zip(mats, xs):
+            oracle.csr_spmv_omp(A, x)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for (_, A), x in zip(mats, xs):
+            oracle.csr_spmv_omp(A, x)
+    dt = time.perf_counter() - t0
+    val = flops * args.steps / dt / 1e9
+    threads = oracle.omp_threads()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(val, 3), "unit": "GFLOP/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "suite4: " + ", ".join(n for n, _ in mats), "format": "CSR (CPU oracle)",
+                   "parallelism": "host OpenMP"},
+        "cpu_baseline": {"value": round(val, 3), "unit": "GFLOP/s", "cores": threads, "kind": "oracle",
+                         "sample": f"full workload, {args.steps} steps of 4 CSR SpMVs, float64, {threads} threads"},
+        "e2e": {"value": round(val, 3), "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ profiling
+
+def run_profile(args):
+    """One matrix, one format: convert, then --reps SpMVs with an L2 flush before
+    each (the command line that the ncu summaries under profiles/ quote)."""
+    import torch
+
+    from paper_1801_01134_gb300 import inputs, spc5
+
+    spc5.load()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    name, gen = next((n, g) for n, g in workload(args.small) if n.startswith(args.profile))
+    A = gen()
+    vdt = {"f64": torch.float64, "f32": torch.float32, "bf16": torch.bfloat16}[args.dtype]
+    xdt = torch.float64 if args.dtype == "f64" else torch.float32
+    d = spc5.upload_csr(A, vdt, dev)
+    x = torch.from_numpy(inputs.vec_uniform(A.m, seed=0)).to(dev).to(xdt)
+    y = torch.empty(A.n, dtype=xdt, device=dev)
+    fa = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    fb = torch.empty_like(fa)
+    if args.shape == "csr":
+        run = lambda: spc5.csr_spmv(d.rowptr, d.colidx, d.values, A.n, A.m, x, y)  # noqa: E731
+        fmt = "csr"
+    else:
+        r, c = (int(v) for v in args.shape.split("x"))
+        M = spc5.convert(d.rowptr, d.colidx, d.values, A.n, A.m, r, c)
+        run = lambda: M.spmv(x, y)  # noqa: E731
+        ex = M.export()
+        fmt = f"beta({r},{c}) nblocks={ex['nblocks']} segments={ex['nsegments']}"
+    ts = []
+    for _ in range(args.reps):
+        spc5.copy(fa, fb)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        run()
+        e1.record()
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    print(json.dumps({"profile": name, "format": fmt, "dtype": args.dtype, "n": A.n, "nnz": A.nnz,
+                      "ms": [round(t, 4) for t in ts], "gflops_last": round(2.0 * A.nnz / ts[-1] / 1e6, 1)}))
+    return 0
+
+
+# ------------------------------------------------------------------------ ours
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    if args.profile:
+        return run_profile(args)
+    import torch
+
+    from paper_1801_01134_gb300 import inputs, spc5
+
+    ws, rank, local = dist_init(args)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    spc5.load()
+    shapes = spc5.SHAPES if args.shapes == "all" else [tuple(int(v) for v in s.split("x")) for s in args.shapes.split(",")]
+
+    # inputs: host generation, one upload (outside every timed region)
+    mats = []
+    for name, gen in workload(args.small):
+        A = gen()
+        x = inputs.vec_uniform(A.m, seed=0)
+        mats.append({"name": name, "A": A, "x": x})
+    flush_a = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    flush_b = torch.empty_like(flush_a)
+
+    def flush():
+        spc5.copy(flush_a, flush_b)
+
+    def time_call(fn, reps, warm=2):
+        for _ in range(warm):
+            flush()
+            fn()
+        ts = []
+        for _ in range(reps):
+            flush()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts)
+
+    def prepare(dtype):
+        """Upload, time every shape (exhaustive selection) and the CSR variants."""
+        xdt = torch.float64 if dtype == torch.float64 else torch.float32
+        out = []
+        for mt in mats:
+            A = mt["A"]
+            d = spc5.upload_csr(A, dtype, dev)
+            xd = torch.from_numpy(mt["x"]).to(dev).to(xdt)
+            yd = torch.empty(A.n, dtype=xdt, device=dev)
+            best = None
+            sweep = {}
+            for (r, c) in shapes:
+                M = spc5.convert(d.rowptr, d.colidx, d.values, A.n, A.m, r, c)
+                t = time_call(lambda: M.spmv(xd, yd), 5)
+                sweep[f"{r}x{c}"] = round(2.0 * A.nnz / t / 1e6, 1)
+                if best is None or t < best[0]:
+                    if best is not None:
+                        best[1].destroy()
+                    best = (t, M, r, c)
+                else:
+                    M.destroy()
+            csr_best = None
+            for g in (1, 2, 4, 8, 16, 32):
+                t = time_call(lambda: spc5.csr_spmv(d.rowptr, d.colidx, d.values, A.n, A.m, xd, yd, group=g), 5)
+                if csr_best is None or t < csr_best[0]:
+                    csr_best = (t, g)
+            _, M, r, c = best
+            ex = M.export()
+            out.append({"name": mt["name"], "A": A, "d": d, "x": xd, "y": yd, "M": M, "r": r, "c": c,
+                        "nblocks": ex["nblocks"], "nseg": ex["nsegments"], "csr_group": csr_best[1],
+                        "sweep_gflops": sweep})
+        return out
+
+    def run_steps(prep, K, W, fn_name="beta", sampler=None):
+        per = {p["name"]: [] for p in prep}
+        for step in range(W + K):
+            for p in prep:
+                flush()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                if fn_name == "beta":
+                    p["M"].spmv(p["x"], p["y"])
+                else:
+                    A, d = p["A"], p["d"]
+                    spc5.csr_spmv(d.rowptr, d.colidx, d.values, A.n, A.m, p["x"], p["y"], group=p["csr_group"])
+                e1.record(stream)
+                if step >= W:
+                    per[p["name"]].append((e0, e1))
+        torch.cuda.synchronize()
+        return {k: [a.elapsed_time(b) for a, b in v] for k, v in per.items()}
+
+    prep64 = prepare(torch.float64)
+    flops_step = sum(2.0 * p["A"].nnz for p in prep64)
+
+    # ---- timed region (float64, selected formats)
+    barrier(ws)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as cs:
+        wall0 = time.perf_counter()
+        times = run_steps(prep64, args.steps, args.warmup)
+        torch.cuda.synchronize()
+        wall1 = time.perf_counter()
+    torch.cuda.synchronize()
+    barrier(ws)
+    step_ms = [sum(times[p["name"]][k] for p in prep64) for k in range(args.steps)]
+    total_ms = max_over_ranks(sum(step_ms), ws, dev)
+    value = flops_step * args.steps * ws / (total_ms * 1e-3) / 1e9
+    launches_per_step = sum(1 + (2 if p["nseg"] > 0 else 0) + 1 for p in prep64)  # SpMV kernels + L2 flush copy
+
+    # bytes model (algorithmic): values + colidx + masks + block_rowptr + valptr + x + y
+    def beta_bytes(p, vsize, xsize):
+        A, r, c = p["A"], p["r"], p["c"]
+        I = (A.n + r - 1) // r
+        mb = (r * c + 7) // 8
+        return vsize * A.nnz + (4 + mb) * p["nblocks"] + 4 * (I + 1) + 8 * (I + 1) + xsize * A.m + xsize * A.n
+
+    def csr_bytes(p, vsize, xsize):
+        A = p["A"]
+        return vsize * A.nnz + 4 * A.nnz + 8 * (A.n + 1) + xsize * A.m + xsize * A.n
+
+    per_matrix = []
+    for p in prep64:
+        t = statistics.median(times[p["name"]])
+        per_matrix.append({"matrix": p["name"], "n": p["A"].n, "nnz": p["A"].nnz, "shape": f"{p['r']}x{p['c']}",
+                           "avg_nnz_per_block": round(p["A"].nnz / max(p["nblocks"], 1), 3),
+                           "ms": round(t, 4), "gflops": round(2.0 * p["A"].nnz / t / 1e6, 1),
+                           "gbs": round(beta_bytes(p, 8, 8) / t / 1e6, 1), "segments": p["nseg"],
+                           "sweep_gflops": p["sweep_gflops"]})
+    dom = max(prep64, key=lambda p: statistics.median(times[p["name"]]))
+    dom_t = statistics.mean(times[dom["name"]])
+    dom_flops = 2.0 * dom["A"].nnz
+    dom_bytes = beta_bytes(dom, 8, 8)
+    hbm_peak = 6682.5
+    try:
+        hbm_peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
+    except Exception:
+        pass
+    kname = "k_spmv_rows" if dom["nseg"] == 0 else "k_spmv_rows+k_spmv_segments+k_spmv_fixup"
+    roofline = {
+        "bound": "alu", "achieved": round(dom_flops / dom_t / 1e6, 1), "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+        "frac": round(dom_flops / dom_t / 1e6 / FP64_PEAK_GFLOPS, 4),
+        "traffic": profile_traffic(kname, dom["name"]),
+        "kernel": f"{kname}<{dom['r']},{dom['c']},f64> on {dom['name']}",
+        "peak_source": "nominal float64 rate of the recipe (1.25 TFLOP/s); measured FMA loop 1.20 TFLOP/s",
+        "hbm": {"achieved": round(dom_bytes / dom_t / 1e6, 1), "peak": hbm_peak, "unit": "GB/s",
+                "frac": round(dom_bytes / dom_t / 1e6 / hbm_peak, 4), "algorithmic_bytes": int(dom_bytes),
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"},
+    }
+
+    # ---- CSR comparator, same protocol
+    csr_times = run_steps(prep64, args.steps, 1, fn_name="csr")
+    csr_ms = sum(sum(v) for v in csr_times.values())
+    csr_value = flops_step * args.steps / (csr_ms * 1e-3) / 1e9
+    csr_per = {p["name"]: {"group": p["csr_group"],
+                           "gflops": round(2.0 * p["A"].nnz / statistics.median(csr_times[p["name"]]) / 1e6, 1),
+                           "gbs": round(csr_bytes(p, 8, 8) / statistics.median(csr_times[p["name"]]) / 1e6, 1)}
+               for p in prep64}
+
+    # ---- end to end: pinned host x -> device, SpMV, y -> pinned host, every step
+    hx = [torch.from_numpy(p["x"].cpu().numpy()).pin_memory() for p in prep64]
+    hy = [torch.empty(p["A"].n, dtype=torch.float64).pin_memory() for p in prep64]
+    h2d = sum(p["A"].m * 8 for p in prep64)
+    d2h = sum(p["A"].n * 8 for p in prep64)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(2):
+        for p, a, b in zip(prep64, hx, hy):
+            p["x"].copy_(a, non_blocking=True)
+            p["M"].spmv(p["x"], p["y"])
+            b.copy_(p["y"], non_blocking=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        for p, a, b in zip(prep64, hx, hy):
+            p["x"].copy_(a, non_blocking=True)
+            p["M"].spmv(p["x"], p["y"])
+            b.copy_(p["y"], non_blocking=True)
+    e1.record(stream)
+    e1.synchronize()
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1), ws, dev)
+    e2e_value = flops_step * args.steps * ws / (e2e_ms * 1e-3) / 1e9
+
+    # ---- float32 storage form
+    for p in prep64:
+        p["M"].destroy()
+        del p["d"]
+    torch.cuda.empty_cache()
+    prep32 = prepare(torch.float32)
+    t32 = run_steps(prep32, args.steps, 1)
+    ms32 = sum(sum(v) for v in t32.values())
+    f32 = {"value": round(flops_step * args.steps / (ms32 * 1e-3) / 1e9, 1), "unit": "GFLOP/s",
+           "per_matrix": [{"matrix": p["name"], "shape": f"{p['r']}x{p['c']}",
+                           "gflops": round(2.0 * p["A"].nnz / statistics.median(t32[p["name"]]) / 1e6, 1),
+                           "gbs": round(beta_bytes(p, 4, 4) / statistics.median(t32[p["name"]]) / 1e6, 1),
+                           "hbm_frac": round(beta_bytes(p, 4, 4) / statistics.median(t32[p["name"]]) / 1e6 / hbm_peak, 4)}
+                          for p in prep32]}
+    csr32_times = run_steps(prep32, args.steps, 1, fn_name="csr")
+    f32["csr_value"] = round(flops_step * args.steps / (sum(sum(v) for v in csr32_times.values()) * 1e-3) / 1e9, 1)
+    for p in prep32:
+        p["M"].destroy()
+
+    # ---- CPU baseline: the oracle as it stands, on the host cores, bounded sample
+    cpu = None
+    if rank == 0:
+        import oracle
+
+        reps = 2
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            for p in prep64:
+                oracle.csr_spmv_omp(p["A"], p["x"].cpu().numpy() if hasattr(p["x"], "cpu") else p["x"])
+        dt = time.perf_counter() - t0
+        cpu = {"value": round(flops_step * reps / dt / 1e9, 3), "unit": "GFLOP/s", "cores": oracle.omp_threads(),
+               "kind": "oracle",
+               "sample": f"{reps} passes of the 4 float64 CSR SpMVs (plain loop, OpenMP over rows), full matrices"}
+
+    line = {
+        "metric": METRIC, "value": round(value, 2), "unit": "GFLOP/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "suite4 float64: " + ", ".join(p["name"] for p in prep64),
+                   "formats": {p["name"]: f"beta({p['r']},{p['c']})" for p in prep64},
+                   "selection": "exhaustive timing over the 12 shapes (the paper's best kernel)",
+                   "l2": f"flushed before every SpMV ({L2_FLUSH_BYTES >> 20} MiB copy, outside the events)",
+                   "parallelism": "replicas" if ws > 1 else "single GPU"},
+        "hbm_gbs": round(sum(beta_bytes(p, 8, 8) for p in prep64) * args.steps / (total_ms * 1e-3) / 1e9, 1),
+        "roofline": roofline, "cpu_baseline": cpu,
+        "e2e": {"value": round(e2e_value, 2), "unit": "GFLOP/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": cs.summary(), "wall_s_timed": round(wall1 - wall0, 3),
+        "csr": {"value": round(csr_value, 2), "unit": "GFLOP/s", "per_matrix": csr_per,
+                "speedup_beta_over_csr": round(value / csr_value, 3)},
+        "per_matrix": per_matrix, "f32": f32,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

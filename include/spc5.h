@@ -1,0 +1,165 @@
+/*
+ * spc5.h - C ABI of the GB300 beta(r,c) sparse matrix-vector product library.
+ *
+ * The method is the mask-based block storage of Bramas & Kus (2018),
+ * "Computing the sparse matrix vector product using block-based kernels
+ * without zero padding": a matrix is cut into r-row intervals; each interval
+ * is covered by r x c blocks that start at any column; a block stores one
+ * column index, an r*c-bit mask and only its nonzero values (section "Block-
+ * based storage without zero padding", Eq. 1). y = A x is computed over that
+ * storage (Algorithm 1).
+ *
+ * General rules for every entry point:
+ *   - Pointers named *_d are device pointers (cudaMalloc'd or equivalent) on
+ *     the current CUDA device; pointers without the suffix are host pointers.
+ *   - The caller owns every buffer it passes. A handle owns the device arrays
+ *     the library allocated for it and frees them in spc5_destroy.
+ *   - Work is enqueued on `stream` (a cudaStream_t; NULL = legacy default
+ *     stream). Calls return once the work is enqueued, except where a
+ *     function's comment says it synchronises.
+ *   - Errors are returned as spc5_status codes, never thrown or trapped on the
+ *     device. Arguments are checked on the host before any launch.
+ *     spc5_last_error() then gives a readable message (per host thread).
+ *   - Block shapes: r in {1, 2, 4, 8}, c in {4, 8, 16}; other shapes return
+ *     SPC5_EUNSUPPORTED.
+ *   - Index limits: int32 column indices and block counts (the paper's
+ *     S_integer = 4, Eq. 4), so m, nnz and N_blocks must be below 2^31; value
+ *     offsets are int64.
+ *   - Value types: SPC5_F64 stores float64 values and takes float64 x and y,
+ *     accumulating in float64. SPC5_F32 and SPC5_BF16 store float32 or
+ *     bfloat16 values and take float32 x and y, accumulating in float32.
+ */
+#ifndef SPC5_H
+#define SPC5_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* spc5_stream_t; /* identical to cudaStream_t */
+typedef struct spc5_matrix* spc5_handle;   /* opaque converted matrix */
+
+typedef enum { SPC5_F64 = 0, SPC5_F32 = 1, SPC5_BF16 = 2 } spc5_dtype;
+
+typedef enum {
+  SPC5_OK = 0,
+  SPC5_EINVAL = 1,       /* bad argument (null pointer, negative size, ...) */
+  SPC5_EUNSORTED = 2,    /* a CSR row lists its columns out of order */
+  SPC5_EDUP = 3,         /* a CSR row repeats a column */
+  SPC5_ERANGE = 4,       /* a column index outside [0, m), or a size too big */
+  SPC5_EUNSUPPORTED = 5, /* block shape or value type not built */
+  SPC5_ENOMEM = 6,       /* device allocation failed */
+  SPC5_ECUDA = 7,        /* a CUDA call failed; see spc5_last_error() */
+  SPC5_ETIMEOUT = 8      /* a bounded device wait gave up */
+} spc5_status;
+
+/* Options of spc5_convert (pass NULL for the defaults). */
+typedef struct {
+  /* An interval with more than long_blocks blocks is processed by whole warps
+   * in segments of seg_blocks blocks instead of one lane per row. 0 selects
+   * the defaults: long_blocks = max(64, 4 x mean blocks per interval),
+   * seg_blocks = 256. */
+  int32_t long_blocks;
+  int32_t seg_blocks;
+  /* SpMV kernel variant: 0 = automatic; other values select a specific
+   * variant (for tuning and tests). */
+  int32_t variant;
+  int32_t reserved[5];
+} spc5_opts;
+
+/* Read-only device views of a handle's arrays (layout of Eq. 1 plus derived
+ * arrays), for tests and for users who keep the converted form. */
+typedef struct {
+  int64_t n, m, nnz, nblocks, nintervals;
+  int32_t r, c, mask_bytes;
+  spc5_dtype dtype;
+  const int32_t* block_rowptr_d; /* int32[nintervals+1], prefix of blocks per interval */
+  const int32_t* block_colidx_d; /* int32[nblocks], column of each block's upper-left corner */
+  const uint8_t* block_masks_d;  /* uint8[nblocks*mask_bytes], bit i*c+k = (row i, col k), LSB first */
+  const void* values_d;          /* dtype[nnz], block order, row-major inside a block */
+  const int64_t* valptr_d;       /* int64[nintervals+1], first value of each interval (derived) */
+  int64_t nsegments;             /* long-interval segments of the execution plan */
+} spc5_arrays;
+
+/*
+ * spc5_convert - CSR -> beta(r,c) (section "Block-based storage without zero
+ * padding"; conversion cost discussed in section "Test matrices").
+ *   n, m, nnz   rows, columns and stored entries of the CSR matrix.
+ *   rowptr_d    int64[n+1] device array, rowptr_d[0] = 0, rowptr_d[n] = nnz.
+ *   colidx_d    int32[nnz] device array, ascending and unique within a row.
+ *   values_d    dtype[nnz] device array (vt gives the type).
+ *   r, c        block shape.
+ *   opt         NULL or tuning options.
+ *   out         receives the new handle (NULL on failure).
+ * Block starts follow greedy leftmost cover: within an interval a block starts
+ * at the smallest column not yet covered and spans c columns (it may run past
+ * column m-1; those mask bits are zero). Explicit zeros are kept.
+ * Errors: SPC5_EUNSORTED / SPC5_EDUP / SPC5_ERANGE for malformed CSR (checked
+ * on the device, reported through a status word), SPC5_ENOMEM, SPC5_ECUDA.
+ * Synchronises `stream` (the array sizes depend on the block count).
+ */
+spc5_status spc5_convert(int64_t n, int64_t m, int64_t nnz, const int64_t* rowptr_d, const int32_t* colidx_d,
+                         const void* values_d, spc5_dtype vt, int r, int c, const spc5_opts* opt,
+                         spc5_stream_t stream, spc5_handle* out);
+
+/*
+ * spc5_spmv - y = A x over the beta(r,c) storage (Algorithm 1; Code 1 shows
+ * the paper's beta(1,8) kernel). x_d has m entries, y_d has n entries, both of
+ * the handle's vector type; y is overwritten. x and y must not overlap.
+ */
+spc5_status spc5_spmv(spc5_handle h, const void* x_d, void* y_d, spc5_stream_t stream);
+
+/*
+ * spc5_spmv_acc - y += A x, the paper's accumulate form (Algorithm 1 adds the
+ * row sums to y; Code 1 adds to y[row] too). Same arguments as spc5_spmv.
+ */
+spc5_status spc5_spmv_acc(spc5_handle h, const void* x_d, void* y_d, spc5_stream_t stream);
+
+/* spc5_export - fill *view with the handle's device arrays (valid until
+ * spc5_destroy). No device work. */
+spc5_status spc5_export(spc5_handle h, spc5_arrays* view);
+
+/* spc5_destroy - free the handle and its device arrays (synchronises the
+ * device first so that no queued kernel still reads them). NULL is allowed. */
+spc5_status spc5_destroy(spc5_handle h);
+
+/* spc5_last_error - message of the last failed call on this host thread. */
+const char* spc5_last_error(void);
+
+/*
+ * spc5_count_blocks - N_blocks(r,c) of a CSR matrix without converting it
+ * (section "Performance polynomial interpolation": the average number of
+ * values per block, Avg(r,c) = nnz / N_blocks(r,c), is obtained without
+ * conversion). Counts all twelve built shapes in one call: nblocks_out[12]
+ * receives N_blocks for (r,c) in the order r in {1,2,4,8} outer, c in
+ * {4,8,16} inner. Host output; synchronises `stream`. The CSR must be valid
+ * (see spc5_convert); it is not re-checked.
+ */
+spc5_status spc5_count_blocks(int64_t n, int64_t m, int64_t nnz, const int64_t* rowptr_d, const int32_t* colidx_d,
+                              int64_t* nblocks_out, spc5_stream_t stream);
+
+/*
+ * spc5_csr_spmv - y = A x directly on CSR (the comparison format of the paper,
+ * section "Sparse Matrix Vector Product (SpMV)"). Same types and vector rules
+ * as spc5_spmv for value type vt. rowptr_d/colidx_d/values_d as in
+ * spc5_convert; the CSR is not re-checked. group = lanes per row (1, 2, 4, 8,
+ * 16 or 32), or 0 to pick it from the mean row length.
+ */
+spc5_status spc5_csr_spmv(int64_t n, int64_t m, int64_t nnz, const int64_t* rowptr_d, const int32_t* colidx_d,
+                          const void* values_d, spc5_dtype vt, const void* x_d, void* y_d, int group,
+                          spc5_stream_t stream);
+
+/*
+ * spc5_copy - dst = src for `bytes` bytes (a multiple of 16, both pointers
+ * 16-byte aligned): the streaming-copy kernel that measures the achievable
+ * HBM bandwidth next to the SpMV kernels.
+ */
+spc5_status spc5_copy(const void* src_d, void* dst_d, int64_t bytes, spc5_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPC5_H */

@@ -1,0 +1,152 @@
+// C ABI of libspc5 (declared in include/spc5.h): argument checks on the host,
+// error reporting, and dispatch to the kernels of the other translation units.
+#include <climits>
+#include <cstdio>
+#include <string>
+
+#include "internal.cuh"
+
+namespace spc5 {
+
+namespace {
+thread_local std::string g_last_error;
+}
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+spc5_status fail(spc5_status st, const std::string& msg) {
+  set_error(msg);
+  return st;
+}
+
+spc5_status cuda_fail(cudaError_t e, const char* what) {
+  set_error(std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")");
+  return e == cudaErrorMemoryAllocation ? SPC5_ENOMEM : SPC5_ECUDA;
+}
+
+int sm_count() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) return 1;
+  return sms;
+}
+
+namespace {
+
+spc5_status check_csr_args(int64_t n, int64_t m, int64_t nnz, const int64_t* rowptr, const int32_t* colidx,
+                           const void* values) {
+  if (n < 0 || m < 0 || nnz < 0) return fail(SPC5_EINVAL, "negative size");
+  if (m > INT_MAX || nnz > INT_MAX) return fail(SPC5_ERANGE, "m and nnz must be below 2^31 (int32 indices)");
+  if (n > 0 && !rowptr) return fail(SPC5_EINVAL, "rowptr is NULL");
+  if (nnz > 0 && (!colidx || !values)) return fail(SPC5_EINVAL, "colidx or values is NULL");
+  return SPC5_OK;
+}
+
+spc5_status spmv_common(spc5_handle h, const void* x, void* y, bool acc, cudaStream_t s) {
+  if (!h) return fail(SPC5_EINVAL, "spmv: NULL handle");
+  if ((h->m > 0 && !x) || (h->n > 0 && !y)) return fail(SPC5_EINVAL, "spmv: NULL vector");
+  cudaError_t e;
+  switch (h->vt) {
+    case SPC5_F64: e = launch_spmv_f64(h, x, y, acc, s); break;
+    case SPC5_F32: e = launch_spmv_f32(h, x, y, acc, s); break;
+    case SPC5_BF16: e = launch_spmv_bf16(h, x, y, acc, s); break;
+    default: return fail(SPC5_EUNSUPPORTED, "spmv: value type");
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "spmv launch");
+  return SPC5_OK;
+}
+
+}  // namespace
+}  // namespace spc5
+
+using namespace spc5;
+
+extern "C" {
+
+spc5_status spc5_convert(int64_t n, int64_t m, int64_t nnz, const int64_t* rowptr_d, const int32_t* colidx_d,
+                         const void* values_d, spc5_dtype vt, int r, int c, const spc5_opts* opt,
+                         spc5_stream_t stream, spc5_handle* out) {
+  if (!out) return fail(SPC5_EINVAL, "convert: out is NULL");
+  *out = nullptr;
+  spc5_status st = check_csr_args(n, m, nnz, rowptr_d, colidx_d, values_d);
+  if (st != SPC5_OK) return st;
+  if (!shape_supported(r, c)) return fail(SPC5_EUNSUPPORTED, "convert: block shape must be r in {1,2,4,8}, c in {4,8,16}");
+  if (vt != SPC5_F64 && vt != SPC5_F32 && vt != SPC5_BF16) return fail(SPC5_EUNSUPPORTED, "convert: value type");
+  if (opt && (opt->long_blocks < 0 || opt->seg_blocks < 0)) return fail(SPC5_EINVAL, "convert: negative option");
+  spc5_matrix* h = nullptr;
+  st = convert_impl(n, m, nnz, rowptr_d, colidx_d, values_d, vt, r, c, opt, (cudaStream_t)stream, &h);
+  if (st != SPC5_OK) return st;
+  *out = h;
+  return SPC5_OK;
+}
+
+spc5_status spc5_spmv(spc5_handle h, const void* x_d, void* y_d, spc5_stream_t stream) {
+  return spmv_common(h, x_d, y_d, false, (cudaStream_t)stream);
+}
+
+spc5_status spc5_spmv_acc(spc5_handle h, const void* x_d, void* y_d, spc5_stream_t stream) {
+  return spmv_common(h, x_d, y_d, true, (cudaStream_t)stream);
+}
+
+spc5_status spc5_export(spc5_handle h, spc5_arrays* v) {
+  if (!h || !v) return fail(SPC5_EINVAL, "export: NULL argument");
+  v->n = h->n;
+  v->m = h->m;
+  v->nnz = h->nnz;
+  v->nblocks = h->nb;
+  v->nintervals = h->I;
+  v->r = h->r;
+  v->c = h->c;
+  v->mask_bytes = h->mb;
+  v->dtype = h->vt;
+  v->block_rowptr_d = h->block_rowptr;
+  v->block_colidx_d = h->block_colidx;
+  v->block_masks_d = h->block_masks;
+  v->values_d = h->values;
+  v->valptr_d = h->valptr;
+  v->nsegments = h->nseg;
+  return SPC5_OK;
+}
+
+spc5_status spc5_destroy(spc5_handle h) {
+  if (!h) return SPC5_OK;
+  cudaError_t e = cudaDeviceSynchronize();
+  destroy_matrix(h);
+  if (e != cudaSuccess) return cuda_fail(e, "destroy: device synchronisation");
+  return SPC5_OK;
+}
+
+const char* spc5_last_error(void) { return g_last_error.c_str(); }
+
+spc5_status spc5_count_blocks(int64_t n, int64_t m, int64_t nnz, const int64_t* rowptr_d, const int32_t* colidx_d,
+                              int64_t* nblocks_out, spc5_stream_t stream) {
+  if (!nblocks_out) return fail(SPC5_EINVAL, "count_blocks: NULL output");
+  spc5_status st = check_csr_args(n, m, nnz, rowptr_d, colidx_d, (const void*)colidx_d);
+  if (st != SPC5_OK) return st;
+  return count_blocks_impl(n, nnz, rowptr_d, colidx_d, nblocks_out, (cudaStream_t)stream);
+}
+
+spc5_status spc5_csr_spmv(int64_t n, int64_t m, int64_t nnz, const int64_t* rowptr_d, const int32_t* colidx_d,
+                          const void* values_d, spc5_dtype vt, const void* x_d, void* y_d, int group,
+                          spc5_stream_t stream) {
+  spc5_status st = check_csr_args(n, m, nnz, rowptr_d, colidx_d, values_d);
+  if (st != SPC5_OK) return st;
+  if (vt != SPC5_F64 && vt != SPC5_F32 && vt != SPC5_BF16) return fail(SPC5_EUNSUPPORTED, "csr_spmv: value type");
+  if (!(group == 0 || group == 1 || group == 2 || group == 4 || group == 8 || group == 16 || group == 32))
+    return fail(SPC5_EINVAL, "csr_spmv: group must be 0 or a power of two up to 32");
+  if ((m > 0 && !x_d) || (n > 0 && !y_d)) return fail(SPC5_EINVAL, "csr_spmv: NULL vector");
+  cudaError_t e = launch_csr_spmv_group(group, n, nnz, rowptr_d, colidx_d, values_d, vt, x_d, y_d, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "csr_spmv launch");
+  return SPC5_OK;
+}
+
+spc5_status spc5_copy(const void* src_d, void* dst_d, int64_t bytes, spc5_stream_t stream) {
+  if (bytes < 0 || (bytes % 16) != 0) return fail(SPC5_EINVAL, "copy: bytes must be a non-negative multiple of 16");
+  if (bytes > 0 && (!src_d || !dst_d)) return fail(SPC5_EINVAL, "copy: NULL pointer");
+  if (((uintptr_t)src_d | (uintptr_t)dst_d) & 15u) return fail(SPC5_EINVAL, "copy: pointers must be 16-byte aligned");
+  cudaError_t e = launch_copy(src_d, dst_d, bytes, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "copy launch");
+  return SPC5_OK;
+}
+
+}  // extern "C"

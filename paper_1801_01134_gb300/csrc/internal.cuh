@@ -1,0 +1,88 @@
+// Internal declarations shared by the translation units of libspc5.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/spc5.h"
+
+namespace spc5 {
+
+// Defaults of the execution plan: an interval with more than
+// max(kLongBlocks, 4 x mean blocks per interval) blocks is split into
+// segments of kSegBlocks blocks, each handled by a warp.
+constexpr int kLongBlocks = 64;
+constexpr int kSegBlocks = 256;
+constexpr int kWarp = 32;
+
+struct Segment {  // one warp task of a long interval
+  int32_t interval;
+  int32_t b_begin;
+  int32_t b_end;
+  int32_t pad;
+  int64_t v_begin;  // value offset of block b_begin
+};
+static_assert(sizeof(Segment) == 24, "segment layout");
+
+}  // namespace spc5
+
+struct spc5_matrix {
+  int64_t n = 0, m = 0, nnz = 0;
+  int32_t r = 0, c = 0, mb = 0;
+  spc5_dtype vt = SPC5_F64;
+  int64_t I = 0;        // number of row intervals, ceil(n / r)
+  int64_t nb = 0;       // N_blocks(r,c)
+  int32_t* block_rowptr = nullptr;  // [I+1]
+  int32_t* block_colidx = nullptr;  // [nb] (+ padding)
+  uint8_t* block_masks = nullptr;   // [nb*mb] (+ padding)
+  void* values = nullptr;           // [nnz] (+ padding)
+  int64_t* valptr = nullptr;        // [I+1]
+  // execution plan
+  int32_t long_blocks = spc5::kLongBlocks;
+  int32_t seg_blocks = spc5::kSegBlocks;
+  int32_t variant = 0;
+  int64_t nseg = 0;
+  spc5::Segment* segs = nullptr;    // [nseg]
+  void* partials = nullptr;         // [nseg * r] accumulation-type scratch
+};
+
+namespace spc5 {
+
+// thread-local last-error message
+void set_error(const std::string& msg);
+spc5_status fail(spc5_status st, const std::string& msg);
+spc5_status cuda_fail(cudaError_t e, const char* what);
+
+inline bool shape_supported(int r, int c) {
+  return (r == 1 || r == 2 || r == 4 || r == 8) && (c == 4 || c == 8 || c == 16);
+}
+inline int mask_bytes(int r, int c) { return (r * c + 7) / 8; }
+inline size_t value_size(spc5_dtype t) { return t == SPC5_F64 ? 8 : (t == SPC5_F32 ? 4 : 2); }
+
+// conversion (convert.cu)
+spc5_status convert_impl(int64_t n, int64_t m, int64_t nnz, const int64_t* rowptr, const int32_t* colidx,
+                         const void* values, spc5_dtype vt, int r, int c, const spc5_opts* opt, cudaStream_t s,
+                         spc5_matrix** out);
+spc5_status count_blocks_impl(int64_t n, int64_t nnz, const int64_t* rowptr, const int32_t* colidx,
+                              int64_t* nblocks_out, cudaStream_t s);
+
+// SpMV launchers, one per value type (spmv_f64.cu, spmv_f32.cu, spmv_bf16.cu)
+cudaError_t launch_spmv_f64(const spc5_matrix* h, const void* x, void* y, bool acc, cudaStream_t s);
+cudaError_t launch_spmv_f32(const spc5_matrix* h, const void* x, void* y, bool acc, cudaStream_t s);
+cudaError_t launch_spmv_bf16(const spc5_matrix* h, const void* x, void* y, bool acc, cudaStream_t s);
+
+// CSR comparator and copy (csr.cu)
+cudaError_t launch_csr_spmv(int64_t n, int64_t nnz, const int64_t* rowptr, const int32_t* colidx,
+                            const void* values, spc5_dtype vt, const void* x, void* y, cudaStream_t s);
+cudaError_t launch_csr_spmv_group(int group, int64_t n, int64_t nnz, const int64_t* rowptr, const int32_t* colidx,
+                                  const void* values, spc5_dtype vt, const void* x, void* y, cudaStream_t s);
+int csr_auto_group(int64_t n, int64_t nnz, spc5_dtype vt);
+void destroy_matrix(spc5_matrix* h);
+cudaError_t launch_copy(const void* src, void* dst, int64_t bytes, cudaStream_t s);
+
+int sm_count();
+
+}  // namespace spc5

@@ -1,0 +1,10 @@
+// beta(r,c) SpMV instantiations for the BF16 value type (all twelve shapes).
+#include "spmv_beta.cuh"
+
+namespace spc5 {
+
+cudaError_t launch_spmv_bf16(const spc5_matrix* h, const void* x, void* y, bool acc, cudaStream_t s) {
+  return dispatch_beta<BF16>(h, x, y, acc, s);
+}
+
+}  // namespace spc5

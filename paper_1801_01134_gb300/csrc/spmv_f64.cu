@@ -1,0 +1,10 @@
+// beta(r,c) SpMV instantiations for the F64 value type (all twelve shapes).
+#include "spmv_beta.cuh"
+
+namespace spc5 {
+
+cudaError_t launch_spmv_f64(const spc5_matrix* h, const void* x, void* y, bool acc, cudaStream_t s) {
+  return dispatch_beta<F64>(h, x, y, acc, s);
+}
+
+}  // namespace spc5

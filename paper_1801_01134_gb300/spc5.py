@@ -1,0 +1,248 @@
+"""Python binding of libspc5 (include/spc5.h): argument marshalling only.
+
+Every step of the method runs in the CUDA library; this module turns torch
+CUDA tensors into device pointers and the current torch stream into a
+cudaStream_t. There is no fallback: if libspc5.so is missing or no GPU is
+present, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import _build
+
+SPC5_F64, SPC5_F32, SPC5_BF16 = 0, 1, 2
+STATUS = {0: "SPC5_OK", 1: "SPC5_EINVAL", 2: "SPC5_EUNSORTED", 3: "SPC5_EDUP", 4: "SPC5_ERANGE",
+          5: "SPC5_EUNSUPPORTED", 6: "SPC5_ENOMEM", 7: "SPC5_ECUDA", 8: "SPC5_ETIMEOUT"}
+OK, EINVAL, EUNSORTED, EDUP, ERANGE, EUNSUPPORTED, ENOMEM, ECUDA, ETIMEOUT = range(9)
+
+_VALUE_DTYPE = {torch.float64: SPC5_F64, torch.float32: SPC5_F32, torch.bfloat16: SPC5_BF16}
+_VECTOR_DTYPE = {SPC5_F64: torch.float64, SPC5_F32: torch.float32, SPC5_BF16: torch.float32}
+SHAPES = [(r, c) for r in (1, 2, 4, 8) for c in (4, 8, 16)]
+
+
+class Spc5Error(RuntimeError):
+    def __init__(self, status: int, where: str, message: str):
+        super().__init__(f"{where}: {STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("long_blocks", ctypes.c_int32), ("seg_blocks", ctypes.c_int32), ("variant", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 5)]
+
+
+class Arrays(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("m", ctypes.c_int64), ("nnz", ctypes.c_int64), ("nblocks", ctypes.c_int64),
+                ("nintervals", ctypes.c_int64), ("r", ctypes.c_int32), ("c", ctypes.c_int32),
+                ("mask_bytes", ctypes.c_int32), ("dtype", ctypes.c_int), ("block_rowptr_d", ctypes.c_void_p),
+                ("block_colidx_d", ctypes.c_void_p), ("block_masks_d", ctypes.c_void_p),
+                ("values_d", ctypes.c_void_p), ("valptr_d", ctypes.c_void_p), ("nsegments", ctypes.c_int64)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load libspc5.so (fails loudly when it is not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_build.LIB):
+        if not build_if_missing:
+            raise RuntimeError(f"{_build.LIB} is not built; run __graft_entry__.build() (no CPU fallback exists)")
+        _build.build()
+    lib = ctypes.CDLL(_build.LIB)
+    vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+    st = ctypes.c_int
+    lib.spc5_convert.argtypes = [i64, i64, i64, vp, vp, vp, i32, i32, i32, ctypes.POINTER(Opts), vp, ctypes.POINTER(vp)]
+    lib.spc5_spmv.argtypes = [vp, vp, vp, vp]
+    lib.spc5_spmv_acc.argtypes = [vp, vp, vp, vp]
+    lib.spc5_export.argtypes = [vp, ctypes.POINTER(Arrays)]
+    lib.spc5_destroy.argtypes = [vp]
+    lib.spc5_last_error.argtypes = []
+    lib.spc5_last_error.restype = ctypes.c_char_p
+    lib.spc5_count_blocks.argtypes = [i64, i64, i64, vp, vp, vp, vp]
+    lib.spc5_csr_spmv.argtypes = [i64, i64, i64, vp, vp, vp, i32, vp, vp, i32, vp]
+    lib.spc5_copy.argtypes = [vp, vp, i64, vp]
+    for f in (lib.spc5_convert, lib.spc5_spmv, lib.spc5_spmv_acc, lib.spc5_export, lib.spc5_destroy,
+              lib.spc5_count_blocks, lib.spc5_csr_spmv, lib.spc5_copy):
+        f.restype = st
+    _lib = lib
+    return lib
+
+
+def last_error() -> str:
+    return load().spc5_last_error().decode()
+
+
+def _check(status: int, where: str):
+    if status != OK:
+        raise Spc5Error(status, where, last_error())
+
+
+def _stream_ptr(stream) -> int | None:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def _ptr(t: torch.Tensor | None) -> int | None:
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return t.data_ptr() if t.numel() > 0 else None
+
+
+def _pad16(nbytes: int) -> int:
+    return (nbytes + 15) // 16 * 16 + 16
+
+
+class Matrix:
+    """A matrix converted to beta(r,c); owns the library handle."""
+
+    def __init__(self, handle: int, n: int, m: int, nnz: int, r: int, c: int, vt: int):
+        self._h = handle
+        self.n, self.m, self.nnz, self.r, self.c, self.vt = n, m, nnz, r, c, vt
+
+    @property
+    def vector_dtype(self) -> torch.dtype:
+        return _VECTOR_DTYPE[self.vt]
+
+    def spmv(self, x: torch.Tensor, y: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """y = A x (overwrites y; allocates it when None)."""
+        if y is None:
+            y = torch.empty(self.n, dtype=self.vector_dtype, device=x.device)
+        self._check_vectors(x, y)
+        _check(load().spc5_spmv(self._h, _ptr(x), _ptr(y), _stream_ptr(stream)), "spc5_spmv")
+        return y
+
+    def spmv_acc(self, x: torch.Tensor, y: torch.Tensor, stream=None) -> torch.Tensor:
+        """y += A x (the paper's accumulate form)."""
+        self._check_vectors(x, y)
+        _check(load().spc5_spmv_acc(self._h, _ptr(x), _ptr(y), _stream_ptr(stream)), "spc5_spmv_acc")
+        return y
+
+    def _check_vectors(self, x, y):
+        if self._h is None:
+            raise ValueError("matrix was destroyed")
+        if x.dtype != self.vector_dtype or y.dtype != self.vector_dtype:
+            raise TypeError(f"x and y must be {self.vector_dtype}")
+        if x.numel() != self.m or y.numel() != self.n:
+            raise ValueError("x must have m entries and y n entries")
+
+    def arrays(self) -> Arrays:
+        a = Arrays()
+        _check(load().spc5_export(self._h, ctypes.byref(a)), "spc5_export")
+        return a
+
+    def export(self) -> dict:
+        """Host copies of the beta(r,c) arrays (via the library's copy kernel)."""
+        a = self.arrays()
+        vsize = {SPC5_F64: 8, SPC5_F32: 4, SPC5_BF16: 2}[self.vt]
+
+        def fetch(ptr, nbytes, dtype, count):
+            buf = torch.empty(_pad16(nbytes), dtype=torch.uint8, device="cuda")
+            copy_raw(ptr, buf.data_ptr(), _pad16(nbytes))
+            torch.cuda.synchronize()
+            return buf.cpu().numpy()[:nbytes].view(dtype)[:count].copy()
+
+        I = a.nintervals
+        out = {
+            "block_rowptr": fetch(a.block_rowptr_d, 4 * (I + 1), np.int32, I + 1),
+            "block_colidx": fetch(a.block_colidx_d, 4 * a.nblocks, np.int32, a.nblocks),
+            "block_masks": fetch(a.block_masks_d, a.mask_bytes * a.nblocks, np.uint8, a.mask_bytes * a.nblocks),
+            "values_raw": fetch(a.values_d, vsize * a.nnz, {8: np.uint64, 4: np.uint32, 2: np.uint16}[vsize], a.nnz),
+            "valptr": fetch(a.valptr_d, 8 * (I + 1), np.int64, I + 1),
+            "nsegments": int(a.nsegments),
+            "nblocks": int(a.nblocks),
+        }
+        return out
+
+    def destroy(self):
+        if self._h is not None:
+            load().spc5_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def convert(rowptr: torch.Tensor, colidx: torch.Tensor, values: torch.Tensor, n: int, m: int, r: int, c: int,
+            long_blocks: int = 0, seg_blocks: int = 0, variant: int = 0, stream=None) -> Matrix:
+    """CSR (device tensors: int64 rowptr, int32 colidx, values) -> beta(r,c)."""
+    if rowptr.dtype != torch.int64 or colidx.dtype != torch.int32:
+        raise TypeError("rowptr must be int64 and colidx int32")
+    if values.dtype not in _VALUE_DTYPE:
+        raise TypeError("values must be float64, float32 or bfloat16")
+    vt = _VALUE_DTYPE[values.dtype]
+    nnz = values.numel()
+    opts = Opts(long_blocks, seg_blocks, variant)
+    h = ctypes.c_void_p()
+    _check(load().spc5_convert(n, m, nnz, _ptr(rowptr), _ptr(colidx), _ptr(values), vt, r, c, ctypes.byref(opts),
+                               _stream_ptr(stream), ctypes.byref(h)), "spc5_convert")
+    return Matrix(h.value, n, m, nnz, r, c, vt)
+
+
+def csr_spmv(rowptr: torch.Tensor, colidx: torch.Tensor, values: torch.Tensor, n: int, m: int, x: torch.Tensor,
+             y: torch.Tensor | None = None, group: int = 0, stream=None) -> torch.Tensor:
+    """y = A x on plain CSR (the comparison kernel)."""
+    vt = _VALUE_DTYPE[values.dtype]
+    if y is None:
+        y = torch.empty(n, dtype=_VECTOR_DTYPE[vt], device=x.device)
+    _check(load().spc5_csr_spmv(n, m, values.numel(), _ptr(rowptr), _ptr(colidx), _ptr(values), vt, _ptr(x), _ptr(y),
+                                group, _stream_ptr(stream)), "spc5_csr_spmv")
+    return y
+
+
+def count_blocks(rowptr: torch.Tensor, colidx: torch.Tensor, n: int, m: int, stream=None) -> np.ndarray:
+    """N_blocks(r,c) for the twelve shapes (r outer, c inner), without conversion."""
+    out = np.zeros(12, dtype=np.int64)
+    _check(load().spc5_count_blocks(n, m, colidx.numel(), _ptr(rowptr), _ptr(colidx), out.ctypes.data,
+                                    _stream_ptr(stream)), "spc5_count_blocks")
+    return out
+
+
+def copy_raw(src_ptr: int, dst_ptr: int, nbytes: int, stream=None):
+    _check(load().spc5_copy(src_ptr, dst_ptr, nbytes, _stream_ptr(stream)), "spc5_copy")
+
+
+def copy(src: torch.Tensor, dst: torch.Tensor, stream=None):
+    """dst = src with the library's streaming copy kernel (HBM ceiling)."""
+    nbytes = src.numel() * src.element_size()
+    copy_raw(_ptr(src), _ptr(dst), nbytes, stream)
+
+
+@dataclass
+class DeviceCSR:
+    n: int
+    m: int
+    rowptr: torch.Tensor
+    colidx: torch.Tensor
+    values: torch.Tensor
+
+    @property
+    def nnz(self) -> int:
+        return int(self.values.numel())
+
+
+def upload_csr(A, dtype: torch.dtype = torch.float64, device="cuda") -> DeviceCSR:
+    """Copy a host CSR (numpy arrays) to the device, values cast to dtype."""
+    rowptr = torch.from_numpy(np.ascontiguousarray(A.rowptr, dtype=np.int64)).to(device)
+    colidx = torch.from_numpy(np.ascontiguousarray(A.colidx, dtype=np.int32)).to(device)
+    values = torch.from_numpy(np.ascontiguousarray(A.values, dtype=np.float64)).to(device).to(dtype)
+    return DeviceCSR(A.n, A.m, rowptr, colidx, values)

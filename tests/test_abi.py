@@ -1,0 +1,71 @@
+"""The C ABI library loads on a machine without a GPU and exports every entry
+point that include/spc5.h declares. Only host-side argument checks are
+exercised here (they return before any CUDA call)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1801_01134_gb300 import _build, spc5
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", h)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names += re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_\s\*]*?\b(spc5_[a-z0-9_]+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    _build.build()
+    return spc5.load()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ("spc5_convert", "spc5_spmv", "spc5_spmv_acc", "spc5_export", "spc5_destroy", "spc5_last_error",
+                 "spc5_count_blocks", "spc5_csr_spmv", "spc5_copy"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+        assert isinstance(getattr(lib, name), ctypes._CFuncPtr)
+
+
+def test_host_side_argument_checks(lib):
+    h = ctypes.c_void_p()
+    # NULL output handle
+    assert lib.spc5_convert(4, 4, 0, None, None, None, 0, 1, 8, None, None, None) == spc5.EINVAL
+    # unsupported block shape / value type, negative sizes, index range
+    assert lib.spc5_convert(4, 4, 0, 1, None, None, 0, 3, 8, None, None, ctypes.byref(h)) == spc5.EUNSUPPORTED
+    assert lib.spc5_convert(4, 4, 0, 1, None, None, 0, 2, 5, None, None, ctypes.byref(h)) == spc5.EUNSUPPORTED
+    assert lib.spc5_convert(4, 4, 0, 1, None, None, 7, 2, 8, None, None, ctypes.byref(h)) == spc5.EUNSUPPORTED
+    assert lib.spc5_convert(-1, 4, 0, 1, None, None, 0, 2, 8, None, None, ctypes.byref(h)) == spc5.EINVAL
+    assert lib.spc5_convert(4, 2**31, 0, 1, None, None, 0, 2, 8, None, None, ctypes.byref(h)) == spc5.ERANGE
+    assert lib.spc5_convert(4, 4, 3, 1, None, None, 0, 2, 8, None, None, ctypes.byref(h)) == spc5.EINVAL
+    assert "NULL" in spc5.last_error()
+    assert lib.spc5_spmv(None, None, None, None) == spc5.EINVAL
+    assert lib.spc5_export(None, None) == spc5.EINVAL
+    assert lib.spc5_destroy(None) == spc5.OK
+    assert lib.spc5_copy(None, None, 17, None) == spc5.EINVAL
+    assert lib.spc5_copy(8, 16, 16, None) == spc5.EINVAL  # misaligned
+    assert lib.spc5_csr_spmv(4, 4, 0, 1, None, None, 0, 1, 1, 3, None) == spc5.EINVAL  # bad group
+    out = (ctypes.c_int64 * 12)()
+    assert lib.spc5_count_blocks(4, 4, 0, None, None, out, None) == spc5.EINVAL
+
+
+def test_product_path_has_no_cpu_fallback():
+    # the binding never imports the oracle
+    src = open(os.path.join(ROOT, "paper_1801_01134_gb300", "spc5.py")).read()
+    assert "oracle" not in src.replace("no CPU fallback", "")
+    for f in os.listdir(os.path.join(ROOT, "paper_1801_01134_gb300", "csrc")):
+        assert "oracle" not in open(os.path.join(ROOT, "paper_1801_01134_gb300", "csrc", f)).read()

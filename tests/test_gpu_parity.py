@@ -1,0 +1,250 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Conversion must be bit-exact. float64 SpMV must satisfy
+|y - y_ref|_i <= 1e-13 * (|A||x|)_i against the compensated (Dot2) oracle.
+float32 / bfloat16 storage is checked against an oracle fed the same rounded
+inputs, within the worst-case float32 summation bound gamma_{L_i+1} * (|A||x|)_i
+(L_i = entries of row i; u = 2^-24), which holds for any summation order.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1801_01134_gb300 import inputs, spc5
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-13
+
+
+def _matrices():
+    out = {
+        "lap128": lambda: inputs.laplacian2d(128, 128),
+        "rand_ragged": lambda: inputs.random_csr(301, 517, 0.03, seed=3),
+        "st27_ragged": lambda: inputs.stencil3d(13, 11, 7, points=27, seed=4),
+        "rmat11": lambda: inputs.rmat(11, seed=2),
+        "uniform": lambda: inputs.uniform(3001, 2500, 8, seed=5),
+        "fem": lambda: inputs.block_fem(700, seed=6),
+        "dense64": lambda: inputs.CSR.from_dense(inputs.vec_normal(64 * 61, seed=8).reshape(64, 61)),
+        "sparse_rows": lambda: inputs.random_csr(203, 90, 0.004, seed=9),  # mostly empty rows
+    }
+    return out
+
+
+MATS = _matrices()
+_cache = {}
+
+
+def get(name):
+    if name not in _cache:
+        _cache[name] = MATS[name]()
+    return _cache[name]
+
+
+def dev_csr(A, dtype=torch.float64):
+    return spc5.upload_csr(A, dtype, "cuda")
+
+
+def guarded(n, dtype):
+    """y with NaN guard cells after it; returns (buffer, view of length n)."""
+    buf = torch.full((n + 64,), float("nan"), dtype=dtype, device="cuda")
+    return buf, buf[:n]
+
+
+@pytest.mark.parametrize("name", list(MATS))
+@pytest.mark.parametrize("r,c", spc5.SHAPES)
+def test_convert_bit_exact(cuda_device, name, r, c):
+    A = get(name)
+    d = dev_csr(A)
+    M = spc5.convert(d.rowptr, d.colidx, d.values, A.n, A.m, r, c)
+    got = M.export()
+    B = oracle.beta_convert(A, r, c)
+    assert got["nblocks"] == B.nblocks
+    assert np.array_equal(got["block_rowptr"], B.block_rowptr)
+    assert np.array_equal(got["block_colidx"], B.block_colidx)
+    assert np.array_equal(got["block_masks"], B.block_masks)
+    assert np.array_equal(got["values_raw"], B.values.view(np.uint64))
+    assert np.array_equal(got["valptr"], B.valptr(A.rowptr))
+    M.destroy()
+
+
+def check64(y, y_ref, absy):
+    err = np.abs(y - y_ref)
+    bad = err > TOL64 * absy
+    assert not bad.any(), f"{bad.sum()} rows over tolerance; worst {err[bad].max()} vs {(TOL64 * absy)[bad].min()}"
+    assert np.all(y[absy == 0] == 0)
+
+
+@pytest.mark.parametrize("name", list(MATS))
+@pytest.mark.parametrize("r,c", spc5.SHAPES)
+def test_spmv_f64(cuda_device, name, r, c):
+    A = get(name)
+    x = inputs.vec_uniform(A.m, seed=0)
+    y_ref, absy = oracle.csr_spmv_dot2(A, x)
+    d = dev_csr(A)
+    M = spc5.convert(d.rowptr, d.colidx, d.values, A.n, A.m, r, c)
+    xd = torch.from_numpy(x).cuda()
+    buf, y = guarded(A.n, torch.float64)
+    M.spmv(xd, y)
+    torch.cuda.synchronize()
+    check64(y.cpu().numpy(), y_ref, absy)
+    assert torch.isnan(buf[A.n:]).all(), "wrote past the end of y"
+    # the paper's accumulate form: y += A x
+    y0 = inputs.vec_uniform(A.n, seed=1)
+    yd = torch.from_numpy(y0.copy()).cuda()
+    M.spmv_acc(xd, yd)
+    ya = yd.cpu().numpy()
+    err = np.abs(ya - (y0 + y_ref))
+    assert np.all(err <= TOL64 * (absy + np.abs(y0)) + 1e-300)
+    M.destroy()
+
+
+@pytest.mark.parametrize("r,c", spc5.SHAPES)
+def test_long_interval_segments(cuda_device, r, c):
+    # force every interval with more than one block onto the segment path
+    A = get("rmat11")
+    x = inputs.vec_uniform(A.m, seed=0)
+    y_ref, absy = oracle.csr_spmv_dot2(A, x)
+    d = dev_csr(A)
+    xd = torch.from_numpy(x).cuda()
+    for lb, sb in [(1, 1), (1, 3), (2, 7), (4, 64)]:
+        M = spc5.convert(d.rowptr, d.colidx, d.values, A.n, A.m, r, c, long_blocks=lb, seg_blocks=sb)
+        assert M.export()["nsegments"] > 0
+        check64(M.spmv(xd).cpu().numpy(), y_ref, absy)
+        y0 = inputs.vec_uniform(A.n, seed=1)
+        yd = torch.from_numpy(y0.copy()).cuda()
+        M.spmv_acc(xd, yd)
+        assert np.all(np.abs(yd.cpu().numpy() - (y0 + y_ref)) <= TOL64 * (absy + np.abs(y0)))
+        M.destroy()
+
+
+@pytest.mark.parametrize("r,c", spc5.SHAPES)
+def test_dyadic_config_bit_exact_all_precisions(cuda_device, r, c):
+    # 5-point Laplacian with x = k / 2^20: every partial sum is exact in float32
+    # and float64, and the values 4 / -1 are exact in bfloat16, so every format
+    # and precision reproduces the oracle bit for bit.
+    A = get("lap128")
+    x = inputs.vec_dyadic(A.m, seed=0, bits=20)
+    y_ref = oracle.csr_spmv(A, x)
+    for vdt, xdt in [(torch.float64, torch.float64), (torch.float32, torch.float32), (torch.bfloat16, torch.float32)]:
+        d = dev_csr(A, vdt)
+        M = spc5.convert(d.rowptr, d.colidx, d.values, A.n, A.m, r, c)
+        y = M.spmv(torch.from_numpy(x).to(xdt).cuda()).double().cpu().numpy()
+        assert np.array_equal(y, y_ref), (vdt, np.abs(y - y_ref).max())
+        M.destroy()
+
+
+def rounded_case(A, kind):
+    """Values rounded to the storage type and x to float32, on the host."""
+    rv = oracle.round_f32(A.values) if kind == "f32" else oracle.round_bf16(A.values)
+    Ar = inputs.CSR(A.n, A.m, A.rowptr, A.colidx, rv)
+    return Ar
+
+
+@pytest.mark.parametrize("kind", ["f32", "bf16"])
+@pytest.mark.parametrize("name", ["st27_ragged", "rmat11", "uniform", "fem", "rand_ragged"])
+@pytest.mark.parametrize("r,c", [(1, 8), (2, 4), (4, 8), (8, 16), (1, 16), (8, 4)])
+def test_spmv_low_precision(cuda_device, kind, name, r, c):
+    A = get(name)
+    Ar = rounded_case(A, kind)
+    x = oracle.round_f32(inputs.vec_uniform(A.m, seed=0))
+    y_ref, absy = oracle.csr_spmv_dot2(Ar, x)
+    vdt = torch.float32 if kind == "f32" else torch.bfloat16
+    vals = torch.from_numpy(Ar.values).to(vdt)  # exact: values are representable
+    assert np.array_equal(vals.double().numpy(), Ar.values)
+    rowptr = torch.from_numpy(A.rowptr).cuda()
+    colidx = torch.from_numpy(A.colidx).cuda()
+    M = spc5.convert(rowptr, colidx, vals.cuda(), A.n, A.m, r, c)
+    y = M.spmv(torch.from_numpy(x).float().cuda()).double().cpu().numpy()
+    L = np.diff(A.rowptr).astype(np.float64)
+    u = 2.0**-24
+    bound = (L + 1) * u / (1 - (L + 1) * u) * absy
+    assert np.all(np.abs(y - y_ref) <= bound + 1e-45)
+    # error against the float64 oracle on unrounded values (reported, loosely bounded)
+    y64, abs64 = oracle.csr_spmv_dot2(A, inputs.vec_uniform(A.m, seed=0))
+    rel = np.abs(y - y64) / np.maximum(abs64, 1e-300)
+    store = 2.0**-8 if kind == "bf16" else u  # unit roundoff of the storage type (8 / 24 significand bits)
+    assert np.all(rel <= store + (L + 3) * u + 1e-12)
+    M.destroy()
+
+
+@pytest.mark.parametrize("group", [0, 1, 2, 4, 8, 16, 32])
+@pytest.mark.parametrize("name", ["lap128", "st27_ragged", "rmat11", "sparse_rows", "fem"])
+def test_csr_kernel(cuda_device, name, group):
+    A = get(name)
+    x = inputs.vec_uniform(A.m, seed=0)
+    y_ref, absy = oracle.csr_spmv_dot2(A, x)
+    d = dev_csr(A)
+    y = spc5.csr_spmv(d.rowptr, d.colidx, d.values, A.n, A.m, torch.from_numpy(x).cuda(), group=group)
+    check64(y.cpu().numpy(), y_ref, absy)
+    Ar = rounded_case(A, "f32")
+    xr = oracle.round_f32(x)
+    y_ref32, absy32 = oracle.csr_spmv_dot2(Ar, xr)
+    y = spc5.csr_spmv(d.rowptr, d.colidx, torch.from_numpy(Ar.values).float().cuda(), A.n, A.m,
+                      torch.from_numpy(xr).float().cuda(), group=group).double().cpu().numpy()
+    L = np.diff(A.rowptr).astype(np.float64)
+    u = 2.0**-24
+    assert np.all(np.abs(y - y_ref32) <= (L + 1) * u / (1 - (L + 1) * u) * absy32 + 1e-45)
+
+
+def test_invalid_csr_is_rejected_with_codes(cuda_device):
+    def attempt(rowptr, colidx, m):
+        rp = torch.tensor(rowptr, dtype=torch.int64, device="cuda")
+        ci = torch.tensor(colidx, dtype=torch.int32, device="cuda")
+        v = torch.ones(len(colidx), dtype=torch.float64, device="cuda")
+        try:
+            spc5.convert(rp, ci, v, len(rowptr) - 1, m, 2, 4)
+        except spc5.Spc5Error as e:
+            return e.status
+        return spc5.OK
+
+    assert attempt([0, 2, 3], [1, 2, 0], 4) == spc5.OK
+    assert attempt([0, 2, 3], [2, 1, 0], 4) == spc5.EUNSORTED
+    assert attempt([0, 2, 3], [1, 1, 0], 4) == spc5.EDUP
+    assert attempt([0, 2, 3], [1, 2, 4], 4) == spc5.ERANGE
+    assert attempt([0, 2, 3], [1, 2, -1], 4) == spc5.ERANGE
+    # the first bad row decides the code
+    assert attempt([0, 2, 4], [1, 1, 3, 2], 4) == spc5.EDUP
+
+
+def test_empty_and_degenerate(cuda_device):
+    # no entries at all
+    A = inputs.CSR(37, 20, np.zeros(38, np.int64), np.zeros(0, np.int32), np.zeros(0))
+    d = dev_csr(A)
+    for r, c in [(1, 4), (8, 16)]:
+        M = spc5.convert(d.rowptr, d.colidx, d.values, A.n, A.m, r, c)
+        y = M.spmv(torch.ones(20, dtype=torch.float64, device="cuda"))
+        assert torch.count_nonzero(y).item() == 0
+        M.destroy()
+    # one row, one column
+    B = inputs.CSR(1, 1, np.array([0, 1], np.int64), np.array([0], np.int32), np.array([3.0]))
+    d = dev_csr(B)
+    M = spc5.convert(d.rowptr, d.colidx, d.values, 1, 1, 8, 16)
+    assert M.spmv(torch.tensor([2.0], dtype=torch.float64, device="cuda")).item() == 6.0
+    # identity and permutation reproduce x exactly
+    n = 1000
+    x = inputs.vec_normal(n, seed=3)
+    perm = np.random.default_rng(1).permutation(n)
+    P = inputs.CSR(n, n, np.arange(n + 1, dtype=np.int64), perm.astype(np.int32), np.ones(n))
+    Pd = dev_csr(P)
+    for r, c in spc5.SHAPES:
+        M = spc5.convert(Pd.rowptr, Pd.colidx, Pd.values, n, n, r, c)
+        assert np.array_equal(M.spmv(torch.from_numpy(x).cuda()).cpu().numpy(), x[perm])
+        M.destroy()
+
+
+def test_count_blocks_matches_oracle(cuda_device):
+    for name in ["lap128", "rmat11", "st27_ragged", "rand_ragged"]:
+        A = get(name)
+        d = dev_csr(A)
+        got = spc5.count_blocks(d.rowptr, d.colidx, A.n, A.m)
+        want = [oracle.beta_count(A, r, c)[1] for r, c in spc5.SHAPES]
+        assert list(got) == want
+
+
+def test_copy_kernel(cuda_device):
+    a = torch.randint(0, 2**31, (1 << 20,), dtype=torch.int32, device="cuda")
+    b = torch.zeros_like(a)
+    spc5.copy(a, b)
+    assert torch.equal(a, b)
