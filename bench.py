@@ -37,6 +37,7 @@ sys.path.insert(0, ROOT)
 METRIC = "SpMV GFLOP/s & HBM GB/s (% of peak), selected β(r,c) vs CSR, 1 GB300"
 L2_FLUSH_BYTES = 512 << 20
 FP64_PEAK_GFLOPS = 1250.0  # nominal GB300 float64 rate (2 FMA lanes/clk/SM x 152 SMs x 2.07 GHz x 2)
+VARIANTS = (5, 10)  # short-interval kernel variants the tuner tries per shape
 
 
 def parse():
@@ -52,6 +53,7 @@ def parse():
     p.add_argument("--shape", default="4x8", help="block shape of the profiling run, e.g. 4x8, or csr")
     p.add_argument("--dtype", default="f64", choices=["f64", "f32", "bf16"], help="profiling run value type")
     p.add_argument("--reps", type=int, default=3)
+    p.add_argument("--variants", default="0", help="profiling run: comma list of kernel variants (0 = default)")
     return p.parse_args()
 
 
@@ -69,6 +71,17 @@ def workload(small: bool):
                  ("rmat_s22", lambda: inputs.rmat(22, 16, 0.57, 0.19, 0.19, relabel=True, seed=1)),
                  ("uniform_n1M", lambda: inputs.uniform(1000000, 1000000, 8, seed=1))]
     return specs
+
+
+def profile_matrices():
+    """Mid-size members of the same families (above L2, a few hundred MB on the
+    device) for hardware-counter captures."""
+    from paper_1801_01134_gb300 import inputs
+
+    return [("stencil27_96^3", lambda: inputs.stencil3d(96, 96, 96, points=27, seed=1)),
+            ("fem3x3_n1M", lambda: inputs.block_fem(333334, bs=3, bmin=9, bmax=27, band_frac=0.05, seed=1)),
+            ("rmat_s20", lambda: inputs.rmat(20, 16, 0.57, 0.19, 0.19, relabel=True, seed=1)),
+            ("uniform_n1M", lambda: inputs.uniform(1000000, 1000000, 8, seed=1))]
 
 
 def kernel_source_hash() -> str:
@@ -229,7 +242,7 @@ def run_profile(args):
     spc5.load()
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
-    name, gen = next((n, g) for n, g in workload(args.small) if n.startswith(args.profile))
+    name, gen = next((n, g) for n, g in workload(args.small) + profile_matrices() if n.startswith(args.profile))
     A = gen()
     vdt = {"f64": torch.float64, "f32": torch.float32, "bf16": torch.bfloat16}[args.dtype]
     xdt = torch.float64 if args.dtype == "f64" else torch.float32
@@ -238,26 +251,32 @@ def run_profile(args):
     y = torch.empty(A.n, dtype=xdt, device=dev)
     fa = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
     fb = torch.empty_like(fa)
-    if args.shape == "csr":
-        run = lambda: spc5.csr_spmv(d.rowptr, d.colidx, d.values, A.n, A.m, x, y)  # noqa: E731
-        fmt = "csr"
-    else:
-        r, c = (int(v) for v in args.shape.split("x"))
-        M = spc5.convert(d.rowptr, d.colidx, d.values, A.n, A.m, r, c)
-        run = lambda: M.spmv(x, y)  # noqa: E731
-        ex = M.export()
-        fmt = f"beta({r},{c}) nblocks={ex['nblocks']} segments={ex['nsegments']}"
-    ts = []
-    for _ in range(args.reps):
-        spc5.copy(fa, fb)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        run()
-        e1.record()
-        e1.synchronize()
-        ts.append(e0.elapsed_time(e1))
-    print(json.dumps({"profile": name, "format": fmt, "dtype": args.dtype, "n": A.n, "nnz": A.nnz,
-                      "ms": [round(t, 4) for t in ts], "gflops_last": round(2.0 * A.nnz / ts[-1] / 1e6, 1)}))
+    for shape in args.shape.split(","):
+        for variant in (int(v) for v in args.variants.split(",")):
+            if shape == "csr":
+                run = lambda: spc5.csr_spmv(d.rowptr, d.colidx, d.values, A.n, A.m, x, y, group=variant)  # noqa: E731
+                fmt = f"csr group={variant}"
+            else:
+                r, c = (int(v) for v in shape.split("x"))
+                M = spc5.convert(d.rowptr, d.colidx, d.values, A.n, A.m, r, c, variant=variant)
+                run = lambda: M.spmv(x, y)  # noqa: E731
+                ex = M.export()
+                fmt = f"beta({r},{c}) variant={variant} nblocks={ex['nblocks']} segments={ex['nsegments']}"
+            ts = []
+            for _ in range(args.reps):
+                spc5.copy(fa, fb)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                run()
+                e1.record()
+                e1.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            best = min(ts)
+            print(json.dumps({"profile": name, "format": fmt, "dtype": args.dtype, "n": A.n, "nnz": A.nnz,
+                              "ms": [round(t, 4) for t in ts], "gflops_best": round(2.0 * A.nnz / best / 1e6, 1)}),
+                  flush=True)
+            if shape != "csr":
+                M.destroy()
     return 0
 
 
@@ -320,12 +339,18 @@ def main():
             sweep = {}
             for (r, c) in shapes:
                 M = spc5.convert(d.rowptr, d.colidx, d.values, A.n, A.m, r, c)
-                t = time_call(lambda: M.spmv(xd, yd), 5)
+                tv = {}
+                for v in VARIANTS:
+                    M.set_variant(v)
+                    tv[v] = time_call(lambda: M.spmv(xd, yd), 5)
+                v = min(tv, key=tv.get)
+                t = tv[v]
+                M.set_variant(v)
                 sweep[f"{r}x{c}"] = round(2.0 * A.nnz / t / 1e6, 1)
                 if best is None or t < best[0]:
                     if best is not None:
                         best[1].destroy()
-                    best = (t, M, r, c)
+                    best = (t, M, r, c, v)
                 else:
                     M.destroy()
             csr_best = None
@@ -333,9 +358,9 @@ def main():
                 t = time_call(lambda: spc5.csr_spmv(d.rowptr, d.colidx, d.values, A.n, A.m, xd, yd, group=g), 5)
                 if csr_best is None or t < csr_best[0]:
                     csr_best = (t, g)
-            _, M, r, c = best
+            _, M, r, c, v = best
             ex = M.export()
-            out.append({"name": mt["name"], "A": A, "d": d, "x": xd, "y": yd, "M": M, "r": r, "c": c,
+            out.append({"name": mt["name"], "A": A, "d": d, "x": xd, "y": yd, "M": M, "r": r, "c": c, "variant": v,
                         "nblocks": ex["nblocks"], "nseg": ex["nsegments"], "csr_group": csr_best[1],
                         "sweep_gflops": sweep})
         return out
@@ -358,6 +383,7 @@ def main():
         torch.cuda.synchronize()
         return {k: [a.elapsed_time(b) for a, b in v] for k, v in per.items()}
 
+    fp64_measured = spc5.fma_rate(torch.float64)  # live measured float64 FMA rate (GFLOP/s)
     prep64 = prepare(torch.float64)
     flops_step = sum(2.0 * p["A"].nnz for p in prep64)
 
@@ -391,6 +417,7 @@ def main():
     for p in prep64:
         t = statistics.median(times[p["name"]])
         per_matrix.append({"matrix": p["name"], "n": p["A"].n, "nnz": p["A"].nnz, "shape": f"{p['r']}x{p['c']}",
+                           "variant": p["variant"],
                            "avg_nnz_per_block": round(p["A"].nnz / max(p["nblocks"], 1), 3),
                            "ms": round(t, 4), "gflops": round(2.0 * p["A"].nnz / t / 1e6, 1),
                            "gbs": round(beta_bytes(p, 8, 8) / t / 1e6, 1), "segments": p["nseg"],
@@ -404,13 +431,14 @@ def main():
         hbm_peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
     except Exception:
         pass
-    kname = "k_spmv_rows" if dom["nseg"] == 0 else "k_spmv_rows+k_spmv_segments+k_spmv_fixup"
+    kname = "k_spmv_rows_u" if dom["nseg"] == 0 else "k_spmv_rows_u+k_spmv_segments+k_spmv_fixup"
     roofline = {
         "bound": "alu", "achieved": round(dom_flops / dom_t / 1e6, 1), "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
         "frac": round(dom_flops / dom_t / 1e6 / FP64_PEAK_GFLOPS, 4),
         "traffic": profile_traffic(kname, dom["name"]),
         "kernel": f"{kname}<{dom['r']},{dom['c']},f64> on {dom['name']}",
-        "peak_source": "nominal float64 rate of the recipe (1.25 TFLOP/s); measured FMA loop 1.20 TFLOP/s",
+        "peak_source": "nominal float64 rate (2 FMA lanes/clk/SM x 152 SMs x 2.07 GHz x 2 = 1.25 TFLOP/s)",
+        "peak_measured": round(fp64_measured, 1), "frac_of_measured": round(dom_flops / dom_t / 1e6 / fp64_measured, 4),
         "hbm": {"achieved": round(dom_bytes / dom_t / 1e6, 1), "peak": hbm_peak, "unit": "GB/s",
                 "frac": round(dom_bytes / dom_t / 1e6 / hbm_peak, 4), "algorithmic_bytes": int(dom_bytes),
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"},
@@ -488,8 +516,8 @@ def main():
         "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": "suite4 float64: " + ", ".join(p["name"] for p in prep64),
-                   "formats": {p["name"]: f"beta({p['r']},{p['c']})" for p in prep64},
-                   "selection": "exhaustive timing over the 12 shapes (the paper's best kernel)",
+                   "formats": {p["name"]: f"beta({p['r']},{p['c']}) variant {p['variant']}" for p in prep64},
+                   "selection": "exhaustive timing over the 12 shapes x kernel variants (the paper's best kernel)",
                    "l2": f"flushed before every SpMV ({L2_FLUSH_BYTES >> 20} MiB copy, outside the events)",
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
         "hbm_gbs": round(sum(beta_bytes(p, 8, 8) for p in prep64) * args.steps / (total_ms * 1e-3) / 1e9, 1),

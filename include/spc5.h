@@ -63,8 +63,14 @@ typedef struct {
    * seg_blocks = 256. */
   int32_t long_blocks;
   int32_t seg_blocks;
-  /* SpMV kernel variant: 0 = automatic; other values select a specific
-   * variant (for tuning and tests). */
+  /* SpMV kernel variant for short intervals (one lane per row):
+   *   0 or 5  natural interval order, next 2 nonzeros decoded per loop trip;
+   *   3       natural order, 4 nonzeros per trip;
+   *   1       natural order, one nonzero per trip (plain form);
+   *   9 / 10  intervals taken in a work order sorted by row length inside
+   *           windows of 4096 rows (2 / 4 nonzeros per trip); the order is
+   *           built at conversion.
+   * All variants compute the same sums in the same order per row. */
   int32_t variant;
   int32_t reserved[5];
 } spc5_opts;
@@ -117,6 +123,14 @@ spc5_status spc5_spmv(spc5_handle h, const void* x_d, void* y_d, spc5_stream_t s
  */
 spc5_status spc5_spmv_acc(spc5_handle h, const void* x_d, void* y_d, spc5_stream_t stream);
 
+/*
+ * spc5_set_variant - switch the short-interval kernel variant of a handle
+ * (values as in spc5_opts.variant). Selecting 9 or 10 builds the sorted work
+ * order if the handle has none yet (synchronises `stream`); the other values
+ * take effect with no device work. SPC5_EINVAL for an unknown variant.
+ */
+spc5_status spc5_set_variant(spc5_handle h, int variant, spc5_stream_t stream);
+
 /* spc5_export - fill *view with the handle's device arrays (valid until
  * spc5_destroy). No device work. */
 spc5_status spc5_export(spc5_handle h, spc5_arrays* view);
@@ -157,6 +171,16 @@ spc5_status spc5_csr_spmv(int64_t n, int64_t m, int64_t nnz, const int64_t* rowp
  * HBM bandwidth next to the SpMV kernels.
  */
 spc5_status spc5_copy(const void* src_d, void* dst_d, int64_t bytes, spc5_stream_t stream);
+
+/*
+ * spc5_fma_rate - launch an arithmetic-rate probe: 8 CTAs of 256 threads per
+ * SM, each thread running 8 independent fused multiply-add chains for `iters`
+ * trips in float64 (vt = SPC5_F64) or float32 (SPC5_F32). *fmas_out receives
+ * the number of multiply-adds the launch performs; timing it with events on
+ * `stream` gives the measured peak of the ALU roofline. sink_d: device buffer
+ * of at least 256 elements of the type (written only in an impossible case).
+ */
+spc5_status spc5_fma_rate(spc5_dtype vt, int64_t iters, void* sink_d, int64_t* fmas_out, spc5_stream_t stream);
 
 #ifdef __cplusplus
 }

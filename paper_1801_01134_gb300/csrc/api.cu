@@ -73,6 +73,9 @@ spc5_status spc5_convert(int64_t n, int64_t m, int64_t nnz, const int64_t* rowpt
   if (!shape_supported(r, c)) return fail(SPC5_EUNSUPPORTED, "convert: block shape must be r in {1,2,4,8}, c in {4,8,16}");
   if (vt != SPC5_F64 && vt != SPC5_F32 && vt != SPC5_BF16) return fail(SPC5_EUNSUPPORTED, "convert: value type");
   if (opt && (opt->long_blocks < 0 || opt->seg_blocks < 0)) return fail(SPC5_EINVAL, "convert: negative option");
+  if (opt && !(opt->variant == 0 || opt->variant == 1 || opt->variant == 3 || opt->variant == 5 || opt->variant == 9 ||
+               opt->variant == 10))
+    return fail(SPC5_EINVAL, "convert: variant must be 0, 1, 3, 5, 9 or 10");
   spc5_matrix* h = nullptr;
   st = convert_impl(n, m, nnz, rowptr_d, colidx_d, values_d, vt, r, c, opt, (cudaStream_t)stream, &h);
   if (st != SPC5_OK) return st;
@@ -86,6 +89,18 @@ spc5_status spc5_spmv(spc5_handle h, const void* x_d, void* y_d, spc5_stream_t s
 
 spc5_status spc5_spmv_acc(spc5_handle h, const void* x_d, void* y_d, spc5_stream_t stream) {
   return spmv_common(h, x_d, y_d, true, (cudaStream_t)stream);
+}
+
+spc5_status spc5_set_variant(spc5_handle h, int variant, spc5_stream_t stream) {
+  if (!h) return fail(SPC5_EINVAL, "set_variant: NULL handle");
+  if (!(variant == 0 || variant == 1 || variant == 3 || variant == 5 || variant == 9 || variant == 10))
+    return fail(SPC5_EINVAL, "set_variant: variant must be 0, 1, 3, 5, 9 or 10");
+  if (variant == 9 || variant == 10) {
+    spc5_status st = build_order(h, (cudaStream_t)stream);
+    if (st != SPC5_OK) return st;
+  }
+  h->variant = variant;
+  return SPC5_OK;
 }
 
 spc5_status spc5_export(spc5_handle h, spc5_arrays* v) {
@@ -146,6 +161,14 @@ spc5_status spc5_copy(const void* src_d, void* dst_d, int64_t bytes, spc5_stream
   if (((uintptr_t)src_d | (uintptr_t)dst_d) & 15u) return fail(SPC5_EINVAL, "copy: pointers must be 16-byte aligned");
   cudaError_t e = launch_copy(src_d, dst_d, bytes, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "copy launch");
+  return SPC5_OK;
+}
+
+spc5_status spc5_fma_rate(spc5_dtype vt, int64_t iters, void* sink_d, int64_t* fmas_out, spc5_stream_t stream) {
+  if ((vt != SPC5_F64 && vt != SPC5_F32) || iters < 0 || !sink_d || !fmas_out)
+    return fail(SPC5_EINVAL, "fma_rate: bad argument");
+  cudaError_t e = launch_fma_rate(vt, iters, sink_d, fmas_out, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "fma_rate launch");
   return SPC5_OK;
 }
 

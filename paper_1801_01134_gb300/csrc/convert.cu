@@ -103,13 +103,19 @@ __global__ void k_count(int64_t n, int64_t I, int c, const int64_t* __restrict__
   counts[it] = cover_interval<R>(rowptr, colidx, row0, rows, c, [](int64_t, int32_t, const int64_t*, const int64_t*) {});
 }
 
-// warp segments of each long interval (0 for short ones)
-__global__ void k_nseg(int64_t I, int long_blocks, int seg_blocks, const int32_t* __restrict__ counts,
+// Warp segments of each long interval (0 for short ones). An interval is long
+// when it has more than long_blocks blocks or more than long_values values:
+// one lane per row would then hold up its whole warp.
+__global__ void k_nseg(int64_t n, int64_t I, int r, int long_blocks, int64_t long_values, int seg_blocks,
+                       const int32_t* __restrict__ counts, const int64_t* __restrict__ rowptr,
                        int32_t* __restrict__ nseg) {
   int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (it >= I) return;
   int32_t nb = counts[it];
-  nseg[it] = nb > long_blocks ? (nb + seg_blocks - 1) / seg_blocks : 0;
+  const int64_t r0 = it * r, r1 = (it + 1) * r < n ? (it + 1) * r : n;
+  const int64_t nv = rowptr[r1] - rowptr[r0];
+  const bool lng = nb > long_blocks || nv > long_values;
+  nseg[it] = lng ? (nb + seg_blocks - 1) / seg_blocks : 0;
 }
 
 template <int R, class VT>
@@ -301,6 +307,7 @@ void count_r(int r, int64_t n, int64_t I, int c, const int64_t* rowptr, const in
 
 void free_matrix(spc5_matrix* h) {
   if (!h) return;
+  cudaFree(h->order);
   cudaFree(h->block_rowptr);
   cudaFree(h->block_colidx);
   cudaFree(h->block_masks);
@@ -319,7 +326,100 @@ cudaError_t alloc_padded(void** p, size_t bytes, cudaStream_t s) {
   return e;
 }
 
+// Longest row (in stored entries) of each short interval, from the masks;
+// -1 for the intervals of the segment path.
+template <int R, int C>
+__global__ void k_order_key(int64_t I, int32_t long_blocks, int64_t long_values, const int32_t* __restrict__ brp,
+                            const uint8_t* __restrict__ masks, const int64_t* __restrict__ valptr,
+                            int32_t* __restrict__ key) {
+  constexpr int MB = (R * C + 7) / 8;
+  const int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (it >= I) return;
+  const int32_t b0 = brp[it], b1 = brp[it + 1];
+  if (b1 - b0 > long_blocks || valptr[it + 1] - valptr[it] > long_values) {
+    key[it] = -1;
+    return;
+  }
+  int32_t len[R];
+#pragma unroll
+  for (int i = 0; i < R; ++i) len[i] = 0;
+  for (int32_t b = b0; b < b1; ++b) {
+    uint32_t w[4] = {0u, 0u, 0u, 0u};
+    for (int q = 0; q < MB; ++q) w[q >> 2] |= (uint32_t)masks[(int64_t)b * MB + q] << (8 * (q & 3));
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+      const int p = i * C;
+      len[i] += __popc((w[p >> 5] >> (p & 31)) & (C == 32 ? 0xffffffffu : ((1u << C) - 1u)));
+    }
+  }
+  int32_t mx = 0;
+#pragma unroll
+  for (int i = 0; i < R; ++i) mx = len[i] > mx ? len[i] : mx;
+  key[it] = mx;
+}
+
+template <int R>
+void launch_order_key(int c, const spc5_matrix* h, int32_t* key, cudaStream_t s) {
+  const unsigned grid = (unsigned)((h->I + 255) / 256);
+  switch (c) {
+    case 4: k_order_key<R, 4><<<grid, 256, 0, s>>>(h->I, h->long_blocks, h->long_values, h->block_rowptr, h->block_masks, h->valptr, key); break;
+    case 8: k_order_key<R, 8><<<grid, 256, 0, s>>>(h->I, h->long_blocks, h->long_values, h->block_rowptr, h->block_masks, h->valptr, key); break;
+    default: k_order_key<R, 16><<<grid, 256, 0, s>>>(h->I, h->long_blocks, h->long_values, h->block_rowptr, h->block_masks, h->valptr, key); break;
+  }
+}
+
 }  // namespace
+
+// Work order of the lane-per-row kernel (variants 9 and 10): the short
+// intervals, sorted by their longest row (descending, stable) inside windows
+// of kOrderWindow rows, so that the 32/r intervals of one warp have rows of
+// similar length and the warp's multiply-adds are fully packed. The storage
+// is untouched; only the assignment of intervals to lanes changes.
+spc5_status build_order(spc5_matrix* h, cudaStream_t s) {
+  if (h->order || h->I == 0) return SPC5_OK;
+  const int64_t I = h->I;
+  DeviceBuf keyd;
+  cudaError_t e = cudaMalloc(&keyd.p, sizeof(int32_t) * (size_t)I);
+  if (e != cudaSuccess) return cuda_fail(e, "work order: scratch");
+  switch (h->r) {
+    case 1: launch_order_key<1>(h->c, h, (int32_t*)keyd.p, s); break;
+    case 2: launch_order_key<2>(h->c, h, (int32_t*)keyd.p, s); break;
+    case 4: launch_order_key<4>(h->c, h, (int32_t*)keyd.p, s); break;
+    default: launch_order_key<8>(h->c, h, (int32_t*)keyd.p, s); break;
+  }
+  std::vector<int32_t> key((size_t)I);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(key.data(), keyd.p, sizeof(int32_t) * (size_t)I, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "work order: keys");
+  std::vector<int32_t> order;
+  order.reserve((size_t)I);
+  std::vector<std::pair<int32_t, int32_t>> win;
+  const int64_t wiv = kOrderWindow / h->r;
+  for (int64_t w0 = 0; w0 < I; w0 += wiv) {
+    const int64_t w1 = w0 + wiv < I ? w0 + wiv : I;
+    win.clear();
+    for (int64_t it = w0; it < w1; ++it)
+      if (key[(size_t)it] >= 0) win.emplace_back(-key[(size_t)it], (int32_t)it);
+    std::stable_sort(win.begin(), win.end(), [](const std::pair<int32_t, int32_t>& a,
+                                                const std::pair<int32_t, int32_t>& b) { return a.first < b.first; });
+    for (auto& pr : win) order.push_back(pr.second);
+  }
+  if (!order.empty()) {
+    int32_t* d = nullptr;
+    e = alloc_padded((void**)&d, sizeof(int32_t) * order.size(), s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(d, order.data(), sizeof(int32_t) * order.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+      cudaFree(d);
+      return cuda_fail(e, "work order: upload");
+    }
+    h->order = d;
+  }
+  h->norder = (int64_t)order.size();
+  return SPC5_OK;
+}
 
 void destroy_matrix(spc5_matrix* h) { free_matrix(h); }
 
@@ -392,9 +492,15 @@ spc5_status convert_impl(int64_t n, int64_t m, int64_t nnz, const int64_t* rowpt
     const double lim = 4.0 * mean;
     h->long_blocks = lim > kLongBlocks ? (lim < (double)INT_MAX ? (int32_t)lim : INT_MAX) : kLongBlocks;
   }
+  {
+    // an interval is also long when it holds many more values than the mean
+    const double mean_v = I > 0 ? (double)nnz / (double)I : 0.0;
+    const double lv = 8.0 * mean_v;
+    h->long_values = lv > 2048.0 * r ? (int64_t)lv : (int64_t)2048 * r;
+  }
   if (I > 0)
-    k_nseg<<<(unsigned)((I + 255) / 256), 256, 0, s>>>(I, h->long_blocks, h->seg_blocks, (const int32_t*)counts.p,
-                                                      (int32_t*)nseg.p);
+    k_nseg<<<(unsigned)((I + 255) / 256), 256, 0, s>>>(n, I, r, h->long_blocks, h->long_values, h->seg_blocks,
+                                                      (const int32_t*)counts.p, rowptr, (int32_t*)nseg.p);
   DeviceBuf segptr;
   e = cudaMalloc(&segptr.p, sizeof(int32_t) * (size_t)(I + 1));
   if (e != cudaSuccess) return bail(cuda_fail(e, "convert: segment pointers"));
@@ -422,6 +528,11 @@ spc5_status convert_impl(int64_t n, int64_t m, int64_t nnz, const int64_t* rowpt
   e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return bail(cuda_fail(e, "convert: fill"));
+
+  if (h->variant == 9 || h->variant == 10) {
+    spc5_status st2 = build_order(h, s);
+    if (st2 != SPC5_OK) return bail(st2);
+  }
   *out = h;
   return SPC5_OK;
 }

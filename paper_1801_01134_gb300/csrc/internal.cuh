@@ -18,6 +18,8 @@ constexpr int kLongBlocks = 64;
 constexpr int kSegBlocks = 256;
 constexpr int kWarp = 32;
 
+constexpr int kOrderWindow = 4096;  // rows per sorting window of the work order
+
 struct Segment {  // one warp task of a long interval
   int32_t interval;
   int32_t b_begin;
@@ -42,11 +44,15 @@ struct spc5_matrix {
   int64_t* valptr = nullptr;        // [I+1]
   // execution plan
   int32_t long_blocks = spc5::kLongBlocks;
+  int64_t long_values = INT64_MAX;  // an interval with more values is long too
   int32_t seg_blocks = spc5::kSegBlocks;
   int32_t variant = 0;
   int64_t nseg = 0;
   spc5::Segment* segs = nullptr;    // [nseg]
   void* partials = nullptr;         // [nseg * r] accumulation-type scratch
+  // work order of the lane-per-row kernel (short intervals only)
+  int64_t norder = 0;
+  int32_t* order = nullptr;            // [norder] interval indices
 };
 
 namespace spc5 {
@@ -66,6 +72,7 @@ inline size_t value_size(spc5_dtype t) { return t == SPC5_F64 ? 8 : (t == SPC5_F
 spc5_status convert_impl(int64_t n, int64_t m, int64_t nnz, const int64_t* rowptr, const int32_t* colidx,
                          const void* values, spc5_dtype vt, int r, int c, const spc5_opts* opt, cudaStream_t s,
                          spc5_matrix** out);
+spc5_status build_order(spc5_matrix* h, cudaStream_t s);
 spc5_status count_blocks_impl(int64_t n, int64_t nnz, const int64_t* rowptr, const int32_t* colidx,
                               int64_t* nblocks_out, cudaStream_t s);
 
@@ -82,6 +89,7 @@ cudaError_t launch_csr_spmv_group(int group, int64_t n, int64_t nnz, const int64
 int csr_auto_group(int64_t n, int64_t nnz, spc5_dtype vt);
 void destroy_matrix(spc5_matrix* h);
 cudaError_t launch_copy(const void* src, void* dst, int64_t bytes, cudaStream_t s);
+cudaError_t launch_fma_rate(spc5_dtype vt, int64_t iters, void* sink, int64_t* fmas, cudaStream_t s);
 
 int sm_count();
 

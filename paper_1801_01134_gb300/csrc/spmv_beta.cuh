@@ -121,6 +121,15 @@ struct BF16 {
   static __device__ __forceinline__ A xv(const X* p, int64_t i) { return __ldg(p + i); }
 };
 
+// value read from shared memory (generic load)
+template <class T>
+__device__ __forceinline__ typename T::A sval(const typename T::V* p, int i) {
+  if constexpr (sizeof(typename T::V) == 2)
+    return __uint_as_float(((uint32_t)p[i]) << 16);
+  else
+    return p[i];
+}
+
 template <class T>
 __device__ __forceinline__ typename T::A fmadd(typename T::A a, typename T::A b, typename T::A c) {
   return fma(a, b, c);
@@ -128,7 +137,7 @@ __device__ __forceinline__ typename T::A fmadd(typename T::A a, typename T::A b,
 
 // ------------------------------------------------------- short intervals
 template <int R, int C, class T, bool ACCUM>
-__global__ void __launch_bounds__(256) k_spmv_rows(int64_t n, int64_t I, int32_t long_blocks,
+__global__ void __launch_bounds__(256) k_spmv_rows(int64_t n, int64_t I, int32_t long_blocks, int64_t long_values,
                                                    const int32_t* __restrict__ brp, const int32_t* __restrict__ bcol,
                                                    const uint8_t* __restrict__ bmask, const typename T::V* __restrict__ val,
                                                    const int64_t* __restrict__ valptr, const typename T::X* __restrict__ x,
@@ -142,8 +151,8 @@ __global__ void __launch_bounds__(256) k_spmv_rows(int64_t n, int64_t I, int32_t
   if (it >= I) return;
   int32_t b = __ldg(brp + it);
   const int32_t bend = __ldg(brp + it + 1);
-  if (bend - b > long_blocks) return;  // written by the segment path
   int64_t vbase = __ldg(valptr + it);
+  if (bend - b > long_blocks || __ldg(valptr + it + 1) - vbase > long_values) return;  // the segment path's
   typename T::A acc = 0;
   uint32_t bits = 0;
   int32_t col0 = 0;
@@ -162,6 +171,92 @@ __global__ void __launch_bounds__(256) k_spmv_rows(int64_t n, int64_t I, int32_t
     bits &= bits - 1;
     acc = fmadd<T>(T::val(val, vo), T::xv(x, (int64_t)col0 + k), acc);
     ++vo;
+  }
+  const int64_t row = it * R + i;
+  if (row < n) {
+    if (ACCUM)
+      y[row] = y[row] + acc;
+    else
+      y[row] = acc;
+  }
+}
+
+// ------------------------------------------- short intervals, unrolled form
+// Same mapping, arithmetic and summation order as k_spmv_rows; each loop trip
+// decodes the lane's next U nonzeros first (the mask and column index of the
+// following block are already loaded one block ahead), then issues their U
+// value loads and U x loads together, then the U multiply-adds (predicated
+// off past the end of the row). U independent loads per lane are in flight
+// instead of one.
+//
+// With ORDER, lane slot q of the warp takes interval order[q] instead of q
+// (the sorted work order built at conversion; long intervals are not in it).
+template <int R, int C, class T, bool ACCUM, int U, bool ORDER>
+__global__ void __launch_bounds__(256) k_spmv_rows_u(int64_t n, int64_t I, int32_t long_blocks, int64_t long_values,
+                                                     const int32_t* __restrict__ brp, const int32_t* __restrict__ bcol,
+                                                     const uint8_t* __restrict__ bmask,
+                                                     const typename T::V* __restrict__ val,
+                                                     const int64_t* __restrict__ valptr,
+                                                     const typename T::X* __restrict__ x,
+                                                     typename T::X* __restrict__ y,
+                                                     const int32_t* __restrict__ order, int64_t norder) {
+  constexpr int MB = (R * C + 7) / 8;
+  constexpr int S = kWarp / R;
+  using A = typename T::A;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int64_t it = warp * S + lane / R;
+  if (ORDER) {
+    if (it >= norder) return;
+    it = __ldg(order + it);
+  }
+  const int i = lane % R;
+  if (it >= I) return;
+  int32_t b = __ldg(brp + it);
+  const int32_t bend = __ldg(brp + it + 1);
+  const int64_t vbase0 = __ldg(valptr + it);
+  if (bend - b > long_blocks || __ldg(valptr + it + 1) - vbase0 > long_values) return;  // the segment path's
+  const typename T::V* __restrict__ vrow = val + vbase0;  // the interval's values
+  int32_t vbase = 0;  // offset of block b's first value inside the interval
+  uint32_t bits = 0;
+  int32_t col0 = 0, vo = 0;
+  Mask<MB> nmk = b < bend ? load_mask<MB>(bmask, b) : zero_mask<MB>();
+  int32_t ncol = b < bend ? __ldg(bcol + b) : 0;
+  A acc = 0;
+  for (;;) {
+    int32_t vi[U], xi[U];
+    bool h[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      while (bits == 0 && b < bend) {
+        const Mask<MB> mk = nmk;
+        col0 = ncol;
+        if (b + 1 < bend) {
+          nmk = load_mask<MB>(bmask, b + 1);
+          ncol = __ldg(bcol + b + 1);
+        }
+        bits = row_bits<C>(mk, i);
+        vo = vbase + popc_below<C>(mk, i);
+        vbase += popc_all(mk);
+        ++b;
+      }
+      h[u] = bits != 0;
+      const int k = __ffs(bits) - 1;
+      bits &= bits - 1;
+      vi[u] = vo;
+      vo += h[u] ? 1 : 0;
+      xi[u] = col0 + k;
+    }
+    if (!h[0]) break;
+    A v[U], xx[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      v[u] = h[u] ? T::val(vrow, vi[u]) : A(0);
+      xx[u] = h[u] ? T::xv(x, xi[u]) : A(0);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (h[u]) acc = fmadd<T>(v[u], xx[u], acc);
   }
   const int64_t row = it * R + i;
   if (row < n) {
@@ -252,13 +347,40 @@ cudaError_t launch_beta(const spc5_matrix* h, const void* xv, void* yv, bool acc
   const int threads = 256;
   if (h->I > 0) {
     const int64_t warps = (h->I + S - 1) / S;
-    const unsigned grid = (unsigned)((warps * kWarp + threads - 1) / threads);
-    if (acc)
-      k_spmv_rows<R, C, T, true><<<grid, threads, 0, s>>>(h->n, h->I, h->long_blocks, h->block_rowptr, h->block_colidx,
-                                                          h->block_masks, val, h->valptr, x, y);
-    else
-      k_spmv_rows<R, C, T, false><<<grid, threads, 0, s>>>(h->n, h->I, h->long_blocks, h->block_rowptr, h->block_colidx,
-                                                           h->block_masks, val, h->valptr, x, y);
+    if (h->variant == 1) {
+      const unsigned grid = (unsigned)((warps * kWarp + threads - 1) / threads);
+      if (acc)
+        k_spmv_rows<R, C, T, true><<<grid, threads, 0, s>>>(h->n, h->I, h->long_blocks, h->long_values, h->block_rowptr,
+                                                            h->block_colidx, h->block_masks, val, h->valptr, x, y);
+      else
+        k_spmv_rows<R, C, T, false><<<grid, threads, 0, s>>>(h->n, h->I, h->long_blocks, h->long_values, h->block_rowptr,
+                                                             h->block_colidx, h->block_masks, val, h->valptr, x, y);
+    } else if ((h->variant == 9 || h->variant == 10) && h->norder > 0) {
+      // sorted work order
+      const int64_t owarps = (h->norder + S - 1) / S;
+      const unsigned grid = (unsigned)((owarps * kWarp + threads - 1) / threads);
+      auto go = [&](auto kern) {
+        kern<<<grid, threads, 0, s>>>(h->n, h->I, h->long_blocks, h->long_values, h->block_rowptr, h->block_colidx,
+                                      h->block_masks, val, h->valptr, x, y, h->order, h->norder);
+      };
+      if (h->variant == 10) {
+        if (acc) go(k_spmv_rows_u<R, C, T, true, 4, true>); else go(k_spmv_rows_u<R, C, T, false, 4, true>);
+      } else {
+        if (acc) go(k_spmv_rows_u<R, C, T, true, 2, true>); else go(k_spmv_rows_u<R, C, T, false, 2, true>);
+      }
+    } else {
+      // natural order; variant 3 unrolls by 4, the default (0 or 5) by 2
+      const unsigned grid = (unsigned)((warps * kWarp + threads - 1) / threads);
+      auto go = [&](auto kern) {
+        kern<<<grid, threads, 0, s>>>(h->n, h->I, h->long_blocks, h->long_values, h->block_rowptr, h->block_colidx,
+                                      h->block_masks, val, h->valptr, x, y, nullptr, (int64_t)0);
+      };
+      if (h->variant == 3) {
+        if (acc) go(k_spmv_rows_u<R, C, T, true, 4, false>); else go(k_spmv_rows_u<R, C, T, false, 4, false>);
+      } else {
+        if (acc) go(k_spmv_rows_u<R, C, T, true, 2, false>); else go(k_spmv_rows_u<R, C, T, false, 2, false>);
+      }
+    }
   }
   if (h->nseg > 0) {
     A* part = static_cast<A*>(h->partials);

@@ -68,14 +68,16 @@ def load(build_if_missing: bool = False):
     lib.spc5_spmv.argtypes = [vp, vp, vp, vp]
     lib.spc5_spmv_acc.argtypes = [vp, vp, vp, vp]
     lib.spc5_export.argtypes = [vp, ctypes.POINTER(Arrays)]
+    lib.spc5_set_variant.argtypes = [vp, i32, vp]
     lib.spc5_destroy.argtypes = [vp]
     lib.spc5_last_error.argtypes = []
     lib.spc5_last_error.restype = ctypes.c_char_p
     lib.spc5_count_blocks.argtypes = [i64, i64, i64, vp, vp, vp, vp]
     lib.spc5_csr_spmv.argtypes = [i64, i64, i64, vp, vp, vp, i32, vp, vp, i32, vp]
     lib.spc5_copy.argtypes = [vp, vp, i64, vp]
-    for f in (lib.spc5_convert, lib.spc5_spmv, lib.spc5_spmv_acc, lib.spc5_export, lib.spc5_destroy,
-              lib.spc5_count_blocks, lib.spc5_csr_spmv, lib.spc5_copy):
+    lib.spc5_fma_rate.argtypes = [i32, i64, vp, vp, vp]
+    for f in (lib.spc5_convert, lib.spc5_spmv, lib.spc5_spmv_acc, lib.spc5_export, lib.spc5_destroy, lib.spc5_set_variant,
+              lib.spc5_count_blocks, lib.spc5_csr_spmv, lib.spc5_copy, lib.spc5_fma_rate):
         f.restype = st
     _lib = lib
     return lib
@@ -141,6 +143,11 @@ class Matrix:
             raise TypeError(f"x and y must be {self.vector_dtype}")
         if x.numel() != self.m or y.numel() != self.n:
             raise ValueError("x must have m entries and y n entries")
+
+    def set_variant(self, variant: int, stream=None):
+        """Switch the short-interval kernel variant (see spc5_opts.variant)."""
+        _check(load().spc5_set_variant(self._h, variant, _stream_ptr(stream)), "spc5_set_variant")
+        self.variant = variant
 
     def arrays(self) -> Arrays:
         a = Arrays()
@@ -225,6 +232,24 @@ def copy(src: torch.Tensor, dst: torch.Tensor, stream=None):
     """dst = src with the library's streaming copy kernel (HBM ceiling)."""
     nbytes = src.numel() * src.element_size()
     copy_raw(_ptr(src), _ptr(dst), nbytes, stream)
+
+
+def fma_rate(dtype: torch.dtype = torch.float64, iters: int = 4096, reps: int = 5) -> float:
+    """Measured multiply-add rate of the library's probe kernel, in GFLOP/s (2 flops per FMA)."""
+    vt = {torch.float64: SPC5_F64, torch.float32: SPC5_F32}[dtype]
+    sink = torch.empty(256, dtype=dtype, device="cuda")
+    fmas = ctypes.c_int64()
+    _check(load().spc5_fma_rate(vt, 16, _ptr(sink), ctypes.byref(fmas), _stream_ptr(None)), "spc5_fma_rate")
+    best = None
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        _check(load().spc5_fma_rate(vt, iters, _ptr(sink), ctypes.byref(fmas), _stream_ptr(None)), "spc5_fma_rate")
+        e1.record()
+        e1.synchronize()
+        t = e0.elapsed_time(e1)
+        best = t if best is None or t < best else best
+    return 2.0 * fmas.value / (best * 1e-3) / 1e9
 
 
 @dataclass

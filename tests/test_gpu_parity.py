@@ -100,6 +100,19 @@ def test_spmv_f64(cuda_device, name, r, c):
     M.destroy()
 
 
+@pytest.mark.parametrize("variant", [1, 3, 5, 9, 10])
+@pytest.mark.parametrize("name", ["st27_ragged", "rmat11", "fem", "sparse_rows"])
+@pytest.mark.parametrize("r,c", [(1, 4), (2, 8), (4, 16), (8, 8)])
+def test_spmv_variants(cuda_device, variant, name, r, c):
+    A = get(name)
+    x = inputs.vec_uniform(A.m, seed=0)
+    y_ref, absy = oracle.csr_spmv_dot2(A, x)
+    d = dev_csr(A)
+    M = spc5.convert(d.rowptr, d.colidx, d.values, A.n, A.m, r, c, variant=variant)
+    check64(M.spmv(torch.from_numpy(x).cuda()).cpu().numpy(), y_ref, absy)
+    M.destroy()
+
+
 @pytest.mark.parametrize("r,c", spc5.SHAPES)
 def test_long_interval_segments(cuda_device, r, c):
     # force every interval with more than one block onto the segment path
