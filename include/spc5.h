@@ -131,6 +131,26 @@ spc5_status spc5_spmv_acc(spc5_handle h, const void* x_d, void* y_d, spc5_stream
  */
 spc5_status spc5_set_variant(spc5_handle h, int variant, spc5_stream_t stream);
 
+/*
+ * spc5_spmv_noalloc - y = A x like spc5_spmv, for callers that cannot have a
+ * library allocate device memory (their memory is owned by another
+ * component's pool, or every allocation is budgeted up front). The paper has
+ * no counterpart; this is an interface convenience.
+ *   - Allocates nothing: the long-interval scratch lives in one fixed 4 MiB
+ *     array inside the library's device image, resident on every GPU that
+ *     loads the library until the process exits.
+ *   - A handle needing more than 4 MiB of segment scratch (n_segments * r
+ *     accumulators of 8 bytes for float64, 4 otherwise; see
+ *     spc5_arrays.nsegments) is rejected with SPC5_ERANGE before any launch.
+ *   - All calls on a device share that array: calls whose kernels may
+ *     overlap on the GPU (unordered streams) race. Nothing needs clearing
+ *     between calls.
+ *   - The first call on each device looks up the array's address with that
+ *     device current; make it before any stream capture begins.
+ * Arguments, vector types and errors otherwise as spc5_spmv.
+ */
+spc5_status spc5_spmv_noalloc(spc5_handle h, const void* x_d, void* y_d, spc5_stream_t stream);
+
 /* spc5_export - fill *view with the handle's device arrays (valid until
  * spc5_destroy). No device work. */
 spc5_status spc5_export(spc5_handle h, spc5_arrays* view);

@@ -76,8 +76,9 @@ def load(build_if_missing: bool = False):
     lib.spc5_csr_spmv.argtypes = [i64, i64, i64, vp, vp, vp, i32, vp, vp, i32, vp]
     lib.spc5_copy.argtypes = [vp, vp, i64, vp]
     lib.spc5_fma_rate.argtypes = [i32, i64, vp, vp, vp]
+    lib.spc5_spmv_noalloc.argtypes = [vp, vp, vp, vp]
     for f in (lib.spc5_convert, lib.spc5_spmv, lib.spc5_spmv_acc, lib.spc5_export, lib.spc5_destroy, lib.spc5_set_variant,
-              lib.spc5_count_blocks, lib.spc5_csr_spmv, lib.spc5_copy, lib.spc5_fma_rate):
+              lib.spc5_count_blocks, lib.spc5_csr_spmv, lib.spc5_copy, lib.spc5_fma_rate, lib.spc5_spmv_noalloc):
         f.restype = st
     _lib = lib
     return lib
@@ -128,6 +129,12 @@ class Matrix:
             y = torch.empty(self.n, dtype=self.vector_dtype, device=x.device)
         self._check_vectors(x, y)
         _check(load().spc5_spmv(self._h, _ptr(x), _ptr(y), _stream_ptr(stream)), "spc5_spmv")
+        return y
+
+    def spmv_noalloc(self, x: torch.Tensor, y: torch.Tensor, stream=None) -> torch.Tensor:
+        """y = A x without any allocation by the library (fixed scratch array; see spc5.h)."""
+        self._check_vectors(x, y)
+        _check(load().spc5_spmv_noalloc(self._h, _ptr(x), _ptr(y), _stream_ptr(stream)), "spc5_spmv_noalloc")
         return y
 
     def spmv_acc(self, x: torch.Tensor, y: torch.Tensor, stream=None) -> torch.Tensor:
