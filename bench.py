@@ -54,6 +54,10 @@ def parse():
     p.add_argument("--dtype", default="f64", choices=["f64", "f32", "bf16"], help="profiling run value type")
     p.add_argument("--reps", type=int, default=3)
     p.add_argument("--variants", default="0", help="profiling run: comma list of kernel variants (0 = default)")
+    p.add_argument("--cg-profile", action="store_true", help="run the CG solvers once each with timings")
+    p.add_argument("--cg-n", type=int, default=96, help="grid edge of the CG profiling matrix")
+    p.add_argument("--cg-every", type=int, default=8)
+    p.add_argument("--cg-graph", type=int, default=1)
     return p.parse_args()
 
 
@@ -230,6 +234,41 @@ def run_reference(args):
     return 0
 
 
+# ------------------------------------------------------------------------ CG
+
+def run_cg_section(dev, reps: int = 3):
+    """Time float64 CG and mixed float32 / bfloat16 refinement to ||r|| / ||b|| <= 1e-10
+    on the 7-point Poisson matrix of a 96^3 grid (b uniform[-1,1] seed 0)."""
+    import torch
+
+    from paper_1801_01134_gb300 import inputs, spc5
+
+    A = inputs.stencil3d(96, 96, 96, points=7, normal_values=False)
+    b = torch.from_numpy(inputs.vec_uniform(A.n, seed=0)).to(dev)
+    hs = {}
+    for name, dt in (("f64", torch.float64), ("f32", torch.float32), ("bf16", torch.bfloat16)):
+        d = spc5.upload_csr(A, dt, dev)
+        hs[name] = spc5.convert(d.rowptr, d.colidx, d.values, A.n, A.m, 2, 4)
+    out = {"workload": "7-point Poisson 96^3 (n=884,736, nnz=6,137,856), b uniform[-1,1] seed 0, tol 1e-10",
+           "format": "beta(2,4)"}
+    for label, inner in (("fp64_cg", None), ("mixed_f32", hs["f32"]), ("mixed_bf16", hs["bf16"])):
+        ts, info = [], None
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            x, info = spc5.cg(hs["f64"], b, A_inner=inner, tol=1e-10, use_graph=True)
+            e1.record()
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        out[label] = {"ms": round(min(ts), 3), "iterations": info["iterations"], "outer": info["outer"],
+                      "rel_residual": info["rel_residual"], "converged": info["converged"]}
+    out["speedup_mixed_f32"] = round(out["fp64_cg"]["ms"] / out["mixed_f32"]["ms"], 3)
+    out["speedup_mixed_bf16"] = round(out["fp64_cg"]["ms"] / out["mixed_bf16"]["ms"], 3)
+    for h in hs.values():
+        h.destroy()
+    return out
+
+
 # ------------------------------------------------------------------ profiling
 
 def run_profile(args):
@@ -288,6 +327,28 @@ def main():
         return run_reference(args)
     if args.profile:
         return run_profile(args)
+    if args.cg_profile:
+        import torch
+
+        from paper_1801_01134_gb300 import inputs, spc5
+
+        spc5.load()
+        dev = torch.device("cuda", 0)
+        N = args.cg_n
+        A = inputs.stencil3d(N, N, N, points=7, normal_values=False)
+        b = torch.from_numpy(inputs.vec_uniform(A.n, seed=0)).to(dev)
+        hs = {}
+        for name, dt in (("f64", torch.float64), ("f32", torch.float32)):
+            d = spc5.upload_csr(A, dt, dev)
+            hs[name] = spc5.convert(d.rowptr, d.colidx, d.values, A.n, A.m, 2, 4)
+        for label, inner in (("fp64_cg", None), ("mixed_f32", hs["f32"])):
+            for rep in range(2):
+                t0 = time.perf_counter()
+                x, info = spc5.cg(hs["f64"], b, A_inner=inner, tol=1e-10, check_every=args.cg_every,
+                                  use_graph=bool(args.cg_graph))
+                dt = time.perf_counter() - t0
+                print(json.dumps({"solver": label, "rep": rep, "ms": round(dt * 1e3, 3), **info}), flush=True)
+        return 0
     import torch
 
     from paper_1801_01134_gb300 import inputs, spc5
@@ -496,6 +557,9 @@ def main():
     for p in prep32:
         p["M"].destroy()
 
+    # ---- precision form: float64 CG vs mixed-precision refinement, 7-point Poisson 96^3
+    cg_res = run_cg_section(dev)
+
     # ---- CPU baseline: the oracle as it stands, on the host cores, bounded sample
     cpu = None
     if rank == 0:
@@ -527,7 +591,7 @@ def main():
         "clocks": cs.summary(), "wall_s_timed": round(wall1 - wall0, 3),
         "csr": {"value": round(csr_value, 2), "unit": "GFLOP/s", "per_matrix": csr_per,
                 "speedup_beta_over_csr": round(value / csr_value, 3)},
-        "per_matrix": per_matrix, "f32": f32,
+        "per_matrix": per_matrix, "f32": f32, "cg": cg_res,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -192,6 +192,50 @@ spc5_status spc5_csr_spmv(int64_t n, int64_t m, int64_t nnz, const int64_t* rowp
  */
 spc5_status spc5_copy(const void* src_d, void* dst_d, int64_t bytes, spc5_stream_t stream);
 
+/* Options of spc5_cg (zero fields select the defaults in brackets). */
+typedef struct {
+  double tol;              /* stop when ||b - A x||_2 <= tol ||b||_2              [1e-10] */
+  int32_t max_iters;       /* CG iterations in total (inner ones when mixed)      [100000] */
+  int32_t max_outer;       /* refinement steps of the mixed solver                [30] */
+  double inner_tol;        /* relative residual reduction of each inner solve     [1e-6] */
+  int32_t inner_max_iters; /* iterations of one inner solve                       [2000] */
+  int32_t check_every;     /* iterations before the first host read of the residual
+                              norm; later reads are placed where the observed
+                              convergence rate predicts the stop (between
+                              check_every/4 and 8 x check_every apart); 1 reads
+                              after every iteration (exact stopping point)       [8] */
+  int32_t use_graph;       /* replay the iteration from a captured CUDA graph     [0: off] */
+  int32_t reserved[5];
+} spc5_cg_opts;
+
+typedef struct {
+  int32_t iterations;  /* CG iterations run (float64 CG) or inner iterations in total (mixed) */
+  int32_t outer;       /* refinement steps (mixed), 0 for float64 CG */
+  int32_t inner_total; /* inner iterations in total (mixed) */
+  int32_t converged;   /* 1 when rel_residual <= tol */
+  double rel_residual; /* ||b - A x||_2 / ||b||_2 of the returned x, recomputed in float64 */
+} spc5_cg_info;
+
+/*
+ * spc5_cg - solve A x = b for symmetric positive definite A by conjugate
+ * gradients (Hestenes & Stiefel), the kind of iterative solver whose many
+ * SpMVs with one matrix the paper targets (Introduction).
+ *   A        SPC5_F64 handle, n == m.
+ *   A_inner  NULL: plain float64 CG on A. Otherwise an SPC5_F32 or SPC5_BF16
+ *            handle of the same matrix: mixed-precision iterative refinement
+ *            - the residual r = b - A x, the update x += d and all norms in
+ *            float64 with A; each correction d solved by CG in float32 with
+ *            A_inner on r / ||r|| to a relative reduction inner_tol.
+ *   b_d, x_d float64 device vectors of n entries; x is overwritten (the
+ *            iteration starts from x = 0).
+ *   info     receives iteration counts and the true relative residual.
+ * Dot products reduce in a fixed order (run-to-run reproducible). Allocates
+ * its workspace (a few vectors); synchronises `stream`. Returns SPC5_OK also
+ * when the tolerance was not reached (see info->converged).
+ */
+spc5_status spc5_cg(spc5_handle A, spc5_handle A_inner, const double* b_d, double* x_d, const spc5_cg_opts* opt,
+                    spc5_cg_info* info, spc5_stream_t stream);
+
 /*
  * spc5_fma_rate - launch an arithmetic-rate probe: 8 CTAs of 256 threads per
  * SM, each thread running 8 independent fused multiply-add chains for `iters`

@@ -164,6 +164,25 @@ spc5_status spc5_copy(const void* src_d, void* dst_d, int64_t bytes, spc5_stream
   return SPC5_OK;
 }
 
+spc5_status spc5_cg(spc5_handle A, spc5_handle A_inner, const double* b_d, double* x_d, const spc5_cg_opts* opt,
+                    spc5_cg_info* info, spc5_stream_t stream) {
+  if (!A || !info) return fail(SPC5_EINVAL, "cg: NULL handle or info");
+  if (A->vt != SPC5_F64) return fail(SPC5_EINVAL, "cg: A must be a float64 handle");
+  if (A->n != A->m) return fail(SPC5_EINVAL, "cg: A must be square");
+  if (A_inner) {
+    if (A_inner->vt != SPC5_F32 && A_inner->vt != SPC5_BF16)
+      return fail(SPC5_EINVAL, "cg: A_inner must be a float32 or bfloat16 handle");
+    if (A_inner->n != A->n || A_inner->m != A->m) return fail(SPC5_EINVAL, "cg: A_inner has another shape");
+  }
+  if (A->n > 0 && (!b_d || !x_d)) return fail(SPC5_EINVAL, "cg: NULL vector");
+  spc5_cg_opts o{};
+  if (opt) o = *opt;
+  if (o.tol < 0 || o.inner_tol < 0 || o.max_iters < 0 || o.max_outer < 0 || o.inner_max_iters < 0 ||
+      o.check_every < 0)
+    return fail(SPC5_EINVAL, "cg: negative option");
+  return cg_impl(A, A_inner, b_d, x_d, &o, info, (cudaStream_t)stream);
+}
+
 spc5_status spc5_fma_rate(spc5_dtype vt, int64_t iters, void* sink_d, int64_t* fmas_out, spc5_stream_t stream) {
   if ((vt != SPC5_F64 && vt != SPC5_F32) || iters < 0 || !sink_d || !fmas_out)
     return fail(SPC5_EINVAL, "fma_rate: bad argument");

@@ -91,6 +91,10 @@ void destroy_matrix(spc5_matrix* h);
 cudaError_t launch_copy(const void* src, void* dst, int64_t bytes, cudaStream_t s);
 cudaError_t launch_fma_rate(spc5_dtype vt, int64_t iters, void* sink, int64_t* fmas, cudaStream_t s);
 
+// conjugate gradients (cg.cu)
+spc5_status cg_impl(const spc5_matrix* A, const spc5_matrix* L, const double* b, double* x, const spc5_cg_opts* o,
+                    spc5_cg_info* info, cudaStream_t s);
+
 int sm_count();
 
 }  // namespace spc5

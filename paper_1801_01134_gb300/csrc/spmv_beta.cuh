@@ -181,42 +181,16 @@ __global__ void __launch_bounds__(256) k_spmv_rows(int64_t n, int64_t I, int32_t
   }
 }
 
-// ------------------------------------------- short intervals, unrolled form
-// Same mapping, arithmetic and summation order as k_spmv_rows; each loop trip
-// decodes the lane's next U nonzeros first (the mask and column index of the
-// following block are already loaded one block ahead), then issues their U
-// value loads and U x loads together, then the U multiply-adds (predicated
-// off past the end of the row). U independent loads per lane are in flight
-// instead of one.
-//
-// With ORDER, lane slot q of the warp takes interval order[q] instead of q
-// (the sorted work order built at conversion; long intervals are not in it).
-template <int R, int C, class T, bool ACCUM, int U, bool ORDER>
-__global__ void __launch_bounds__(256) k_spmv_rows_u(int64_t n, int64_t I, int32_t long_blocks, int64_t long_values,
-                                                     const int32_t* __restrict__ brp, const int32_t* __restrict__ bcol,
-                                                     const uint8_t* __restrict__ bmask,
-                                                     const typename T::V* __restrict__ val,
-                                                     const int64_t* __restrict__ valptr,
-                                                     const typename T::X* __restrict__ x,
-                                                     typename T::X* __restrict__ y,
-                                                     const int32_t* __restrict__ order, int64_t norder) {
+// Sum of one row of a short interval (lane-per-row form): walks blocks
+// [b, bend) of the interval whose values start at vrow, consuming the bits of
+// block row i, U nonzeros decoded per trip (see k_spmv_rows_u).
+template <int R, int C, class T, int U>
+__device__ __forceinline__ typename T::A row_sum_u(int i, int32_t b, int32_t bend,
+                                                   const typename T::V* __restrict__ vrow,
+                                                   const int32_t* __restrict__ bcol, const uint8_t* __restrict__ bmask,
+                                                   const typename T::X* __restrict__ x) {
   constexpr int MB = (R * C + 7) / 8;
-  constexpr int S = kWarp / R;
   using A = typename T::A;
-  const int lane = threadIdx.x & 31;
-  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  int64_t it = warp * S + lane / R;
-  if (ORDER) {
-    if (it >= norder) return;
-    it = __ldg(order + it);
-  }
-  const int i = lane % R;
-  if (it >= I) return;
-  int32_t b = __ldg(brp + it);
-  const int32_t bend = __ldg(brp + it + 1);
-  const int64_t vbase0 = __ldg(valptr + it);
-  if (bend - b > long_blocks || __ldg(valptr + it + 1) - vbase0 > long_values) return;  // the segment path's
-  const typename T::V* __restrict__ vrow = val + vbase0;  // the interval's values
   int32_t vbase = 0;  // offset of block b's first value inside the interval
   uint32_t bits = 0;
   int32_t col0 = 0, vo = 0;
@@ -258,6 +232,44 @@ __global__ void __launch_bounds__(256) k_spmv_rows_u(int64_t n, int64_t I, int32
     for (int u = 0; u < U; ++u)
       if (h[u]) acc = fmadd<T>(v[u], xx[u], acc);
   }
+  return acc;
+}
+
+// ------------------------------------------- short intervals, unrolled form
+// Same mapping, arithmetic and summation order as k_spmv_rows; each loop trip
+// decodes the lane's next U nonzeros first (the mask and column index of the
+// following block are already loaded one block ahead), then issues their U
+// value loads and U x loads together, then the U multiply-adds (predicated
+// off past the end of the row). U independent loads per lane are in flight
+// instead of one.
+//
+// With ORDER, lane slot q of the warp takes interval order[q] instead of q
+// (the sorted work order built at conversion; long intervals are not in it).
+template <int R, int C, class T, bool ACCUM, int U, bool ORDER>
+__global__ void __launch_bounds__(256) k_spmv_rows_u(int64_t n, int64_t I, int32_t long_blocks, int64_t long_values,
+                                                     const int32_t* __restrict__ brp, const int32_t* __restrict__ bcol,
+                                                     const uint8_t* __restrict__ bmask,
+                                                     const typename T::V* __restrict__ val,
+                                                     const int64_t* __restrict__ valptr,
+                                                     const typename T::X* __restrict__ x,
+                                                     typename T::X* __restrict__ y,
+                                                     const int32_t* __restrict__ order, int64_t norder) {
+  constexpr int S = kWarp / R;
+  using A = typename T::A;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int64_t it = warp * S + lane / R;
+  if (ORDER) {
+    if (it >= norder) return;
+    it = __ldg(order + it);
+  }
+  const int i = lane % R;
+  if (it >= I) return;
+  int32_t b = __ldg(brp + it);
+  const int32_t bend = __ldg(brp + it + 1);
+  const int64_t vbase0 = __ldg(valptr + it);
+  if (bend - b > long_blocks || __ldg(valptr + it + 1) - vbase0 > long_values) return;  // the segment path's
+  const typename T::A acc = row_sum_u<R, C, T, U>(i, b, bend, val + vbase0, bcol, bmask, x);
   const int64_t row = it * R + i;
   if (row < n) {
     if (ACCUM)

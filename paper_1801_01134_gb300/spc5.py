@@ -37,6 +37,17 @@ class Opts(ctypes.Structure):
                 ("reserved", ctypes.c_int32 * 5)]
 
 
+class CgOpts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("max_iters", ctypes.c_int32), ("max_outer", ctypes.c_int32),
+                ("inner_tol", ctypes.c_double), ("inner_max_iters", ctypes.c_int32), ("check_every", ctypes.c_int32),
+                ("use_graph", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+
+
+class CgInfo(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("outer", ctypes.c_int32), ("inner_total", ctypes.c_int32),
+                ("converged", ctypes.c_int32), ("rel_residual", ctypes.c_double)]
+
+
 class Arrays(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("m", ctypes.c_int64), ("nnz", ctypes.c_int64), ("nblocks", ctypes.c_int64),
                 ("nintervals", ctypes.c_int64), ("r", ctypes.c_int32), ("c", ctypes.c_int32),
@@ -77,8 +88,9 @@ def load(build_if_missing: bool = False):
     lib.spc5_copy.argtypes = [vp, vp, i64, vp]
     lib.spc5_fma_rate.argtypes = [i32, i64, vp, vp, vp]
     lib.spc5_spmv_noalloc.argtypes = [vp, vp, vp, vp]
+    lib.spc5_cg.argtypes = [vp, vp, vp, vp, ctypes.POINTER(CgOpts), ctypes.POINTER(CgInfo), vp]
     for f in (lib.spc5_convert, lib.spc5_spmv, lib.spc5_spmv_acc, lib.spc5_export, lib.spc5_destroy, lib.spc5_set_variant,
-              lib.spc5_count_blocks, lib.spc5_csr_spmv, lib.spc5_copy, lib.spc5_fma_rate, lib.spc5_spmv_noalloc):
+              lib.spc5_count_blocks, lib.spc5_csr_spmv, lib.spc5_copy, lib.spc5_fma_rate, lib.spc5_spmv_noalloc, lib.spc5_cg):
         f.restype = st
     _lib = lib
     return lib
@@ -239,6 +251,20 @@ def copy(src: torch.Tensor, dst: torch.Tensor, stream=None):
     """dst = src with the library's streaming copy kernel (HBM ceiling)."""
     nbytes = src.numel() * src.element_size()
     copy_raw(_ptr(src), _ptr(dst), nbytes, stream)
+
+
+def cg(A: Matrix, b: torch.Tensor, A_inner: Matrix | None = None, x: torch.Tensor | None = None, tol: float = 1e-10,
+       max_iters: int = 0, max_outer: int = 0, inner_tol: float = 0.0, inner_max_iters: int = 0, check_every: int = 0,
+       use_graph: bool = False, stream=None):
+    """Solve A x = b (float64 CG, or mixed-precision refinement with A_inner). Returns (x, info dict)."""
+    if x is None:
+        x = torch.empty_like(b)
+    opts = CgOpts(tol, max_iters, max_outer, inner_tol, inner_max_iters, check_every, 1 if use_graph else 0)
+    info = CgInfo()
+    _check(load().spc5_cg(A._h, A_inner._h if A_inner is not None else None, _ptr(b), _ptr(x), ctypes.byref(opts),
+                          ctypes.byref(info), _stream_ptr(stream)), "spc5_cg")
+    return x, {"iterations": info.iterations, "outer": info.outer, "inner_total": info.inner_total,
+               "converged": bool(info.converged), "rel_residual": info.rel_residual}
 
 
 def fma_rate(dtype: torch.dtype = torch.float64, iters: int = 4096, reps: int = 5) -> float:
