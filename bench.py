@@ -234,6 +234,58 @@ def run_reference(args):
     return 0
 
 
+# ---------------------------------------------------------------------- SpMM
+
+def run_spmm_section(mats, dev, ks=(1, 4, 8, 16, 32), tiles=(4, 8, 16, 32), reps: int = 5):
+    """float32 Y = A X for k right-hand sides on the stencil and R-MAT matrices,
+    best (shape, k-tile) per k from a small tuning sweep; GFLOP/s = 2 nnz k / t."""
+    import torch
+
+    from paper_1801_01134_gb300 import spc5
+
+    fa = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    fb = torch.empty_like(fa)
+
+    def timed(fn):
+        ts = []
+        for _ in range(reps):
+            spc5.copy(fa, fb)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return min(ts[1:]) if len(ts) > 1 else ts[0]
+
+    out = {}
+    for mt in mats:
+        if not (mt["name"].startswith("stencil") or mt["name"].startswith("rmat")):
+            continue
+        A = mt["A"]
+        d = spc5.upload_csr(A, torch.float32, dev)
+        res = {}
+        Ms = {rc: spc5.convert(d.rowptr, d.colidx, d.values, A.n, A.m, *rc) for rc in ((1, 8), (2, 4), (4, 8))}
+        for k in ks:
+            X = torch.rand(A.m, k, dtype=torch.float32, device=dev)
+            Y = torch.empty(A.n, k, dtype=torch.float32, device=dev)
+            best = None
+            for rc, M in Ms.items():
+                for kt in (tiles if k > 1 else (1,)):
+                    if kt > 1 and kt > 2 * k:
+                        continue
+                    t = timed(lambda: M.spmm(X, Y, ktile=kt))
+                    if best is None or t < best[0]:
+                        best = (t, rc, kt)
+            t, rc, kt = best
+            res[f"k{k}"] = {"ms": round(t, 4), "gflops": round(2.0 * A.nnz * k / t / 1e6, 1),
+                            "shape": f"{rc[0]}x{rc[1]}", "ktile": kt}
+        for M in Ms.values():
+            M.destroy()
+        out[mt["name"]] = res
+    return out
+
+
 # ------------------------------------------------------------------------ CG
 
 def run_cg_section(dev, reps: int = 3):
@@ -559,6 +611,8 @@ def main():
 
     # ---- precision form: float64 CG vs mixed-precision refinement, 7-point Poisson 96^3
     cg_res = run_cg_section(dev)
+    # ---- batched form: multi-RHS SpMM, float32
+    spmm_res = run_spmm_section(mats, dev)
 
     # ---- CPU baseline: the oracle as it stands, on the host cores, bounded sample
     cpu = None
@@ -591,7 +645,7 @@ def main():
         "clocks": cs.summary(), "wall_s_timed": round(wall1 - wall0, 3),
         "csr": {"value": round(csr_value, 2), "unit": "GFLOP/s", "per_matrix": csr_per,
                 "speedup_beta_over_csr": round(value / csr_value, 3)},
-        "per_matrix": per_matrix, "f32": f32, "cg": cg_res,
+        "per_matrix": per_matrix, "f32": f32, "cg": cg_res, "spmm_f32": spmm_res,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

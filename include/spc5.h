@@ -192,6 +192,22 @@ spc5_status spc5_csr_spmv(int64_t n, int64_t m, int64_t nnz, const int64_t* rowp
  */
 spc5_status spc5_copy(const void* src_d, void* dst_d, int64_t bytes, spc5_stream_t stream);
 
+/*
+ * spc5_spmm - Y = A X for k right-hand sides (the paper cites multiplying by
+ * several vectors as a way to reuse the matrix stream, section "Sparse Matrix
+ * Vector Product (SpMV)").
+ *   X_d   m-by-k, row-major, leading dimension ldx >= k (row j at X_d + j*ldx).
+ *   Y_d   n-by-k, row-major, leading dimension ldy >= k; overwritten.
+ *   Element type of X and Y: float64 for SPC5_F64 handles, float32 otherwise.
+ *   k     1..1024; ktile = column tile: 1 or 4 (one lane per row holding that
+ *         many columns), 8, 16 or 32 (that many lanes per row, one column
+ *         each); 0 = choose from k. The grid covers ceil(k / ktile) tiles.
+ * A handle with long intervals keeps n_segments * r * k partial sums; the first
+ * call with a larger k grows that buffer (cudaMalloc, device synchronisation).
+ */
+spc5_status spc5_spmm(spc5_handle h, int k, const void* X_d, int64_t ldx, void* Y_d, int64_t ldy, int ktile,
+                      spc5_stream_t stream);
+
 /* Options of spc5_cg (zero fields select the defaults in brackets). */
 typedef struct {
   double tol;              /* stop when ||b - A x||_2 <= tol ||b||_2              [1e-10] */

@@ -295,3 +295,25 @@ def round_bf16(a: np.ndarray) -> np.ndarray:
     lsb = (u >> 16) & 1
     u = ((u + 0x7FFF + lsb) >> 16) << 16
     return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+# ---------------------------------------------------------------- SpMM
+
+def csr_spmm(A, X: np.ndarray) -> np.ndarray:
+    """Y = A X for a dense m-by-k X, one column at a time with the plain CSR
+    loop (the definition: column j of Y is the SpMV with column j of X)."""
+    X = np.asarray(X, dtype=np.float64)
+    Y = np.empty((A.n, X.shape[1]))
+    for j in range(X.shape[1]):
+        Y[:, j] = csr_spmv(A, np.ascontiguousarray(X[:, j]))
+    return Y
+
+
+def csr_spmm_dot2(A, X: np.ndarray):
+    """Compensated Y = A X (Dot2 per entry) and |A||X| per entry."""
+    X = np.asarray(X, dtype=np.float64)
+    Y = np.empty((A.n, X.shape[1]))
+    S = np.empty_like(Y)
+    for j in range(X.shape[1]):
+        Y[:, j], S[:, j] = csr_spmv_dot2(A, np.ascontiguousarray(X[:, j]))
+    return Y, S

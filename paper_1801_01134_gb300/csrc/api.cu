@@ -164,6 +164,17 @@ spc5_status spc5_copy(const void* src_d, void* dst_d, int64_t bytes, spc5_stream
   return SPC5_OK;
 }
 
+spc5_status spc5_spmm(spc5_handle h, int k, const void* X_d, int64_t ldx, void* Y_d, int64_t ldy, int ktile,
+                      spc5_stream_t stream) {
+  if (!h) return fail(SPC5_EINVAL, "spmm: NULL handle");
+  if (k < 1 || k > 1024) return fail(SPC5_EINVAL, "spmm: k must be in [1, 1024]");
+  if (ldx < k || ldy < k) return fail(SPC5_EINVAL, "spmm: leading dimensions must be >= k");
+  if (!(ktile == 0 || ktile == 1 || ktile == 4 || ktile == 8 || ktile == 16 || ktile == 32))
+    return fail(SPC5_EINVAL, "spmm: ktile must be 0, 1, 4, 8, 16 or 32");
+  if ((h->m > 0 && !X_d) || (h->n > 0 && !Y_d)) return fail(SPC5_EINVAL, "spmm: NULL matrix");
+  return spmm_impl(h, k, X_d, ldx, Y_d, ldy, ktile, (cudaStream_t)stream);
+}
+
 spc5_status spc5_cg(spc5_handle A, spc5_handle A_inner, const double* b_d, double* x_d, const spc5_cg_opts* opt,
                     spc5_cg_info* info, spc5_stream_t stream) {
   if (!A || !info) return fail(SPC5_EINVAL, "cg: NULL handle or info");

@@ -308,6 +308,7 @@ void count_r(int r, int64_t n, int64_t I, int c, const int64_t* rowptr, const in
 void free_matrix(spc5_matrix* h) {
   if (!h) return;
   cudaFree(h->order);
+  cudaFree(h->spmm_scratch);
   cudaFree(h->block_rowptr);
   cudaFree(h->block_colidx);
   cudaFree(h->block_masks);

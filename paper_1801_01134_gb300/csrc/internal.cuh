@@ -50,6 +50,9 @@ struct spc5_matrix {
   int64_t nseg = 0;
   spc5::Segment* segs = nullptr;    // [nseg]
   void* partials = nullptr;         // [nseg * r] accumulation-type scratch
+  // SpMM segment partials, grown on demand
+  void* spmm_scratch = nullptr;
+  size_t spmm_scratch_bytes = 0;
   // work order of the lane-per-row kernel (short intervals only)
   int64_t norder = 0;
   int32_t* order = nullptr;            // [norder] interval indices
@@ -90,6 +93,11 @@ int csr_auto_group(int64_t n, int64_t nnz, spc5_dtype vt);
 void destroy_matrix(spc5_matrix* h);
 cudaError_t launch_copy(const void* src, void* dst, int64_t bytes, cudaStream_t s);
 cudaError_t launch_fma_rate(spc5_dtype vt, int64_t iters, void* sink, int64_t* fmas, cudaStream_t s);
+
+// multi-RHS SpMM (spmm.cu)
+spc5_status spmm_impl(spc5_matrix* h, int k, const void* X, int64_t ldx, void* Y, int64_t ldy, int ktile,
+                      cudaStream_t s);
+int spmm_auto_tile(int k);
 
 // conjugate gradients (cg.cu)
 spc5_status cg_impl(const spc5_matrix* A, const spc5_matrix* L, const double* b, double* x, const spc5_cg_opts* o,

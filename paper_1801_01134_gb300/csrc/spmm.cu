@@ -1,0 +1,349 @@
+// Y = A X for k right-hand sides over the beta(r,c) storage (multi-RHS SpMM).
+//
+// The paper cites multiplication by several vectors as a known way to reuse
+// the matrix stream (section "Sparse Matrix Vector Product (SpMV)"): every
+// decoded nonzero of A is applied to k values of X at once. X is m-by-k and
+// Y n-by-k, both row-major with leading dimensions ldx, ldy >= k.
+//
+// Mappings for the short intervals, chosen by the column tile ktile:
+//   ktile 1 or 4   one lane per row keeps ktile accumulators and, per nonzero,
+//                  reads one matrix value and a ktile-wide slice of an X row;
+//   ktile 8/16/32  ktile lanes per row, one column each: the X values of a
+//                  nonzero are one coalesced load (better for large k).
+// The grid's y dimension covers the column tiles. Long intervals go through
+// warp segments and a fix-up, as in the SpMV, with per-row partials per
+// segment and column.
+//
+// The block shape is a run-time argument here (not a template one): the
+// decode is amortised over k multiply-adds per nonzero, and it keeps the
+// number of kernel instantiations small.
+#include "spmv_beta.cuh"
+
+namespace spc5 {
+namespace {
+
+struct RtMask {
+  uint32_t w[4];
+};
+
+__device__ __forceinline__ RtMask load_mask_rt(const uint8_t* __restrict__ masks, int64_t b, int mb) {
+  RtMask m{{0u, 0u, 0u, 0u}};
+  switch (mb) {
+    case 1: m.w[0] = __ldg(masks + b); break;
+    case 2: m.w[0] = __ldg(reinterpret_cast<const uint16_t*>(masks) + b); break;
+    case 4: m.w[0] = __ldg(reinterpret_cast<const uint32_t*>(masks) + b); break;
+    case 8: {
+      const uint2 v = __ldg(reinterpret_cast<const uint2*>(masks) + b);
+      m.w[0] = v.x;
+      m.w[1] = v.y;
+      break;
+    }
+    default: {
+      const uint4 v = __ldg(reinterpret_cast<const uint4*>(masks) + b);
+      m.w[0] = v.x;
+      m.w[1] = v.y;
+      m.w[2] = v.z;
+      m.w[3] = v.w;
+    }
+  }
+  return m;
+}
+
+__device__ __forceinline__ uint32_t row_bits_rt(const RtMask& m, int i, int c) {
+  const int p = i * c;
+  return (m.w[p >> 5] >> (p & 31)) & ((1u << c) - 1u);
+}
+
+__device__ __forceinline__ int popc_below_rt(const RtMask& m, int i, int c) {
+  const int p = i * c;
+  int cnt = 0;
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    if (q < (p >> 5)) cnt += __popc(m.w[q]);
+  if (p & 31) cnt += __popc(m.w[p >> 5] & ((1u << (p & 31)) - 1u));
+  return cnt;
+}
+
+__device__ __forceinline__ int popc_all_rt(const RtMask& m) {
+  return __popc(m.w[0]) + __popc(m.w[1]) + __popc(m.w[2]) + __popc(m.w[3]);
+}
+
+template <class T, int KT>
+__device__ __forceinline__ void fma_row(typename T::A (&acc)[KT], typename T::A v, const typename T::X* __restrict__ xr,
+                                        int kk) {
+#pragma unroll
+  for (int t = 0; t < KT; ++t)
+    if (t < kk) acc[t] = fma(v, (typename T::A)__ldg(xr + t), acc[t]);
+}
+
+// short intervals: one lane per row, KT columns of X per lane
+template <class T, int KT>
+__global__ void __launch_bounds__(256) k_spmm_rows(int64_t n, int64_t I, int r, int c, int mb, int32_t long_blocks,
+                                                   int64_t long_values, const int32_t* __restrict__ brp,
+                                                   const int32_t* __restrict__ bcol, const uint8_t* __restrict__ bmask,
+                                                   const typename T::V* __restrict__ val,
+                                                   const int64_t* __restrict__ valptr,
+                                                   const typename T::X* __restrict__ X, int64_t ldx,
+                                                   typename T::X* __restrict__ Y, int64_t ldy, int k) {
+  using A = typename T::A;
+  const int lane = threadIdx.x & 31;
+  const int S = kWarp / r;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t it = warp * S + lane / r;
+  const int i = lane % r;
+  const int j0 = blockIdx.y * KT;
+  const int kk = k - j0 < KT ? k - j0 : KT;
+  if (it >= I || lane >= S * r) return;
+  int32_t b = __ldg(brp + it);
+  const int32_t bend = __ldg(brp + it + 1);
+  const int64_t v0 = __ldg(valptr + it);
+  if (bend - b > long_blocks || __ldg(valptr + it + 1) - v0 > long_values) return;  // the segment path's
+  const typename T::V* __restrict__ vrow = val + v0;
+  A acc[KT];
+#pragma unroll
+  for (int t = 0; t < KT; ++t) acc[t] = 0;
+  int32_t vbase = 0;
+  for (; b < bend; ++b) {
+    const RtMask mk = load_mask_rt(bmask, b, mb);
+    uint32_t bits = row_bits_rt(mk, i, c);
+    int32_t vo = vbase + popc_below_rt(mk, i, c);
+    vbase += popc_all_rt(mk);
+    if (!bits) continue;
+    const int64_t col0 = __ldg(bcol + b);
+    while (bits) {
+      const int kb = __ffs(bits) - 1;
+      bits &= bits - 1;
+      fma_row<T, KT>(acc, T::val(vrow, vo++), X + (col0 + kb) * ldx + j0, kk);
+    }
+  }
+  const int64_t row = it * r + i;
+  if (row < n) {
+#pragma unroll
+    for (int t = 0; t < KT; ++t)
+      if (t < kk) Y[row * ldy + j0 + t] = acc[t];
+  }
+}
+
+// short intervals, G lanes per row: lane g of a group takes column j0 + g, so
+// the G values of X a nonzero needs are one coalesced load; every lane of the
+// group decodes the same blocks (the decode is redundant, the loads are not)
+template <class T, int G>
+__global__ void __launch_bounds__(256) k_spmm_rows_cols(int64_t n, int64_t I, int r, int c, int mb,
+                                                        int32_t long_blocks, int64_t long_values,
+                                                        const int32_t* __restrict__ brp,
+                                                        const int32_t* __restrict__ bcol,
+                                                        const uint8_t* __restrict__ bmask,
+                                                        const typename T::V* __restrict__ val,
+                                                        const int64_t* __restrict__ valptr,
+                                                        const typename T::X* __restrict__ X, int64_t ldx,
+                                                        typename T::X* __restrict__ Y, int64_t ldy, int k) {
+  using A = typename T::A;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t row = t / G;  // rows in order: interval it = row / r, block row i = row % r
+  const int g = (int)(t % G);
+  const int j = blockIdx.y * G + g;
+  if (row >= n || j >= k) return;
+  const int64_t it = row / r;
+  const int i = (int)(row % r);
+  int32_t b = __ldg(brp + it);
+  const int32_t bend = __ldg(brp + it + 1);
+  const int64_t v0 = __ldg(valptr + it);
+  if (bend - b > long_blocks || __ldg(valptr + it + 1) - v0 > long_values) return;  // the segment path's
+  const typename T::V* __restrict__ vrow = val + v0;
+  A acc = 0;
+  int32_t vbase = 0;
+  for (; b < bend; ++b) {
+    const RtMask mk = load_mask_rt(bmask, b, mb);
+    uint32_t bits = row_bits_rt(mk, i, c);
+    int32_t vo = vbase + popc_below_rt(mk, i, c);
+    vbase += popc_all_rt(mk);
+    if (!bits) continue;
+    const int64_t col0 = __ldg(bcol + b);
+    while (bits) {
+      const int kb = __ffs(bits) - 1;
+      bits &= bits - 1;
+      acc = fma(T::val(vrow, vo++), (A)__ldg(X + (col0 + kb) * ldx + j), acc);
+    }
+  }
+  Y[row * ldy + j] = acc;
+}
+
+// long intervals: a warp per segment, lane = (block slot, row); KT partials
+// per (segment, row) go to part[(seg * r + i) * k + j]
+template <class T, int KT>
+__global__ void __launch_bounds__(256) k_spmm_segments(int64_t nseg, int r, int c, int mb,
+                                                       const Segment* __restrict__ segs,
+                                                       const int32_t* __restrict__ bcol,
+                                                       const uint8_t* __restrict__ bmask,
+                                                       const typename T::V* __restrict__ val,
+                                                       const typename T::X* __restrict__ X, int64_t ldx,
+                                                       typename T::A* __restrict__ part, int k) {
+  using A = typename T::A;
+  const int lane = threadIdx.x & 31;
+  const int64_t seg = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (seg >= nseg) return;
+  const int S = kWarp / r;
+  const int slot = lane / r, i = lane % r;
+  const bool active = lane < S * r;
+  const int j0 = blockIdx.y * KT;
+  const int kk = k - j0 < KT ? k - j0 : KT;
+  const Segment sg = segs[seg];
+  int64_t vbase = sg.v_begin;
+  A acc[KT];
+#pragma unroll
+  for (int t = 0; t < KT; ++t) acc[t] = 0;
+  for (int32_t b0 = sg.b_begin; b0 < sg.b_end; b0 += S) {
+    const int32_t b = b0 + slot;
+    const bool valid = active && b < sg.b_end;
+    RtMask mk{{0u, 0u, 0u, 0u}};
+    if (valid) mk = load_mask_rt(bmask, b, mb);
+    const int cnt = popc_all_rt(mk);
+    int incl = cnt;
+    for (int d = r; d < kWarp; d <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, d);
+      if (lane >= d) incl += t;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, kWarp - 1);
+    int64_t vo = vbase + (incl - cnt) + (valid ? popc_below_rt(mk, i, c) : 0);
+    uint32_t bits = valid ? row_bits_rt(mk, i, c) : 0u;
+    const int64_t col0 = valid ? __ldg(bcol + b) : 0;
+    while (bits) {
+      const int kb = __ffs(bits) - 1;
+      bits &= bits - 1;
+      fma_row<T, KT>(acc, T::val(val, vo++), X + (col0 + kb) * ldx + j0, kk);
+    }
+    vbase += total;
+  }
+#pragma unroll
+  for (int t = 0; t < KT; ++t)
+    for (int d = kWarp / 2; d >= r; d >>= 1) acc[t] += __shfl_xor_sync(0xffffffffu, acc[t], d);
+  if (lane < r) {
+#pragma unroll
+    for (int t = 0; t < KT; ++t)
+      if (t < kk) part[(seg * r + lane) * (int64_t)k + j0 + t] = acc[t];
+  }
+}
+
+// first segment of each long interval adds its segments' partials in order
+template <class T>
+__global__ void k_spmm_fixup(int64_t n, int64_t nseg, int r, const Segment* __restrict__ segs,
+                             const typename T::A* __restrict__ part, typename T::X* __restrict__ Y, int64_t ldy,
+                             int k) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t seg = t / ((int64_t)r * k);
+  const int rem = (int)(t % ((int64_t)r * k));
+  const int i = rem / k, j = rem % k;
+  if (seg >= nseg) return;
+  const int32_t it = segs[seg].interval;
+  if (seg > 0 && segs[seg - 1].interval == it) return;
+  typename T::A s = 0;
+  for (int64_t q = seg; q < nseg && segs[q].interval == it; ++q) s += part[(q * r + i) * (int64_t)k + j];
+  const int64_t row = (int64_t)it * r + i;
+  if (row < n) Y[row * ldy + j] = s;
+}
+
+template <class T, int KT>
+cudaError_t spmm_launch(const spc5_matrix* h, int k, const void* Xv, int64_t ldx, void* Yv, int64_t ldy, void* part,
+                        cudaStream_t s) {
+  using X = typename T::X;
+  using A = typename T::A;
+  const X* Xm = static_cast<const X*>(Xv);
+  X* Ym = static_cast<X*>(Yv);
+  const typename T::V* val = static_cast<const typename T::V*>(h->values);
+  const int S = kWarp / h->r;
+  const unsigned tiles = (unsigned)((k + KT - 1) / KT);
+  if (h->I > 0) {
+    const int64_t warps = (h->I + S - 1) / S;
+    dim3 grid((unsigned)((warps * kWarp + 255) / 256), tiles);
+    k_spmm_rows<T, KT><<<grid, 256, 0, s>>>(h->n, h->I, h->r, h->c, h->mb, h->long_blocks, h->long_values,
+                                            h->block_rowptr, h->block_colidx, h->block_masks, val, h->valptr, Xm, ldx,
+                                            Ym, ldy, k);
+  }
+  if (h->nseg > 0) {
+    dim3 grid((unsigned)((h->nseg * kWarp + 255) / 256), tiles);
+    k_spmm_segments<T, KT><<<grid, 256, 0, s>>>(h->nseg, h->r, h->c, h->mb, h->segs, h->block_colidx, h->block_masks,
+                                                val, Xm, ldx, static_cast<A*>(part), k);
+    const int64_t nt = h->nseg * h->r * (int64_t)k;
+    k_spmm_fixup<T><<<(unsigned)((nt + 255) / 256), 256, 0, s>>>(h->n, h->nseg, h->r, h->segs,
+                                                                 static_cast<const A*>(part), Ym, ldy, k);
+  }
+  return cudaGetLastError();
+}
+
+// G lanes per row for the short intervals; the long ones keep the segment
+// path with 8 columns per lane
+template <class T, int G>
+cudaError_t spmm_launch_cols(const spc5_matrix* h, int k, const void* Xv, int64_t ldx, void* Yv, int64_t ldy,
+                             void* part, cudaStream_t s) {
+  using X = typename T::X;
+  using A = typename T::A;
+  const X* Xm = static_cast<const X*>(Xv);
+  X* Ym = static_cast<X*>(Yv);
+  const typename T::V* val = static_cast<const typename T::V*>(h->values);
+  if (h->n > 0) {
+    dim3 grid((unsigned)((h->n * G + 255) / 256), (unsigned)((k + G - 1) / G));
+    k_spmm_rows_cols<T, G><<<grid, 256, 0, s>>>(h->n, h->I, h->r, h->c, h->mb, h->long_blocks, h->long_values,
+                                                h->block_rowptr, h->block_colidx, h->block_masks, val, h->valptr, Xm,
+                                                ldx, Ym, ldy, k);
+  }
+  if (h->nseg > 0) {
+    constexpr int KT = 8;
+    dim3 grid((unsigned)((h->nseg * kWarp + 255) / 256), (unsigned)((k + KT - 1) / KT));
+    k_spmm_segments<T, KT><<<grid, 256, 0, s>>>(h->nseg, h->r, h->c, h->mb, h->segs, h->block_colidx, h->block_masks,
+                                                val, Xm, ldx, static_cast<A*>(part), k);
+    const int64_t nt = h->nseg * h->r * (int64_t)k;
+    k_spmm_fixup<T><<<(unsigned)((nt + 255) / 256), 256, 0, s>>>(h->n, h->nseg, h->r, h->segs,
+                                                                 static_cast<const A*>(part), Ym, ldy, k);
+  }
+  return cudaGetLastError();
+}
+
+// ktile 1 or 4: one lane per row holding that many columns; 8, 16, 32: that
+// many lanes per row, one column each
+template <class T>
+cudaError_t spmm_tile(int kt, const spc5_matrix* h, int k, const void* X, int64_t ldx, void* Y, int64_t ldy,
+                      void* part, cudaStream_t s) {
+  switch (kt) {
+    case 1: return spmm_launch<T, 1>(h, k, X, ldx, Y, ldy, part, s);
+    case 4: return spmm_launch<T, 4>(h, k, X, ldx, Y, ldy, part, s);
+    case 8: return spmm_launch_cols<T, 8>(h, k, X, ldx, Y, ldy, part, s);
+    case 16: return spmm_launch_cols<T, 16>(h, k, X, ldx, Y, ldy, part, s);
+    default: return spmm_launch_cols<T, 32>(h, k, X, ldx, Y, ldy, part, s);
+  }
+}
+
+}  // namespace
+
+int spmm_auto_tile(int k) {
+  if (k <= 1) return 1;
+  if (k <= 4) return 4;
+  if (k <= 8) return 8;
+  if (k <= 16) return 16;
+  return 32;
+}
+
+spc5_status spmm_impl(spc5_matrix* h, int k, const void* X, int64_t ldx, void* Y, int64_t ldy, int ktile,
+                      cudaStream_t s) {
+  const int kt = ktile > 0 ? ktile : spmm_auto_tile(k);
+  // segment partials: n_segments * r * k accumulators, kept by the handle and
+  // grown on demand (the growth synchronises the device)
+  const size_t need = (size_t)h->nseg * (size_t)h->r * (size_t)k * (h->vt == SPC5_F64 ? 8 : 4);
+  if (need > h->spmm_scratch_bytes) {
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, need);
+    if (e != cudaSuccess) return cuda_fail(e, "spmm: segment scratch");
+    cudaFree(h->spmm_scratch);  // synchronises: no queued kernel still uses the old buffer
+    h->spmm_scratch = p;
+    h->spmm_scratch_bytes = need;
+  }
+  cudaError_t e;
+  switch (h->vt) {
+    case SPC5_F64: e = spmm_tile<F64>(kt, h, k, X, ldx, Y, ldy, h->spmm_scratch, s); break;
+    case SPC5_F32: e = spmm_tile<F32>(kt, h, k, X, ldx, Y, ldy, h->spmm_scratch, s); break;
+    default: e = spmm_tile<BF16>(kt, h, k, X, ldx, Y, ldy, h->spmm_scratch, s); break;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "spmm launch");
+  return SPC5_OK;
+}
+
+}  // namespace spc5

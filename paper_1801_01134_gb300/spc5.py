@@ -89,8 +89,9 @@ def load(build_if_missing: bool = False):
     lib.spc5_fma_rate.argtypes = [i32, i64, vp, vp, vp]
     lib.spc5_spmv_noalloc.argtypes = [vp, vp, vp, vp]
     lib.spc5_cg.argtypes = [vp, vp, vp, vp, ctypes.POINTER(CgOpts), ctypes.POINTER(CgInfo), vp]
+    lib.spc5_spmm.argtypes = [vp, i32, vp, i64, vp, i64, i32, vp]
     for f in (lib.spc5_convert, lib.spc5_spmv, lib.spc5_spmv_acc, lib.spc5_export, lib.spc5_destroy, lib.spc5_set_variant,
-              lib.spc5_count_blocks, lib.spc5_csr_spmv, lib.spc5_copy, lib.spc5_fma_rate, lib.spc5_spmv_noalloc, lib.spc5_cg):
+              lib.spc5_count_blocks, lib.spc5_csr_spmv, lib.spc5_copy, lib.spc5_fma_rate, lib.spc5_spmv_noalloc, lib.spc5_cg, lib.spc5_spmm):
         f.restype = st
     _lib = lib
     return lib
@@ -162,6 +163,22 @@ class Matrix:
             raise TypeError(f"x and y must be {self.vector_dtype}")
         if x.numel() != self.m or y.numel() != self.n:
             raise ValueError("x must have m entries and y n entries")
+
+    def spmm(self, X: torch.Tensor, Y: torch.Tensor | None = None, ktile: int = 0, stream=None) -> torch.Tensor:
+        """Y = A X for row-major X (m x k) with unit column stride; returns Y (n x k)."""
+        if self._h is None:
+            raise ValueError("matrix was destroyed")
+        if X.dim() != 2 or X.shape[0] != self.m or X.stride(1) != 1 or X.dtype != self.vector_dtype or not X.is_cuda:
+            raise ValueError("X must be a CUDA (m, k) tensor of the vector type with unit column stride")
+        k = X.shape[1]
+        if Y is None:
+            Y = torch.empty(self.n, k, dtype=self.vector_dtype, device=X.device)
+        if Y.shape != (self.n, k) or Y.stride(1) != 1 or Y.dtype != self.vector_dtype:
+            raise ValueError("Y must be (n, k) of the vector type with unit column stride")
+        _check(load().spc5_spmm(self._h, k, X.data_ptr() if X.numel() else None, X.stride(0),
+                                Y.data_ptr() if Y.numel() else None, Y.stride(0), ktile, _stream_ptr(stream)),
+               "spc5_spmm")
+        return Y
 
     def set_variant(self, variant: int, stream=None):
         """Switch the short-interval kernel variant (see spc5_opts.variant)."""

@@ -1,0 +1,77 @@
+"""Multi-RHS SpMM (Y = A X) against the oracle, column by column."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1801_01134_gb300 import inputs, spc5
+
+pytestmark = pytest.mark.gpu
+
+MATS = {
+    "st27_ragged": lambda: inputs.stencil3d(13, 11, 7, points=27, seed=4),
+    "rmat11": lambda: inputs.rmat(11, seed=2),
+    "uniform": lambda: inputs.uniform(3001, 2500, 8, seed=5),
+    "fem": lambda: inputs.block_fem(500, seed=6),
+}
+_cache = {}
+
+
+def get(name):
+    if name not in _cache:
+        _cache[name] = MATS[name]()
+    return _cache[name]
+
+
+@pytest.mark.parametrize("name", list(MATS))
+@pytest.mark.parametrize("r,c", [(1, 8), (2, 4), (4, 16), (8, 8)])
+@pytest.mark.parametrize("k,ktile", [(1, 0), (3, 4), (8, 0), (13, 8), (32, 0), (32, 32), (5, 1)])
+def test_spmm_f64(cuda_device, name, r, c, k, ktile):
+    A = get(name)
+    X = inputs.vec_uniform(A.m * k, seed=k).reshape(A.m, k)
+    Yref, S = oracle.csr_spmm_dot2(A, X)
+    d = spc5.upload_csr(A, torch.float64, "cuda")
+    M = spc5.convert(d.rowptr, d.colidx, d.values, A.n, A.m, r, c, long_blocks=4 if name == "rmat11" else 0)
+    # padded leading dimensions; NaN guard columns must stay untouched
+    ld = k + 3
+    Xd = torch.zeros(A.m, ld, dtype=torch.float64, device="cuda")
+    Xd[:, :k] = torch.from_numpy(X)
+    Yd = torch.full((A.n, ld), float("nan"), dtype=torch.float64, device="cuda")
+    M.spmm(Xd[:, :k], Yd[:, :k], ktile=ktile)
+    Y = Yd.cpu().numpy()
+    assert np.all(np.abs(Y[:, :k] - Yref) <= 1e-13 * S), np.abs(Y[:, :k] - Yref).max()
+    assert np.isnan(Y[:, k:]).all()
+    M.destroy()
+
+
+@pytest.mark.parametrize("name", ["st27_ragged", "rmat11"])
+@pytest.mark.parametrize("k", [4, 16, 32])
+def test_spmm_f32_and_column_equals_spmv(cuda_device, name, k):
+    A = get(name)
+    Ar = inputs.CSR(A.n, A.m, A.rowptr, A.colidx, oracle.round_f32(A.values))
+    X = oracle.round_f32(inputs.vec_uniform(A.m * k, seed=k)).reshape(A.m, k)
+    Yref, S = oracle.csr_spmm_dot2(Ar, X)
+    d = spc5.upload_csr(Ar, torch.float32, "cuda")
+    M = spc5.convert(d.rowptr, d.colidx, d.values, A.n, A.m, 2, 8)
+    Xd = torch.from_numpy(X).float().cuda()
+    Y = M.spmm(Xd).double().cpu().numpy()
+    L = np.diff(A.rowptr).astype(np.float64)[:, None]
+    u = 2.0**-24
+    assert np.all(np.abs(Y - Yref) <= (L + 1) * u / (1 - (L + 1) * u) * S + 1e-45)
+    # column j of Y is the SpMV with column j of X
+    for j in (0, k - 1):
+        yj = M.spmv(Xd[:, j].contiguous()).double().cpu().numpy()
+        assert np.all(np.abs(Y[:, j] - yj) <= 2 * (L[:, 0] + 1) * u * S[:, j] + 1e-45)
+    M.destroy()
+
+
+def test_spmm_rejects_bad_arguments(cuda_device):
+    A = get("uniform")
+    d = spc5.upload_csr(A, torch.float32, "cuda")
+    M = spc5.convert(d.rowptr, d.colidx, d.values, A.n, A.m, 1, 8)
+    X = torch.zeros(A.m, 4, dtype=torch.float32, device="cuda")
+    with pytest.raises(spc5.Spc5Error):
+        M.spmm(X, ktile=3)
+    with pytest.raises(ValueError):
+        M.spmm(X.double())
+    M.destroy()

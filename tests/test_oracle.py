@@ -368,3 +368,24 @@ def test_dyadic_inputs_make_laplacian_spmv_exact():
     yd, _ = oracle.csr_spmv_dot2(A, x)
     assert np.array_equal(y, yd)
     assert np.array_equal(y.astype(np.float32).astype(np.float64), y)  # exact in float32 too
+
+
+# ------------------------------------------------------------------ SpMM
+
+def test_spmm_oracle_against_dense_matmul_and_linearity():
+    for seed, (n, m, k) in enumerate([(30, 40, 1), (17, 9, 4), (64, 64, 32)]):
+        A = tiny_random(n, m, 0.2, 50 + seed)
+        X = inputs.vec_uniform(m * k, seed=seed).reshape(m, k)
+        D = A.to_dense()
+        Y = oracle.csr_spmm(A, X)
+        ref = np.array([[sum(D[i, q] * X[q, j] for q in range(m)) for j in range(k)] for i in range(n)])
+        assert np.allclose(Y, ref, rtol=0, atol=1e-13 * (np.abs(D) @ np.abs(X)).max() + 1e-300)
+        Yd, S = oracle.csr_spmm_dot2(A, X)
+        assert np.all(np.abs(Yd - ref) <= 1e-14 * S + 1e-300)
+        # column j equals the SpMV with column j
+        assert np.array_equal(Y[:, 0], oracle.csr_spmv(A, np.ascontiguousarray(X[:, 0])))
+        # linearity in X with exactly representable data
+        X1 = inputs.vec_dyadic(m * k, seed=seed, bits=10).reshape(m, k)
+        X2 = inputs.vec_dyadic(m * k, seed=seed + 7, bits=10).reshape(m, k)
+        Ad = inputs.CSR(A.n, A.m, A.rowptr, A.colidx, inputs.vec_dyadic(A.nnz, seed=3, bits=10))
+        assert np.array_equal(oracle.csr_spmm(Ad, X1 + X2), oracle.csr_spmm(Ad, X1) + oracle.csr_spmm(Ad, X2))
