@@ -1,0 +1,79 @@
+"""Pins of the selection oracle: features on matrices with known block
+counts, exact polynomial recovery, and the MLP gradient against central
+finite differences."""
+import numpy as np
+
+import oracle
+from oracle import select as osel
+from paper_1801_01134_gb300 import inputs
+
+
+def test_features_known_matrices():
+    # dense 64 x 64: every block full, Avg = r*c; rows all of length 64
+    D = inputs.CSR.from_dense(np.ones((64, 64)))
+    f = osel.features(D)
+    assert list(f[:12]) == [r * c for r, c in oracle.SHAPES]
+    assert f[12] == 64 and f[13] == 0 and f[14] == 64 and abs(f[15] - np.log10(64)) < 1e-15
+    # identity: one value per block for every shape with r <= c
+    I = inputs.CSR.from_dense(np.eye(64))
+    f = osel.features(I)
+    for q, (r, c) in enumerate(oracle.SHAPES):
+        assert f[q] == (r if r <= c else c)
+    # Laplacian 128x128, beta(1,8): 81408 / 48896 (hand-derived count)
+    L = inputs.laplacian2d(128, 128)
+    f = osel.features(L)
+    assert f[oracle.SHAPES.index((1, 8))] == 81408 / 48896
+    lens = np.diff(L.rowptr)
+    assert f[12] == lens.mean() and f[14] == 5
+
+
+def test_poly_fit_recovers_exact_polynomials():
+    rng = np.random.default_rng(0)
+    for deg in (1, 2, 3, 4):
+        c = rng.standard_normal(deg + 1)
+        x = np.linspace(1.0, 32.0, 40)
+        y = np.polynomial.polynomial.polyval(x, c)
+        got = osel.poly_fit(x, y, deg)
+        assert np.allclose(got, c, rtol=1e-8, atol=1e-8)
+        assert np.allclose(osel.poly_eval(got, x), y, rtol=1e-10, atol=1e-8)
+
+
+def test_mlp_gradient_matches_central_differences():
+    rng = np.random.default_rng(1)
+    theta = rng.standard_normal(osel.mlp_nparams()) * 0.3
+    X = rng.standard_normal((7, osel.NFEAT))
+    Y = rng.standard_normal((7, osel.NFMT))
+    M = (rng.random((7, osel.NFMT)) > 0.2).astype(float)
+    g = osel.mlp_grad(theta, X, Y, M)
+    h = 1e-6
+    idx = rng.choice(theta.size, 200, replace=False)
+    for i in idx:
+        e = np.zeros_like(theta)
+        e[i] = h
+        fd = (osel.mlp_loss(theta + e, X, Y, M) - osel.mlp_loss(theta - e, X, Y, M)) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(fd)), (i, fd, g[i])
+
+
+def test_mlp_forward_is_the_layer_composition():
+    rng = np.random.default_rng(2)
+    theta = rng.standard_normal(osel.mlp_nparams())
+    X = rng.standard_normal((3, osel.NFEAT))
+    W1, b1, W2, b2, W3, b3 = osel.mlp_unpack(theta)
+    out, _ = osel.mlp_forward(theta, X)
+    for s in range(3):
+        h1 = [max(0.0, sum(W1[j, q] * X[s, q] for q in range(16)) + b1[j]) for j in range(64)]
+        h2 = [max(0.0, sum(W2[j, q] * h1[q] for q in range(64)) + b2[j]) for j in range(64)]
+        o = [sum(W3[j, q] * h2[q] for q in range(64)) + b3[j] for j in range(12)]
+        assert np.allclose(out[s], o, rtol=1e-12, atol=1e-12)
+
+
+def test_adam_minimises_a_quadratic_and_regret_definition():
+    theta = np.array([3.0, -2.0])
+    m = v = np.zeros(2)
+    for t in range(1, 2001):
+        theta, m, v = osel.adam_step(theta, 2 * theta, m, v, t, 0.05)
+    assert np.all(np.abs(theta) < 1e-3)
+    times = np.array([[1.0, 2.0, 4.0], [3.0, 1.5, 6.0]])
+    assert np.allclose(osel.regret(times, np.array([0, 0])), [0.0, 1.0])
+    c = osel.centred_log_times(times)
+    assert np.allclose(c.sum(axis=1), 0.0)
