@@ -286,6 +286,97 @@ def run_spmm_section(mats, dev, ks=(1, 4, 8, 16, 32), tiles=(4, 8, 16, 32), reps
     return out
 
 
+# ------------------------------------------------------------------ selector
+
+def run_selector_section(prep, dev):
+    """Shapes the committed MLP and polynomial models pick for the bench
+    matrices, with their regret against the exhaustive sweep of the run, and
+    the models' held-out regret from the corpus they were trained on."""
+    import numpy as np
+
+    from paper_1801_01134_gb300 import spc5
+
+    path = os.path.join(ROOT, "paper_1801_01134_gb300", "models", "selector_gb300.npz")
+    if not os.path.exists(path):
+        return None
+    z = np.load(path)
+    import torch
+
+    P = torch.from_numpy(z["mlp_params"]).to(dev)
+    out = {"model": "paper_1801_01134_gb300/models/selector_gb300.npz",
+           "held_out": {k: json.loads(str(z["result"]))[k] for k in ("regret_mlp", "regret_poly", "regret_fixed")}}
+    per = {}
+    for p in prep:
+        d = p["d"]
+        sweep = p["sweep_gflops"]
+        best = max(sweep.values())
+        rm, cm, _ = spc5.select(d, spc5.SELECT_MLP, mlp_params=P, feat_mean=z["feat_mean"], feat_scale=z["feat_scale"])
+        rp, cp, _ = spc5.select(d, spc5.SELECT_POLY, poly_coef=z["poly_coef"])
+        per[p["name"]] = {"best": f"{p['r']}x{p['c']}", "mlp": f"{rm}x{cm}",
+                          "mlp_regret": round(best / sweep[f"{rm}x{cm}"] - 1.0, 4),
+                          "poly": f"{rp}x{cp}", "poly_regret": round(best / sweep[f"{rp}x{cp}"] - 1.0, 4)}
+    out["bench_matrices"] = per
+    return out
+
+
+# ------------------------------------------------------------------- batched
+
+def run_batch_section(dev, count: int = 256, reps: int = 20):
+    """256 uneven float32 matrices (n lognormal in [1k, 64k], 3..60 per row,
+    stencil / banded / uniform, seed 2), each in the shape exhaustive timing
+    picks for it: one graph-replayed persistent launch vs one SpMV launch per
+    matrix. GFLOP/s = sum(2 nnz) / t."""
+    import torch
+
+    from paper_1801_01134_gb300 import inputs, spc5
+
+    mats, keep, xs, ys, shapes = [], [], [], [], {}
+    flops = 0.0
+    t_tune = time.time()
+    for j in range(count):
+        A = inputs.batch_matrix(j, seed=2)
+        d = spc5.upload_csr(A, torch.float32, dev)
+        r, c, _ = spc5.select(d, spc5.SELECT_EXHAUSTIVE)
+        shapes[f"{r}x{c}"] = shapes.get(f"{r}x{c}", 0) + 1
+        mats.append(spc5.convert(d.rowptr, d.colidx, d.values, A.n, A.m, r, c))
+        keep.append(d)
+        xs.append(torch.rand(A.m, dtype=torch.float32, device=dev))
+        ys.append(torch.empty(A.n, dtype=torch.float32, device=dev))
+        flops += 2.0 * A.nnz
+    t_tune = time.time() - t_tune
+    B = spc5.Batch(mats, xs, ys)
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        e1.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    t_graph = timed(lambda: B.run(graph=True))
+    t_direct = timed(lambda: B.run(graph=False))
+
+    def each():
+        for M, x, y in zip(mats, xs, ys):
+            M.spmv(x, y)
+
+    t_each = timed(each)
+    B.destroy()
+    for M in mats:
+        M.destroy()
+    return {"workload": f"{count} float32 matrices, n lognormal in [1k, 64k], 3..60 per row, seed 2",
+            "nnz_total": int(flops / 2), "shapes": shapes, "tune_s": round(t_tune, 2),
+            "graph_ms": round(t_graph, 4), "gflops_graph": round(flops / t_graph / 1e6, 1),
+            "direct_ms": round(t_direct, 4), "gflops_direct": round(flops / t_direct / 1e6, 1),
+            "per_matrix_launches_ms": round(t_each, 4), "gflops_per_matrix_launches": round(flops / t_each / 1e6, 1),
+            "speedup_vs_per_matrix": round(t_each / t_graph, 3)}
+
+
 # ------------------------------------------------------------------------ CG
 
 def run_cg_section(dev, reps: int = 3):
@@ -590,6 +681,9 @@ def main():
     e2e_ms = max_over_ranks(e0.elapsed_time(e1), ws, dev)
     e2e_value = flops_step * args.steps * ws / (e2e_ms * 1e-3) / 1e9
 
+    # ---- learned selector vs the paper-style polynomial on the bench matrices
+    sel_res = run_selector_section(prep64, dev)
+
     # ---- float32 storage form
     for p in prep64:
         p["M"].destroy()
@@ -611,8 +705,9 @@ def main():
 
     # ---- precision form: float64 CG vs mixed-precision refinement, 7-point Poisson 96^3
     cg_res = run_cg_section(dev)
-    # ---- batched form: multi-RHS SpMM, float32
+    # ---- batched form: multi-RHS SpMM, float32; many uneven matrices in one launch
     spmm_res = run_spmm_section(mats, dev)
+    batch_res = run_batch_section(dev)
 
     # ---- CPU baseline: the oracle as it stands, on the host cores, bounded sample
     cpu = None
@@ -645,7 +740,7 @@ def main():
         "clocks": cs.summary(), "wall_s_timed": round(wall1 - wall0, 3),
         "csr": {"value": round(csr_value, 2), "unit": "GFLOP/s", "per_matrix": csr_per,
                 "speedup_beta_over_csr": round(value / csr_value, 3)},
-        "per_matrix": per_matrix, "f32": f32, "cg": cg_res, "spmm_f32": spmm_res,
+        "per_matrix": per_matrix, "f32": f32, "cg": cg_res, "spmm_f32": spmm_res, "batch_f32": batch_res, "selector": sel_res,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

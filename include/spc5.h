@@ -208,6 +208,32 @@ spc5_status spc5_copy(const void* src_d, void* dst_d, int64_t bytes, spc5_stream
 spc5_status spc5_spmm(spc5_handle h, int k, const void* X_d, int64_t ldx, void* Y_d, int64_t ldy, int ktile,
                       spc5_stream_t stream);
 
+/* ----------------------------------------------------------------- batches */
+typedef struct spc5_batch_s* spc5_batch; /* opaque batched product */
+
+/*
+ * spc5_batch_create - prepare y_j = A_j x_j for `count` handles of one value
+ * type (each with its own block shape) as one persistent launch: the short
+ * intervals of all matrices are cut into work items of 32/r intervals (the
+ * long ones into their warp segments) that persistent warps take from a
+ * shared counter, so uneven matrices balance themselves. x_d[j] / y_d[j]:
+ * device vectors of matrix j (fixed for the batch's lifetime; refill them in
+ * place between products). The counter reset, the kernel and the segment
+ * fix-up are captured into a CUDA graph here. The handles must outlive the
+ * batch. Synchronises the device.
+ */
+spc5_status spc5_batch_create(const spc5_handle* mats, const void* const* x_d, void* const* y_d, int count,
+                              spc5_batch* out);
+
+/* spc5_batch_spmv - all products of the batch: one graph launch on `stream`. */
+spc5_status spc5_batch_spmv(spc5_batch b, spc5_stream_t stream);
+
+/* spc5_batch_spmv_direct - the same products launched without the graph. */
+spc5_status spc5_batch_spmv_direct(spc5_batch b, spc5_stream_t stream);
+
+/* spc5_batch_destroy - free the batch (not its handles); NULL is allowed. */
+spc5_status spc5_batch_destroy(spc5_batch b);
+
 /* Options of spc5_cg (zero fields select the defaults in brackets). */
 typedef struct {
   double tol;              /* stop when ||b - A x||_2 <= tol ||b||_2              [1e-10] */
@@ -251,6 +277,95 @@ typedef struct {
  */
 spc5_status spc5_cg(spc5_handle A, spc5_handle A_inner, const double* b_d, double* x_d, const spc5_cg_opts* opt,
                     spc5_cg_info* info, spc5_stream_t stream);
+
+/* ------------------------------------------------------------- selection */
+#define SPC5_NFEATURES 16
+#define SPC5_NFORMATS 12 /* r in {1,2,4,8} outer, c in {4,8,16} inner */
+
+/*
+ * spc5_features - the selection features of a CSR matrix, without converting
+ * it (the paper's predictor uses Avg(r,c) = N_nnz / N_blocks(r,c), which is
+ * cheap to obtain, section "Performance polynomial interpolation"; its
+ * conclusion asks for more inputs): features_out[0..11] = Avg(r,c) for the
+ * twelve shapes; [12], [13], [14] = mean, standard deviation and maximum of
+ * the row lengths; [15] = log10(n). Host output (16 doubles); synchronises
+ * `stream`. The CSR must be valid (not re-checked).
+ */
+spc5_status spc5_features(int64_t n, int64_t m, int64_t nnz, const int64_t* rowptr_d, const int32_t* colidx_d,
+                          double* features_out, spc5_stream_t stream);
+
+/*
+ * spc5_time_formats - the timing recorder: converts the CSR to each of the
+ * twelve shapes and times `reps` SpMVs of each (after one untimed product),
+ * writing the median milliseconds to ms_out[12] (host). x_d / y_d: work
+ * vectors of the vector type (m and n entries). Synchronises `stream`.
+ */
+spc5_status spc5_time_formats(int64_t n, int64_t m, int64_t nnz, const int64_t* rowptr_d, const int32_t* colidx_d,
+                              const void* values_d, spc5_dtype vt, const void* x_d, void* y_d, int reps,
+                              float* ms_out, spc5_stream_t stream);
+
+/*
+ * Format-scoring MLP: 16 -> 64 -> 64 -> 12, ReLU, float32, parameters flat in
+ * the order W1[64][16], b1[64], W2[64][64], b2[64], W3[12][64], b3[12]
+ * (spc5_mlp_nparams() floats, device memory). Inputs: x_q = (log1p(f_q) -
+ * mean_q) / scale_q of the features f. Output: a score per format (the
+ * trainer fits centred log times: lower is faster).
+ */
+int spc5_mlp_nparams(void);
+
+/*
+ * spc5_mlp_train - minibatch Adam (beta1 0.9, beta2 0.999, eps 1e-8) on the
+ * masked mean squared error sum(M (out - Y)^2) / sum(M). X_d: N x 16 inputs,
+ * Y_d / M_d: N x 12 targets and 0/1 mask (device, row-major). batch 1..32;
+ * samples are shuffled per epoch with `seed`. One fused kernel per step.
+ * loss_history (host, `epochs` floats, nullable) receives the mean loss of
+ * each epoch. Synchronises `stream`.
+ */
+spc5_status spc5_mlp_train(float* params_d, const float* X_d, const float* Y_d, const float* M_d, int N, int epochs,
+                           int batch, float lr, uint64_t seed, float* loss_history, spc5_stream_t stream);
+
+/*
+ * spc5_mlp_grad - loss (host) and gradient (device, spc5_mlp_nparams()
+ * floats) of the first B (1..32) samples, parameters unchanged.
+ */
+spc5_status spc5_mlp_grad(const float* params_d, const float* X_d, const float* Y_d, const float* M_d, int B,
+                          float* loss_out, float* grad_d, spc5_stream_t stream);
+
+/* spc5_mlp_infer - scores (N x 12, device) of N input rows (N x 16, device). */
+spc5_status spc5_mlp_infer(const float* params_d, const float* X_d, int N, float* out_d, spc5_stream_t stream);
+
+/*
+ * spc5_poly_fit - the paper's per-kernel polynomial interpolation: for each
+ * format f, least-squares coefficients c_0..c_d of perf[:, f] ~ sum_j c_j
+ * avg[:, f]^j (Householder QR). avg, perf: N x 12 host arrays; coef_out:
+ * 12 x (degree + 1) host array. 0 <= degree <= 6, N > degree.
+ */
+spc5_status spc5_poly_fit(const double* avg, const double* perf, int N, int degree, double* coef_out);
+
+typedef enum { SPC5_SELECT_EXHAUSTIVE = 0, SPC5_SELECT_POLY = 1, SPC5_SELECT_MLP = 2 } spc5_select_method;
+
+typedef struct {
+  int32_t poly_degree;      /* POLY: degree of the fitted polynomials */
+  const double* poly_coef;  /* POLY: host, 12 x (degree + 1), from spc5_poly_fit on GFLOP/s */
+  const float* mlp_params_d;/* MLP: device parameters */
+  float feat_mean[SPC5_NFEATURES];  /* MLP input standardisation (see above) */
+  float feat_scale[SPC5_NFEATURES];
+} spc5_selector;
+
+/*
+ * spc5_select - pick a block shape for a CSR matrix before converting it
+ * (section "Performance prediction and optimal kernel selection").
+ *   EXHAUSTIVE  time every shape (spc5_time_formats) and take the fastest;
+ *               needs values_d and vt; model unused.
+ *   POLY        highest polynomial estimate of GFLOP/s at the matrix's Avg(r,c).
+ *   MLP         lowest MLP score.
+ * r_out, c_out: the choice; score_out (host, 12 floats, nullable): the
+ * per-format times (EXHAUSTIVE, ms), estimates (POLY) or scores (MLP).
+ * Synchronises `stream`.
+ */
+spc5_status spc5_select(int64_t n, int64_t m, int64_t nnz, const int64_t* rowptr_d, const int32_t* colidx_d,
+                        const void* values_d, spc5_dtype vt, int method, const spc5_selector* model, int* r_out,
+                        int* c_out, float* score_out, spc5_stream_t stream);
 
 /*
  * spc5_fma_rate - launch an arithmetic-rate probe: 8 CTAs of 256 threads per

@@ -1,8 +1,11 @@
 // C ABI of libspc5 (declared in include/spc5.h): argument checks on the host,
 // error reporting, and dispatch to the kernels of the other translation units.
+#include <algorithm>
 #include <climits>
+#include <cmath>
 #include <cstdio>
 #include <string>
+#include <vector>
 
 #include "internal.cuh"
 
@@ -192,6 +195,148 @@ spc5_status spc5_cg(spc5_handle A, spc5_handle A_inner, const double* b_d, doubl
       o.check_every < 0)
     return fail(SPC5_EINVAL, "cg: negative option");
   return cg_impl(A, A_inner, b_d, x_d, &o, info, (cudaStream_t)stream);
+}
+
+spc5_status spc5_features(int64_t n, int64_t m, int64_t nnz, const int64_t* rowptr_d, const int32_t* colidx_d,
+                          double* features_out, spc5_stream_t stream) {
+  if (!features_out) return fail(SPC5_EINVAL, "features: NULL output");
+  spc5_status st = check_csr_args(n, m, nnz, rowptr_d, colidx_d, (const void*)colidx_d);
+  if (st != SPC5_OK) return st;
+  return features_impl(n, nnz, rowptr_d, colidx_d, features_out, (cudaStream_t)stream);
+}
+
+spc5_status spc5_time_formats(int64_t n, int64_t m, int64_t nnz, const int64_t* rowptr_d, const int32_t* colidx_d,
+                              const void* values_d, spc5_dtype vt, const void* x_d, void* y_d, int reps,
+                              float* ms_out, spc5_stream_t stream) {
+  if (!ms_out || reps < 1) return fail(SPC5_EINVAL, "time_formats: NULL output or reps < 1");
+  if ((m > 0 && !x_d) || (n > 0 && !y_d)) return fail(SPC5_EINVAL, "time_formats: NULL vector");
+  const cudaStream_t s = (cudaStream_t)stream;
+  const int rs[4] = {1, 2, 4, 8}, cs[3] = {4, 8, 16};
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e != cudaSuccess) return cuda_fail(e, "time_formats: events");
+  spc5_status st = SPC5_OK;
+  for (int q = 0; q < 12 && st == SPC5_OK; ++q) {
+    spc5_handle h = nullptr;
+    st = spc5_convert(n, m, nnz, rowptr_d, colidx_d, values_d, vt, rs[q / 3], cs[q % 3], nullptr, stream, &h);
+    if (st != SPC5_OK) break;
+    std::vector<float> t((size_t)reps);
+    st = spc5_spmv(h, x_d, y_d, stream);  // untimed
+    for (int k = 0; k < reps && st == SPC5_OK; ++k) {
+      e = cudaEventRecord(e0, s);
+      if (e == cudaSuccess) st = spc5_spmv(h, x_d, y_d, stream);
+      if (e == cudaSuccess && st == SPC5_OK) e = cudaEventRecord(e1, s);
+      if (e == cudaSuccess && st == SPC5_OK) e = cudaEventSynchronize(e1);
+      if (e == cudaSuccess && st == SPC5_OK) e = cudaEventElapsedTime(&t[(size_t)k], e0, e1);
+      if (e != cudaSuccess) st = cuda_fail(e, "time_formats: timing");
+    }
+    spc5_destroy(h);
+    if (st == SPC5_OK) {
+      std::sort(t.begin(), t.end());
+      ms_out[q] = t[(size_t)reps / 2];
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return st;
+}
+
+int spc5_mlp_nparams(void) { return mlp_param_count(); }
+
+spc5_status spc5_mlp_train(float* params_d, const float* X_d, const float* Y_d, const float* M_d, int N, int epochs,
+                           int batch, float lr, uint64_t seed, float* loss_history, spc5_stream_t stream) {
+  if (!params_d || N < 1 || epochs < 0 || !X_d || !Y_d || !M_d || !(lr >= 0.f))
+    return fail(SPC5_EINVAL, "mlp_train: bad argument");
+  return mlp_train_impl(params_d, X_d, Y_d, M_d, N, epochs, batch, lr, seed, loss_history, (cudaStream_t)stream);
+}
+
+spc5_status spc5_mlp_grad(const float* params_d, const float* X_d, const float* Y_d, const float* M_d, int B,
+                          float* loss_out, float* grad_d, spc5_stream_t stream) {
+  if (!params_d || !X_d || !Y_d || !M_d || !loss_out || !grad_d) return fail(SPC5_EINVAL, "mlp_grad: NULL argument");
+  return mlp_grad_impl(params_d, X_d, Y_d, M_d, B, loss_out, grad_d, (cudaStream_t)stream);
+}
+
+spc5_status spc5_mlp_infer(const float* params_d, const float* X_d, int N, float* out_d, spc5_stream_t stream) {
+  if (!params_d || N < 0 || (N > 0 && (!X_d || !out_d))) return fail(SPC5_EINVAL, "mlp_infer: bad argument");
+  return mlp_infer_impl(params_d, X_d, N, out_d, (cudaStream_t)stream);
+}
+
+spc5_status spc5_poly_fit(const double* avg, const double* perf, int N, int degree, double* coef_out) {
+  if (!avg || !perf || !coef_out) return fail(SPC5_EINVAL, "poly_fit: NULL argument");
+  return poly_fit_impl(avg, perf, N, degree, coef_out);
+}
+
+spc5_status spc5_select(int64_t n, int64_t m, int64_t nnz, const int64_t* rowptr_d, const int32_t* colidx_d,
+                        const void* values_d, spc5_dtype vt, int method, const spc5_selector* model, int* r_out,
+                        int* c_out, float* score_out, spc5_stream_t stream) {
+  if (!r_out || !c_out) return fail(SPC5_EINVAL, "select: NULL output");
+  const int rs[4] = {1, 2, 4, 8}, cs[3] = {4, 8, 16};
+  const cudaStream_t s = (cudaStream_t)stream;
+  float score[12] = {0};
+  int best = 0;
+  if (method == SPC5_SELECT_EXHAUSTIVE) {
+    spc5_status st = check_csr_args(n, m, nnz, rowptr_d, colidx_d, values_d);
+    if (st != SPC5_OK) return st;
+    const size_t xs = vt == SPC5_F64 ? 8 : 4;
+    void *x = nullptr, *y = nullptr;
+    cudaError_t e = cudaMalloc(&x, xs * (size_t)(m > 0 ? m : 1));
+    if (e == cudaSuccess) e = cudaMalloc(&y, xs * (size_t)(n > 0 ? n : 1));
+    if (e == cudaSuccess) e = cudaMemsetAsync(x, 0, xs * (size_t)(m > 0 ? m : 1), s);
+    if (e != cudaSuccess) {
+      cudaFree(x);
+      cudaFree(y);
+      return cuda_fail(e, "select: work vectors");
+    }
+    st = spc5_time_formats(n, m, nnz, rowptr_d, colidx_d, values_d, vt, x, y, 5, score, stream);
+    cudaFree(x);
+    cudaFree(y);
+    if (st != SPC5_OK) return st;
+    for (int q = 1; q < 12; ++q)
+      if (score[q] < score[best]) best = q;
+  } else if (method == SPC5_SELECT_POLY || method == SPC5_SELECT_MLP) {
+    if (!model) return fail(SPC5_EINVAL, "select: NULL model");
+    double f[16];
+    spc5_status st = spc5_features(n, m, nnz, rowptr_d, colidx_d, f, stream);
+    if (st != SPC5_OK) return st;
+    if (method == SPC5_SELECT_POLY) {
+      if (!model->poly_coef || model->poly_degree < 0 || model->poly_degree > 6)
+        return fail(SPC5_EINVAL, "select: no polynomial model");
+      double est[12];
+      best = poly_select_impl(model->poly_coef, model->poly_degree, f, est);
+      for (int q = 0; q < 12; ++q) score[q] = (float)est[q];
+    } else {
+      if (!model->mlp_params_d) return fail(SPC5_EINVAL, "select: no MLP parameters");
+      float xin[16];
+      for (int q = 0; q < 16; ++q)
+        xin[q] = (float)((std::log1p(f[q]) - (double)model->feat_mean[q]) /
+                         (double)(model->feat_scale[q] != 0.f ? model->feat_scale[q] : 1.f));
+      void* buf = nullptr;
+      cudaError_t e = cudaMalloc(&buf, sizeof(float) * 28);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(buf, xin, sizeof(xin), cudaMemcpyHostToDevice, s);
+      if (e != cudaSuccess) {
+        cudaFree(buf);
+        return cuda_fail(e, "select: MLP input");
+      }
+      st = mlp_infer_impl(model->mlp_params_d, (const float*)buf, 1, (float*)buf + 16, s);
+      if (st == SPC5_OK) {
+        e = cudaMemcpyAsync(score, (float*)buf + 16, sizeof(float) * 12, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) st = cuda_fail(e, "select: MLP output");
+      }
+      cudaFree(buf);
+      if (st != SPC5_OK) return st;
+      for (int q = 1; q < 12; ++q)
+        if (score[q] < score[best]) best = q;
+    }
+  } else {
+    return fail(SPC5_EINVAL, "select: unknown method");
+  }
+  *r_out = rs[best / 3];
+  *c_out = cs[best % 3];
+  if (score_out)
+    for (int q = 0; q < 12; ++q) score_out[q] = score[q];
+  return SPC5_OK;
 }
 
 spc5_status spc5_fma_rate(spc5_dtype vt, int64_t iters, void* sink_d, int64_t* fmas_out, spc5_stream_t stream) {

@@ -1,0 +1,360 @@
+// Batched SpMV: y_j = A_j x_j for many uneven matrices in one persistent,
+// graph-replayed launch.
+//
+// Many small products launched one by one leave the GPU idle between tiny
+// kernels. Here every short interval of every matrix belongs to a work item
+// of 32/r consecutive intervals (one warp's worth, lane per row as in the
+// single-matrix kernel); persistent warps take items from a global counter
+// with one atomicAdd each (no waiting on other warps), so uneven matrices
+// balance themselves. Each matrix keeps its own block shape (a run-time
+// argument here), chosen per matrix by the caller's tuner or selector. Long
+// intervals are items of a second kind - one warp per segment, partials into
+// the matrix's scratch - followed by one fix-up kernel over all segments.
+// The counter reset, the persistent kernel and the fix-up are captured once
+// into a CUDA graph at batch creation; a batched SpMV is one graph launch.
+#include <vector>
+
+#include "spmv_beta.cuh"
+
+namespace spc5 {
+namespace {
+
+struct MatDesc {  // one matrix of the batch (device copy)
+  const int32_t* brp;
+  const int32_t* bcol;
+  const uint8_t* bmask;
+  const void* val;
+  const int64_t* valptr;
+  const Segment* segs;
+  void* partials;
+  const void* x;
+  void* y;
+  int64_t n, I, nseg, long_values;
+  int32_t r, c, mb, long_blocks, log2r, pad;
+};
+
+struct Item {  // kind 0: intervals [i0, i0 + 32/r) of matrix mat; kind 1: segment i0 of mat
+  int32_t mat;
+  int32_t i0;
+  int32_t kind;
+  int32_t pad;
+};
+
+__device__ __forceinline__ uint32_t rb(const uint32_t (&w)[4], int p, int c) {
+  return (w[p >> 5] >> (p & 31)) & ((1u << c) - 1u);
+}
+
+__device__ __forceinline__ int pb(const uint32_t (&w)[4], int p) {
+  int cnt = 0;
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    if (q < (p >> 5)) cnt += __popc(w[q]);
+  if (p & 31) cnt += __popc(w[p >> 5] & ((1u << (p & 31)) - 1u));
+  return cnt;
+}
+
+__device__ __forceinline__ void ldmask(const uint8_t* __restrict__ m, int64_t b, int mb, uint32_t (&w)[4]) {
+  w[0] = w[1] = w[2] = w[3] = 0u;
+  switch (mb) {
+    case 1: w[0] = __ldg(m + b); break;
+    case 2: w[0] = __ldg(reinterpret_cast<const uint16_t*>(m) + b); break;
+    case 4: w[0] = __ldg(reinterpret_cast<const uint32_t*>(m) + b); break;
+    case 8: {
+      const uint2 v = __ldg(reinterpret_cast<const uint2*>(m) + b);
+      w[0] = v.x;
+      w[1] = v.y;
+      break;
+    }
+    default: {
+      const uint4 v = __ldg(reinterpret_cast<const uint4*>(m) + b);
+      w[0] = v.x;
+      w[1] = v.y;
+      w[2] = v.z;
+      w[3] = v.w;
+    }
+  }
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_batch(const MatDesc* __restrict__ mats, const Item* __restrict__ items,
+                                               int64_t nitems, unsigned long long* __restrict__ counter) {
+  using V = typename T::V;
+  using X = typename T::X;
+  using A = typename T::A;
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    unsigned long long k = 0;
+    if (lane == 0) k = atomicAdd(counter, 1ull);
+    k = __shfl_sync(0xffffffffu, k, 0);
+    if (k >= (unsigned long long)nitems) break;
+    const Item itm = items[k];
+    const MatDesc& d = mats[itm.mat];
+    const int r = d.r, c = d.c, mb = d.mb;
+    const V* __restrict__ val = static_cast<const V*>(d.val);
+    const X* __restrict__ x = static_cast<const X*>(d.x);
+    if (itm.kind == 0) {
+      const int64_t it = (int64_t)itm.i0 + (lane >> d.log2r);
+      const int i = lane & (r - 1);
+      if (it >= d.I) continue;
+      int32_t b = __ldg(d.brp + it);
+      const int32_t bend = __ldg(d.brp + it + 1);
+      const int64_t v0 = __ldg(d.valptr + it);
+      if (bend - b > d.long_blocks || __ldg(d.valptr + it + 1) - v0 > d.long_values) continue;
+      A acc = 0;
+      int32_t vbase = 0;
+      for (; b < bend; ++b) {
+        uint32_t w[4];
+        ldmask(d.bmask, b, mb, w);
+        uint32_t bits = rb(w, i * c, c);
+        int32_t vo = vbase + pb(w, i * c);
+        vbase += __popc(w[0]) + __popc(w[1]) + __popc(w[2]) + __popc(w[3]);
+        if (!bits) continue;
+        const int64_t col0 = __ldg(d.bcol + b);
+        while (bits) {
+          const int kb = __ffs(bits) - 1;
+          bits &= bits - 1;
+          acc = fma(T::val(val + v0, vo++), T::xv(x, col0 + kb), acc);
+        }
+      }
+      const int64_t row = it * r + i;
+      if (row < d.n) static_cast<X*>(d.y)[row] = acc;
+    } else {
+      // one warp per segment, lane = (block slot, row), as k_spmv_segments
+      const Segment sg = d.segs[itm.i0];
+      const int S = kWarp >> d.log2r;
+      const int slot = lane >> d.log2r, i = lane & (r - 1);
+      int64_t vbase = sg.v_begin;
+      A acc = 0;
+      for (int32_t b0 = sg.b_begin; b0 < sg.b_end; b0 += S) {
+        const int32_t b = b0 + slot;
+        const bool valid = b < sg.b_end;
+        uint32_t w[4] = {0u, 0u, 0u, 0u};
+        if (valid) ldmask(d.bmask, b, mb, w);
+        const int cnt = __popc(w[0]) + __popc(w[1]) + __popc(w[2]) + __popc(w[3]);
+        int incl = cnt;
+        for (int dd = r; dd < kWarp; dd <<= 1) {
+          const int t = __shfl_up_sync(0xffffffffu, incl, dd);
+          if (lane >= dd) incl += t;
+        }
+        const int total = __shfl_sync(0xffffffffu, incl, kWarp - 1);
+        int64_t vo = vbase + (incl - cnt) + (valid ? pb(w, i * c) : 0);
+        uint32_t bits = valid ? rb(w, i * c, c) : 0u;
+        const int64_t col0 = valid ? __ldg(d.bcol + b) : 0;
+        while (bits) {
+          const int kb = __ffs(bits) - 1;
+          bits &= bits - 1;
+          acc = fma(T::val(val, vo++), T::xv(x, col0 + kb), acc);
+        }
+        vbase += total;
+      }
+      for (int dd = kWarp / 2; dd >= r; dd >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, dd);
+      if (lane < r) static_cast<A*>(d.partials)[(int64_t)itm.i0 * r + lane] = acc;
+    }
+  }
+}
+
+// one thread per (matrix, segment, row): the first segment of each long
+// interval adds its interval's partials in order
+template <class T>
+__global__ void k_batch_fixup(const MatDesc* __restrict__ mats, const int2* __restrict__ segrows, int64_t nrows) {
+  using X = typename T::X;
+  using A = typename T::A;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nrows) return;
+  const int2 e = segrows[t];  // (matrix, segment * r + row)
+  const MatDesc& d = mats[e.x];
+  const int64_t seg = e.y / d.r;
+  const int i = e.y % d.r;
+  const int32_t it = d.segs[seg].interval;
+  if (seg > 0 && d.segs[seg - 1].interval == it) return;
+  const A* part = static_cast<const A*>(d.partials);
+  A s = 0;
+  for (int64_t q = seg; q < d.nseg && d.segs[q].interval == it; ++q) s += part[q * d.r + i];
+  const int64_t row = (int64_t)it * d.r + i;
+  if (row < d.n) static_cast<X*>(d.y)[row] = s;
+}
+
+}  // namespace
+}  // namespace spc5
+
+struct spc5_batch_s {
+  spc5_dtype vt = SPC5_F32;
+  int count = 0;
+  int64_t nitems = 0, nsegrows = 0;
+  spc5::MatDesc* mats_d = nullptr;
+  spc5::Item* items_d = nullptr;
+  int2* segrows_d = nullptr;
+  unsigned long long* counter_d = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int blocks = 0;
+};
+
+namespace spc5 {
+
+static void batch_free(spc5_batch_s* b) {
+  if (!b) return;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  cudaFree(b->mats_d);
+  cudaFree(b->items_d);
+  cudaFree(b->segrows_d);
+  cudaFree(b->counter_d);
+  delete b;
+}
+
+template <class T>
+cudaError_t batch_enqueue(spc5_batch_s* b, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(b->counter_d, 0, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  if (b->nitems > 0) k_batch<T><<<b->blocks, 256, 0, s>>>(b->mats_d, b->items_d, b->nitems, b->counter_d);
+  if (b->nsegrows > 0)
+    k_batch_fixup<T><<<(unsigned)((b->nsegrows + 255) / 256), 256, 0, s>>>(b->mats_d, b->segrows_d, b->nsegrows);
+  return cudaGetLastError();
+}
+
+cudaError_t batch_enqueue_any(spc5_batch_s* b, cudaStream_t s) {
+  switch (b->vt) {
+    case SPC5_F64: return batch_enqueue<F64>(b, s);
+    case SPC5_F32: return batch_enqueue<F32>(b, s);
+    default: return batch_enqueue<BF16>(b, s);
+  }
+}
+
+spc5_status batch_create_impl(const spc5_handle* mats, const void* const* xs, void* const* ys, int count,
+                              spc5_batch_s** out) {
+  spc5_batch_s* b = new spc5_batch_s();
+  b->count = count;
+  b->vt = mats[0]->vt;
+  std::vector<MatDesc> md((size_t)count);
+  std::vector<Item> items;
+  std::vector<int2> segrows;
+  for (int j = 0; j < count; ++j) {
+    const spc5_matrix* h = mats[j];
+    if (h->vt != b->vt) {
+      batch_free(b);
+      return fail(SPC5_EINVAL, "batch: all matrices must have the same value type");
+    }
+    MatDesc& d = md[(size_t)j];
+    d.brp = h->block_rowptr;
+    d.bcol = h->block_colidx;
+    d.bmask = h->block_masks;
+    d.val = h->values;
+    d.valptr = h->valptr;
+    d.segs = h->segs;
+    d.partials = h->partials;
+    d.x = xs[j];
+    d.y = ys[j];
+    d.n = h->n;
+    d.I = h->I;
+    d.nseg = h->nseg;
+    d.long_values = h->long_values;
+    d.r = h->r;
+    d.c = h->c;
+    d.mb = h->mb;
+    d.long_blocks = h->long_blocks;
+    d.log2r = h->r == 1 ? 0 : h->r == 2 ? 1 : h->r == 4 ? 2 : 3;
+    d.pad = 0;
+    const int S = kWarp / h->r;
+    for (int64_t i0 = 0; i0 < h->I; i0 += S) items.push_back(Item{j, (int32_t)i0, 0, 0});
+    for (int64_t q = 0; q < h->nseg; ++q) {
+      items.push_back(Item{j, (int32_t)q, 1, 0});
+      for (int i = 0; i < h->r; ++i) segrows.push_back(make_int2(j, (int)(q * h->r + i)));
+    }
+  }
+  b->nitems = (int64_t)items.size();
+  b->nsegrows = (int64_t)segrows.size();
+  cudaError_t e = cudaMalloc((void**)&b->mats_d, sizeof(MatDesc) * (size_t)count);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->items_d, sizeof(Item) * (items.size() + 1));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->segrows_d, sizeof(int2) * (segrows.size() + 1));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->counter_d, sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMemcpy(b->mats_d, md.data(), sizeof(MatDesc) * (size_t)count, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !items.empty())
+    e = cudaMemcpy(b->items_d, items.data(), sizeof(Item) * items.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !segrows.empty())
+    e = cudaMemcpy(b->segrows_d, segrows.data(), sizeof(int2) * segrows.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    batch_free(b);
+    return cuda_fail(e, "batch: descriptors");
+  }
+  // persistent grid: the CTAs resident at once (at most one item per warp)
+  int per_sm = 8;
+  {
+    int v = 0;
+    cudaError_t oe;
+    switch (b->vt) {
+      case SPC5_F64: oe = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_batch<F64>, 256, 0); break;
+      case SPC5_F32: oe = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_batch<F32>, 256, 0); break;
+      default: oe = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_batch<BF16>, 256, 0); break;
+    }
+    if (oe == cudaSuccess && v > 0) per_sm = v;
+  }
+  int64_t blocks = (int64_t)sm_count() * per_sm;
+  const int64_t need = (b->nitems + 7) / 8;
+  if (blocks > need) blocks = need > 0 ? need : 1;
+  b->blocks = (int)blocks;
+  // capture the whole batched product once; replays reuse it
+  cudaStream_t cs = nullptr;
+  cudaGraph_t g = nullptr;
+  e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    cudaError_t e2 = batch_enqueue_any(b, cs);
+    e = cudaStreamEndCapture(cs, &g);
+    if (e2 != cudaSuccess) e = e2;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, g, 0);
+  if (g) cudaGraphDestroy(g);
+  if (cs) cudaStreamDestroy(cs);
+  if (e != cudaSuccess) {
+    batch_free(b);
+    return cuda_fail(e, "batch: graph");
+  }
+  *out = b;
+  return SPC5_OK;
+}
+
+}  // namespace spc5
+
+using namespace spc5;
+
+extern "C" {
+
+spc5_status spc5_batch_create(const spc5_handle* mats, const void* const* x_d, void* const* y_d, int count,
+                              spc5_batch* out) {
+  if (!out) return fail(SPC5_EINVAL, "batch_create: NULL output");
+  *out = nullptr;
+  if (count < 1 || !mats || !x_d || !y_d) return fail(SPC5_EINVAL, "batch_create: empty batch or NULL array");
+  for (int j = 0; j < count; ++j) {
+    if (!mats[j]) return fail(SPC5_EINVAL, "batch_create: NULL handle");
+    if ((mats[j]->m > 0 && !x_d[j]) || (mats[j]->n > 0 && !y_d[j])) return fail(SPC5_EINVAL, "batch_create: NULL vector");
+    if (mats[j]->I > INT32_MAX || mats[j]->nseg > INT32_MAX / 8) return fail(SPC5_ERANGE, "batch_create: matrix too large");
+  }
+  spc5_batch_s* b = nullptr;
+  spc5_status st = batch_create_impl(mats, x_d, y_d, count, &b);
+  if (st != SPC5_OK) return st;
+  *out = b;
+  return SPC5_OK;
+}
+
+spc5_status spc5_batch_spmv(spc5_batch b, spc5_stream_t stream) {
+  if (!b) return fail(SPC5_EINVAL, "batch_spmv: NULL batch");
+  cudaError_t e = cudaGraphLaunch(b->exec, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "batch_spmv: graph launch");
+  return SPC5_OK;
+}
+
+spc5_status spc5_batch_spmv_direct(spc5_batch b, spc5_stream_t stream) {
+  if (!b) return fail(SPC5_EINVAL, "batch_spmv_direct: NULL batch");
+  cudaError_t e = batch_enqueue_any(b, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "batch_spmv_direct: launch");
+  return SPC5_OK;
+}
+
+spc5_status spc5_batch_destroy(spc5_batch b) {
+  if (!b) return SPC5_OK;
+  cudaError_t e = cudaDeviceSynchronize();
+  batch_free(b);
+  if (e != cudaSuccess) return cuda_fail(e, "batch_destroy: device synchronisation");
+  return SPC5_OK;
+}
+
+}  // extern "C"

@@ -99,6 +99,18 @@ spc5_status spmm_impl(spc5_matrix* h, int k, const void* X, int64_t ldx, void* Y
                       cudaStream_t s);
 int spmm_auto_tile(int k);
 
+// selection (select.cu)
+spc5_status features_impl(int64_t n, int64_t nnz, const int64_t* rowptr, const int32_t* colidx, double* f,
+                          cudaStream_t s);
+spc5_status mlp_train_impl(float* P, const float* X, const float* Y, const float* M, int N, int epochs, int batch,
+                           float lr, uint64_t seed, float* loss_hist, cudaStream_t s);
+spc5_status mlp_grad_impl(const float* P, const float* X, const float* Y, const float* M, int B, float* loss,
+                          float* grad, cudaStream_t s);
+spc5_status mlp_infer_impl(const float* P, const float* X, int N, float* out, cudaStream_t s);
+spc5_status poly_fit_impl(const double* avg, const double* perf, int N, int degree, double* coef);
+int poly_select_impl(const double* coef, int degree, const double* feat, double* est);
+int mlp_param_count();
+
 // conjugate gradients (cg.cu)
 spc5_status cg_impl(const spc5_matrix* A, const spc5_matrix* L, const double* b, double* x, const spc5_cg_opts* o,
                     spc5_cg_info* info, cudaStream_t s);

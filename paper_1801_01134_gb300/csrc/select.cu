@@ -1,0 +1,433 @@
+// Block-shape selection: features without conversion, a timing recorder,
+// the paper-style polynomial predictor and a small MLP trained on the GPU.
+//
+// The paper picks a kernel before converting the matrix from the average
+// number of values per block, Avg(r,c) = N_nnz / N_blocks(r,c), which is
+// cheap to count (section "Performance prediction and optimal kernel
+// selection"), through one fitted polynomial per kernel (section "Performance
+// polynomial interpolation"); its conclusion asks for richer inputs. Here:
+//   * k_features: one pass over the CSR structure counts N_blocks for all
+//     twelve shapes (one merge of each interval's rows per r, three greedy
+//     covers c = 4, 8, 16 along the same merge) and the row-length sum, sum
+//     of squares and maximum;
+//   * spc5_time_formats: converts to each shape and times the SpMV (the
+//     exhaustive choice, and the training targets);
+//   * a least-squares polynomial per format (Householder QR on the
+//     Vandermonde matrix of Avg(r,c));
+//   * an MLP 16 -> 64 -> 64 -> 12 (ReLU, float32) scoring the formats, trained
+//     with mean squared error and Adam by one fused kernel per minibatch step
+//     (forward, loss gradient, backward, update inside one CTA, so the step is
+//     deterministic); the layers are far too small for tensor cores to pay.
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <cstring>
+#include <random>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace spc5 {
+namespace {
+
+constexpr int kNF = SPC5_NFEATURES;  // 16
+constexpr int kNO = SPC5_NFORMATS;   // 12
+constexpr int kH = 64;
+constexpr int kNP = kH * kNF + kH + kH * kH + kH + kNO * kH + kNO;  // 6028 parameters
+
+// ------------------------------------------------------------ features
+// acc[0..11] = N_blocks per shape, acc[12] = sum of row lengths, acc[13] =
+// sum of squared row lengths, acc[14] = max row length
+__global__ void __launch_bounds__(128) k_features(int64_t n, const int64_t* __restrict__ rowptr,
+                                                  const int32_t* __restrict__ colidx,
+                                                  unsigned long long* __restrict__ acc) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // group of 8 rows
+  unsigned long long cnt[12];
+#pragma unroll
+  for (int q = 0; q < 12; ++q) cnt[q] = 0;
+  unsigned long long s1 = 0, s2 = 0, mx = 0;
+  const int64_t row0 = g * 8;
+  if (row0 < n) {
+    const int rows = (int)(n - row0 < 8 ? n - row0 : 8);
+    int64_t beg[8], end[8];
+    for (int i = 0; i < 8; ++i) {
+      if (i < rows) {
+        beg[i] = rowptr[row0 + i];
+        end[i] = rowptr[row0 + i + 1];
+        const unsigned long long len = (unsigned long long)(end[i] - beg[i]);
+        s1 += len;
+        s2 += len * len;
+        mx = len > mx ? len : mx;
+      } else {
+        beg[i] = end[i] = 0;
+      }
+    }
+    // r = 1, 2, 4, 8: merge the rows of each interval in column order; a
+    // column at or beyond the current block's end starts a new block
+    const int rs[4] = {1, 2, 4, 8};
+    for (int a = 0; a < 4; ++a) {
+      const int r = rs[a];
+      for (int i0 = 0; i0 < rows; i0 += r) {
+        int64_t h[8];
+        const int ri = rows - i0 < r ? rows - i0 : r;
+        for (int i = 0; i < ri; ++i) h[i] = beg[i0 + i];
+        int64_t e4 = LLONG_MIN, e8 = LLONG_MIN, e16 = LLONG_MIN;
+        for (;;) {
+          int best = -1;
+          int64_t bc = LLONG_MAX;
+          for (int i = 0; i < ri; ++i)
+            if (h[i] < end[i0 + i]) {
+              const int64_t cc = colidx[h[i]];
+              if (cc < bc) {
+                bc = cc;
+                best = i;
+              }
+            }
+          if (best < 0) break;
+          ++h[best];
+          if (bc >= e4) { ++cnt[a * 3 + 0]; e4 = bc + 4; }
+          if (bc >= e8) { ++cnt[a * 3 + 1]; e8 = bc + 8; }
+          if (bc >= e16) { ++cnt[a * 3 + 2]; e16 = bc + 16; }
+        }
+      }
+    }
+  }
+  // block sums (integers: the order does not matter) then one atomic each
+  __shared__ unsigned long long red[15][4];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  unsigned long long v[15];
+#pragma unroll
+  for (int q = 0; q < 12; ++q) v[q] = cnt[q];
+  v[12] = s1;
+  v[13] = s2;
+  v[14] = mx;
+#pragma unroll
+  for (int q = 0; q < 15; ++q) {
+    unsigned long long x = v[q];
+    for (int d = 16; d >= 1; d >>= 1) {
+      const unsigned long long o = __shfl_xor_sync(0xffffffffu, x, d);
+      x = q == 14 ? (o > x ? o : x) : x + o;
+    }
+    if (lane == 0) red[q][w] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < 15) {
+    const int q = threadIdx.x;
+    unsigned long long x = red[q][0];
+    for (int k = 1; k < 4; ++k) x = q == 14 ? (red[q][k] > x ? red[q][k] : x) : x + red[q][k];
+    if (q == 14)
+      atomicMax(&acc[q], x);
+    else
+      atomicAdd(&acc[q], x);
+  }
+}
+
+// ----------------------------------------------------------------- MLP
+// Parameter layout (float32, flat): W1[64][16], b1[64], W2[64][64], b2[64],
+// W3[12][64], b3[12].
+constexpr int oW1 = 0, ob1 = oW1 + kH * kNF, oW2 = ob1 + kH, ob2 = oW2 + kH * kH, oW3 = ob2 + kH,
+              ob3 = oW3 + kNO * kH;
+constexpr int kMaxBatch = 32;  // keeps the step's activations in static shared memory
+constexpr int kStepThreads = 1024;
+
+// One training step on a minibatch of B <= 32 samples (rows idx[0..B) of X and
+// Y, with the 0/1 mask M saying which targets exist): forward, mean squared
+// error gradient, backward, Adam update of the parameters, all in one CTA.
+__global__ void __launch_bounds__(kStepThreads) k_mlp_step(float* __restrict__ P, float* __restrict__ mom,
+                                                           float* __restrict__ vel, const float* __restrict__ X,
+                                                           const float* __restrict__ Y, const float* __restrict__ Mk,
+                                                           const int32_t* __restrict__ idx, int B, int t, float lr,
+                                                           float* __restrict__ loss_out, float* __restrict__ grad_out) {
+  __shared__ float xs[kMaxBatch][kNF];
+  __shared__ float z1[kMaxBatch][kH], z2[kMaxBatch][kH];  // pre-activations, then reused for gradients
+  __shared__ float h1[kMaxBatch][kH], h2[kMaxBatch][kH];
+  __shared__ float dout[kMaxBatch][kNO];
+  __shared__ float red[kStepThreads / 32];
+  const int tid = threadIdx.x;
+  for (int e = tid; e < B * kNF; e += kStepThreads) xs[e / kNF][e % kNF] = X[(int64_t)idx[e / kNF] * kNF + e % kNF];
+  __syncthreads();
+  // layer 1
+  for (int e = tid; e < B * kH; e += kStepThreads) {
+    const int s = e / kH, j = e % kH;
+    float a = P[ob1 + j];
+    for (int q = 0; q < kNF; ++q) a = fmaf(P[oW1 + j * kNF + q], xs[s][q], a);
+    z1[s][j] = a;
+    h1[s][j] = a > 0.f ? a : 0.f;
+  }
+  __syncthreads();
+  for (int e = tid; e < B * kH; e += kStepThreads) {
+    const int s = e / kH, j = e % kH;
+    float a = P[ob2 + j];
+    for (int q = 0; q < kH; ++q) a = fmaf(P[oW2 + j * kH + q], h1[s][q], a);
+    z2[s][j] = a;
+    h2[s][j] = a > 0.f ? a : 0.f;
+  }
+  __syncthreads();
+  // outputs, masked squared error and its gradient
+  float msum = 0.f;
+  for (int s = 0; s < B; ++s)
+    for (int o = 0; o < kNO; ++o) msum += Mk[(int64_t)idx[s] * kNO + o];  // every thread: same value
+  float lsum = 0.f;
+  for (int e = tid; e < B * kNO; e += kStepThreads) {
+    const int s = e / kNO, o = e % kNO;
+    float a = P[ob3 + o];
+    for (int q = 0; q < kH; ++q) a = fmaf(P[oW3 + o * kH + q], h2[s][q], a);
+    const float m = Mk[(int64_t)idx[s] * kNO + o];
+    const float d = a - Y[(int64_t)idx[s] * kNO + o];
+    dout[s][o] = msum > 0.f ? 2.f * m * d / msum : 0.f;
+    lsum += m * d * d;
+  }
+  // loss (block sum, fixed order)
+  for (int d = 16; d >= 1; d >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, d);
+  if ((tid & 31) == 0) red[tid >> 5] = lsum;
+  __syncthreads();
+  if (tid == 0) {
+    float l = 0.f;
+    for (int k = 0; k < kStepThreads / 32; ++k) l += red[k];
+    if (loss_out) *loss_out = msum > 0.f ? l / msum : 0.f;
+  }
+  // dH2 -> dZ2 (into z2)
+  for (int e = tid; e < B * kH; e += kStepThreads) {
+    const int s = e / kH, j = e % kH;
+    float a = 0.f;
+    for (int o = 0; o < kNO; ++o) a = fmaf(dout[s][o], P[oW3 + o * kH + j], a);
+    z2[s][j] = z2[s][j] > 0.f ? a : 0.f;
+  }
+  __syncthreads();
+  // dH1 -> dZ1 (into z1)
+  for (int e = tid; e < B * kH; e += kStepThreads) {
+    const int s = e / kH, j = e % kH;
+    float a = 0.f;
+    for (int o = 0; o < kH; ++o) a = fmaf(z2[s][o], P[oW2 + o * kH + j], a);
+    z1[s][j] = z1[s][j] > 0.f ? a : 0.f;
+  }
+  __syncthreads();
+  // gradients (sum over the batch in sample order) and the Adam update; each
+  // parameter is owned by one thread
+  const float b1c = 1.f - powf(0.9f, (float)t), b2c = 1.f - powf(0.999f, (float)t);
+  for (int p = tid; p < kNP; p += kStepThreads) {
+    float g = 0.f;
+    if (p < ob1) {
+      const int j = (p - oW1) / kNF, q = (p - oW1) % kNF;
+      for (int s = 0; s < B; ++s) g = fmaf(z1[s][j], xs[s][q], g);
+    } else if (p < oW2) {
+      const int j = p - ob1;
+      for (int s = 0; s < B; ++s) g += z1[s][j];
+    } else if (p < ob2) {
+      const int j = (p - oW2) / kH, q = (p - oW2) % kH;
+      for (int s = 0; s < B; ++s) g = fmaf(z2[s][j], h1[s][q], g);
+    } else if (p < oW3) {
+      const int j = p - ob2;
+      for (int s = 0; s < B; ++s) g += z2[s][j];
+    } else if (p < ob3) {
+      const int o = (p - oW3) / kH, q = (p - oW3) % kH;
+      for (int s = 0; s < B; ++s) g = fmaf(dout[s][o], h2[s][q], g);
+    } else {
+      const int o = p - ob3;
+      for (int s = 0; s < B; ++s) g += dout[s][o];
+    }
+    if (grad_out) grad_out[p] = g;
+    if (lr > 0.f) {
+      const float m = 0.9f * mom[p] + 0.1f * g;
+      const float v = 0.999f * vel[p] + 0.001f * g * g;
+      mom[p] = m;
+      vel[p] = v;
+      P[p] -= lr * (m / b1c) / (sqrtf(v / b2c) + 1e-8f);
+    }
+  }
+}
+
+// scores of N samples: one thread per (sample, output); hidden layers of a
+// sample recomputed per output is wasteful but N is small; instead one thread
+// per sample with the activations in local arrays
+__global__ void __launch_bounds__(128) k_mlp_infer(const float* __restrict__ P, const float* __restrict__ X, int N,
+                                                   float* __restrict__ out) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= N) return;
+  float a1[kH], a2[kH];
+  for (int j = 0; j < kH; ++j) {
+    float a = P[ob1 + j];
+    for (int q = 0; q < kNF; ++q) a = fmaf(P[oW1 + j * kNF + q], X[(int64_t)s * kNF + q], a);
+    a1[j] = a > 0.f ? a : 0.f;
+  }
+  for (int j = 0; j < kH; ++j) {
+    float a = P[ob2 + j];
+    for (int q = 0; q < kH; ++q) a = fmaf(P[oW2 + j * kH + q], a1[q], a);
+    a2[j] = a > 0.f ? a : 0.f;
+  }
+  for (int o = 0; o < kNO; ++o) {
+    float a = P[ob3 + o];
+    for (int q = 0; q < kH; ++q) a = fmaf(P[oW3 + o * kH + q], a2[q], a);
+    out[(int64_t)s * kNO + o] = a;
+  }
+}
+
+struct DBuf {
+  void* p = nullptr;
+  ~DBuf() {
+    if (p) cudaFree(p);
+  }
+};
+
+// Householder QR least squares: minimise ||V c - y|| for V (N x k), N >= k.
+bool lstsq(std::vector<double> V, std::vector<double> y, int N, int k, double* c) {
+  for (int j = 0; j < k; ++j) {
+    double nrm = 0;
+    for (int i = j; i < N; ++i) nrm += V[(size_t)i * k + j] * V[(size_t)i * k + j];
+    nrm = std::sqrt(nrm);
+    if (nrm == 0) return false;
+    const double alpha = V[(size_t)j * k + j] > 0 ? -nrm : nrm;
+    std::vector<double> v((size_t)N, 0.0);
+    for (int i = j; i < N; ++i) v[(size_t)i] = V[(size_t)i * k + j];
+    v[(size_t)j] -= alpha;
+    double vv = 0;
+    for (int i = j; i < N; ++i) vv += v[(size_t)i] * v[(size_t)i];
+    if (vv == 0) continue;
+    for (int col = j; col < k; ++col) {
+      double d = 0;
+      for (int i = j; i < N; ++i) d += v[(size_t)i] * V[(size_t)i * k + col];
+      d = 2 * d / vv;
+      for (int i = j; i < N; ++i) V[(size_t)i * k + col] -= d * v[(size_t)i];
+    }
+    double d = 0;
+    for (int i = j; i < N; ++i) d += v[(size_t)i] * y[(size_t)i];
+    d = 2 * d / vv;
+    for (int i = j; i < N; ++i) y[(size_t)i] -= d * v[(size_t)i];
+  }
+  for (int j = k - 1; j >= 0; --j) {
+    double s = y[(size_t)j];
+    for (int q = j + 1; q < k; ++q) s -= V[(size_t)j * k + q] * c[q];
+    if (V[(size_t)j * k + j] == 0) return false;
+    c[j] = s / V[(size_t)j * k + j];
+  }
+  return true;
+}
+
+}  // namespace
+
+spc5_status features_impl(int64_t n, int64_t nnz, const int64_t* rowptr, const int32_t* colidx, double* f,
+                          cudaStream_t s) {
+  DBuf acc;
+  cudaError_t e = cudaMalloc(&acc.p, sizeof(unsigned long long) * 16);
+  if (e == cudaSuccess) e = cudaMemsetAsync(acc.p, 0, sizeof(unsigned long long) * 16, s);
+  if (e != cudaSuccess) return cuda_fail(e, "features: scratch");
+  const int64_t groups = (n + 7) / 8;
+  if (groups > 0)
+    k_features<<<(unsigned)((groups + 127) / 128), 128, 0, s>>>(n, rowptr, colidx, (unsigned long long*)acc.p);
+  unsigned long long h[16];
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h, acc.p, sizeof(h), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "features");
+  for (int q = 0; q < 12; ++q) f[q] = h[q] ? (double)nnz / (double)h[q] : 0.0;
+  const double mean = n > 0 ? (double)h[12] / (double)n : 0.0;
+  const double var = n > 0 ? (double)h[13] / (double)n - mean * mean : 0.0;
+  f[12] = mean;
+  f[13] = var > 0 ? std::sqrt(var) : 0.0;
+  f[14] = (double)h[14];
+  f[15] = std::log10((double)(n > 1 ? n : 1));
+  return SPC5_OK;
+}
+
+spc5_status mlp_train_impl(float* P, const float* X, const float* Y, const float* M, int N, int epochs, int batch,
+                           float lr, uint64_t seed, float* loss_hist, cudaStream_t s) {
+  if (batch < 1 || batch > kMaxBatch) return fail(SPC5_EINVAL, "mlp_train: batch must be in [1, 32]");
+  const int steps_per_epoch = (N + batch - 1) / batch;
+  DBuf mom, vel, idx, loss;
+  cudaError_t e = cudaMalloc(&mom.p, sizeof(float) * kNP);
+  if (e == cudaSuccess) e = cudaMalloc(&vel.p, sizeof(float) * kNP);
+  if (e == cudaSuccess) e = cudaMalloc(&idx.p, sizeof(int32_t) * (size_t)N);
+  if (e == cudaSuccess) e = cudaMalloc(&loss.p, sizeof(float) * (size_t)steps_per_epoch);
+  if (e == cudaSuccess) e = cudaMemsetAsync(mom.p, 0, sizeof(float) * kNP, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(vel.p, 0, sizeof(float) * kNP, s);
+  if (e != cudaSuccess) return cuda_fail(e, "mlp_train: workspace");
+  std::mt19937_64 rng(seed);
+  std::vector<int32_t> order((size_t)N);
+  std::vector<float> lh((size_t)steps_per_epoch);
+  int t = 0;
+  for (int ep = 0; ep < epochs; ++ep) {
+    for (int i = 0; i < N; ++i) order[(size_t)i] = i;
+    std::shuffle(order.begin(), order.end(), rng);
+    e = cudaMemcpyAsync(idx.p, order.data(), sizeof(int32_t) * (size_t)N, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(e, "mlp_train: indices");
+    for (int st = 0; st < steps_per_epoch; ++st) {
+      const int b0 = st * batch;
+      const int B = N - b0 < batch ? N - b0 : batch;
+      ++t;
+      k_mlp_step<<<1, kStepThreads, 0, s>>>(P, (float*)mom.p, (float*)vel.p, X, Y, M, (const int32_t*)idx.p + b0, B,
+                                            t, lr, (float*)loss.p + st, nullptr);
+    }
+    e = cudaMemcpyAsync(lh.data(), loss.p, sizeof(float) * (size_t)steps_per_epoch, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "mlp_train: step");
+    if (loss_hist) {
+      double a = 0;
+      for (int st = 0; st < steps_per_epoch; ++st) a += lh[(size_t)st];
+      loss_hist[ep] = (float)(a / steps_per_epoch);
+    }
+  }
+  return SPC5_OK;
+}
+
+spc5_status mlp_grad_impl(const float* P, const float* X, const float* Y, const float* M, int B, float* loss,
+                          float* grad, cudaStream_t s) {
+  if (B < 1 || B > kMaxBatch) return fail(SPC5_EINVAL, "mlp_grad: batch must be in [1, 32]");
+  std::vector<int32_t> order((size_t)B);
+  for (int i = 0; i < B; ++i) order[(size_t)i] = i;
+  DBuf idx, l, Pc;
+  cudaError_t e = cudaMalloc(&idx.p, sizeof(int32_t) * (size_t)B);
+  if (e == cudaSuccess) e = cudaMalloc(&l.p, sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&Pc.p, sizeof(float) * kNP);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(Pc.p, P, sizeof(float) * kNP, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(idx.p, order.data(), sizeof(int32_t) * (size_t)B, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return cuda_fail(e, "mlp_grad: workspace");
+  // lr = 0: gradient only, the parameter copy is left as it is
+  k_mlp_step<<<1, kStepThreads, 0, s>>>((float*)Pc.p, nullptr, nullptr, X, Y, M, (const int32_t*)idx.p, B, 1, 0.f,
+                                        (float*)l.p, grad);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(loss, l.p, sizeof(float), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "mlp_grad");
+  return SPC5_OK;
+}
+
+spc5_status mlp_infer_impl(const float* P, const float* X, int N, float* out, cudaStream_t s) {
+  if (N > 0) k_mlp_infer<<<(unsigned)((N + 127) / 128), 128, 0, s>>>(P, X, N, out);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "mlp_infer");
+  return SPC5_OK;
+}
+
+spc5_status poly_fit_impl(const double* avg, const double* perf, int N, int degree, double* coef) {
+  const int k = degree + 1;
+  if (degree < 0 || degree > 6 || N < k) return fail(SPC5_EINVAL, "poly_fit: need 0 <= degree <= 6 and N > degree");
+  for (int f = 0; f < kNO; ++f) {
+    std::vector<double> V((size_t)N * k), y((size_t)N);
+    for (int i = 0; i < N; ++i) {
+      double p = 1.0;
+      for (int j = 0; j < k; ++j) {
+        V[(size_t)i * k + j] = p;
+        p *= avg[(size_t)i * kNO + f];
+      }
+      y[(size_t)i] = perf[(size_t)i * kNO + f];
+    }
+    if (!lstsq(V, y, N, k, coef + (size_t)f * k)) return fail(SPC5_EINVAL, "poly_fit: rank-deficient data");
+  }
+  return SPC5_OK;
+}
+
+int poly_select_impl(const double* coef, int degree, const double* feat, double* est) {
+  int best = 0;
+  for (int f = 0; f < kNO; ++f) {
+    double v = 0.0;
+    for (int j = degree; j >= 0; --j) v = v * feat[f] + coef[(size_t)f * (degree + 1) + j];
+    est[f] = v;
+    if (v > est[best]) best = f;
+  }
+  return best;
+}
+
+int mlp_param_count() { return kNP; }
+
+}  // namespace spc5

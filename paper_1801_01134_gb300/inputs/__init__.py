@@ -17,7 +17,6 @@ import ctypes
 import os
 import subprocess
 import tempfile
-import weakref
 from dataclasses import dataclass
 
 import numpy as np
@@ -121,18 +120,20 @@ class CSR:
 
 
 def _take(ptr) -> CSR:
+    """Copy the generator's arrays into numpy-owned memory and free the C side
+    (views into C memory would dangle once their first owner is collected)."""
     if not ptr:
         raise MemoryError("generator failed (bad arguments or out of memory)")
     lib = _load()
-    s = ptr.contents
-    n, m, nnz = int(s.n), int(s.m), int(s.nnz)
-    rowptr = np.ctypeslib.as_array(s.rowptr, shape=(n + 1,))
-    colidx = np.ctypeslib.as_array(s.colidx, shape=(max(nnz, 1),))[:nnz]
-    values = np.ctypeslib.as_array(s.values, shape=(max(nnz, 1),))[:nnz]
-    out = CSR(n, m, rowptr, colidx, values)
-    # the arrays view C memory: free it when the CSR object goes away
-    weakref.finalize(out, lib.gen_free, ptr)
-    return out
+    try:
+        s = ptr.contents
+        n, m, nnz = int(s.n), int(s.m), int(s.nnz)
+        rowptr = np.ctypeslib.as_array(s.rowptr, shape=(n + 1,)).copy()
+        colidx = np.ctypeslib.as_array(s.colidx, shape=(max(nnz, 1),))[:nnz].copy()
+        values = np.ctypeslib.as_array(s.values, shape=(max(nnz, 1),))[:nnz].copy()
+    finally:
+        lib.gen_free(ptr)
+    return CSR(n, m, rowptr, colidx, values)
 
 
 def laplacian2d(nx: int, ny: int) -> CSR:
@@ -198,3 +199,82 @@ def raw_u64(n: int, seed: int, stream: int) -> np.ndarray:
 
 def splitmix_mix(z: int) -> int:
     return int(_load().gen_splitmix_mix(z))
+
+
+# ------------------------------------------------------------ timing corpus
+# Matrices for the block-shape selector: families stencil 2D / 3D, banded,
+# block-FEM, R-MAT and uniform in turn (index modulo 6), n log-uniform in
+# [1e4, 4e6], parameters drawn from the counter generator (stream 7000 under
+# the corpus seed). Training matrices are indices 0..1999 of seed 3, held-out
+# ones 2000..2299.
+CORPUS_FAMILIES = ("stencil2d", "stencil3d", "banded", "block_fem", "rmat", "uniform")
+_STREAM_CORPUS = 7000
+
+
+def corpus_params(index: int, seed: int = 3, n_min: float = 1e4, n_max: float = 4e6) -> dict:
+    d = raw_u64(8, seed=seed * 1_000_003 + index, stream=_STREAM_CORPUS)
+    u = (d >> np.uint64(11)).astype(np.float64) * 2.0**-53
+    n = int(round(np.exp(np.log(n_min) + u[0] * (np.log(n_max) - np.log(n_min)))))
+    fam = CORPUS_FAMILIES[index % len(CORPUS_FAMILIES)]
+    p = {"family": fam, "index": index, "seed": seed, "n_target": n, "values_seed": int(seed * 1_000_003 + index)}
+    if fam == "stencil2d":
+        side = max(8, int(round(np.sqrt(n))))
+        p.update(nx=side, ny=side)
+    elif fam == "stencil3d":
+        side = max(4, int(round(n ** (1.0 / 3.0))))
+        p.update(nx=side, ny=side, nz=side, points=7 if u[1] < 0.5 else 27)
+    elif fam == "banded":
+        p.update(n=n, half_bw=2 + int(u[1] * 63), density=0.05 + 0.9 * u[2])
+    elif fam == "block_fem":
+        bs = (2, 3, 4, 6)[int(u[1] * 4)]
+        bmin = 2 + int(u[2] * 11)
+        p.update(nb=max(16, n // bs), bs=bs, bmin=bmin, bmax=bmin + int(u[3] * 21), band_frac=0.001 + 0.099 * u[4])
+    elif fam == "rmat":
+        scale = int(min(22, max(13, round(np.log2(n)))))
+        a = 0.45 + 0.15 * u[1]
+        bc = (1.0 - a - 0.05) / 2.0
+        p.update(scale=scale, edge_factor=4 + int(u[2] * 21), a=a, b=bc, c=bc)
+    else:
+        p.update(n=n, per_row=2 + int(u[1] * 39))
+    return p
+
+
+def corpus_matrix(index: int, seed: int = 3, **kw) -> CSR:
+    p = corpus_params(index, seed, **kw)
+    f, vs = p["family"], p["values_seed"]
+    if f == "stencil2d":
+        return laplacian2d(p["nx"], p["ny"])
+    if f == "stencil3d":
+        return stencil3d(p["nx"], p["ny"], p["nz"], points=p["points"], normal_values=True, seed=vs)
+    if f == "banded":
+        return banded(p["n"], p["half_bw"], p["density"], seed=vs)
+    if f == "block_fem":
+        return block_fem(p["nb"], bs=p["bs"], bmin=p["bmin"], bmax=p["bmax"], band_frac=p["band_frac"], seed=vs)
+    if f == "rmat":
+        return rmat(p["scale"], p["edge_factor"], p["a"], p["b"], p["c"], relabel=True, seed=vs)
+    return uniform(p["n"], p["n"], p["per_row"], seed=vs)
+
+
+# ------------------------------------------------------------ batch corpus
+# Many uneven small matrices for the batched product: n lognormal (median
+# 8192, sigma 1) clipped to [1024, 65536], 3..60 entries per row; even indices
+# a stencil or banded pattern, odd indices uniform random columns.
+_STREAM_BATCH = 7100
+
+
+def batch_matrix(index: int, seed: int = 2) -> CSR:
+    d = raw_u64(6, seed=seed * 1_000_003 + index, stream=_STREAM_BATCH)
+    u = (d >> np.uint64(11)).astype(np.float64) * 2.0**-53
+    # standard normal from two uniforms (Box-Muller), for the lognormal size
+    z = np.sqrt(-2.0 * np.log(1.0 - u[0])) * np.cos(2.0 * np.pi * u[1])
+    n = int(min(65536, max(1024, round(8192.0 * np.exp(z)))))
+    per_row = 3 + int(u[2] * 58)
+    vs = int(seed * 1_000_003 + index)
+    if index % 2 == 0:
+        if u[3] < 0.5:
+            side = max(2, int(round(np.sqrt(n))))
+            return laplacian2d(side, max(1, n // side)) if per_row < 8 else \
+                stencil3d(max(2, round(n ** (1 / 3))), max(2, round(n ** (1 / 3))), max(2, round(n ** (1 / 3))),
+                          points=27 if per_row > 16 else 7, normal_values=True, seed=vs)
+        return banded(n, max(1, per_row // 2), min(0.95, per_row / (2.0 * max(1, per_row // 2) + 1)), seed=vs)
+    return uniform(n, n, per_row, seed=vs)

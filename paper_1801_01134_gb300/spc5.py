@@ -48,6 +48,15 @@ class CgInfo(ctypes.Structure):
                 ("converged", ctypes.c_int32), ("rel_residual", ctypes.c_double)]
 
 
+NFEATURES, NFORMATS = 16, 12
+SELECT_EXHAUSTIVE, SELECT_POLY, SELECT_MLP = 0, 1, 2
+
+
+class Selector(ctypes.Structure):
+    _fields_ = [("poly_degree", ctypes.c_int32), ("poly_coef", ctypes.c_void_p), ("mlp_params_d", ctypes.c_void_p),
+                ("feat_mean", ctypes.c_float * NFEATURES), ("feat_scale", ctypes.c_float * NFEATURES)]
+
+
 class Arrays(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("m", ctypes.c_int64), ("nnz", ctypes.c_int64), ("nblocks", ctypes.c_int64),
                 ("nintervals", ctypes.c_int64), ("r", ctypes.c_int32), ("c", ctypes.c_int32),
@@ -90,8 +99,24 @@ def load(build_if_missing: bool = False):
     lib.spc5_spmv_noalloc.argtypes = [vp, vp, vp, vp]
     lib.spc5_cg.argtypes = [vp, vp, vp, vp, ctypes.POINTER(CgOpts), ctypes.POINTER(CgInfo), vp]
     lib.spc5_spmm.argtypes = [vp, i32, vp, i64, vp, i64, i32, vp]
+    lib.spc5_features.argtypes = [i64, i64, i64, vp, vp, vp, vp]
+    lib.spc5_batch_create.argtypes = [vp, vp, vp, i32, ctypes.POINTER(vp)]
+    lib.spc5_batch_spmv.argtypes = [vp, vp]
+    lib.spc5_batch_spmv_direct.argtypes = [vp, vp]
+    lib.spc5_batch_destroy.argtypes = [vp]
+    lib.spc5_time_formats.argtypes = [i64, i64, i64, vp, vp, vp, i32, vp, vp, i32, vp, vp]
+    lib.spc5_mlp_nparams.argtypes = []
+    lib.spc5_mlp_nparams.restype = i32
+    lib.spc5_mlp_train.argtypes = [vp, vp, vp, vp, i32, i32, i32, ctypes.c_float, ctypes.c_uint64, vp, vp]
+    lib.spc5_mlp_grad.argtypes = [vp, vp, vp, vp, i32, vp, vp, vp]
+    lib.spc5_mlp_infer.argtypes = [vp, vp, i32, vp, vp]
+    lib.spc5_poly_fit.argtypes = [vp, vp, i32, i32, vp]
+    lib.spc5_select.argtypes = [i64, i64, i64, vp, vp, vp, i32, i32, ctypes.POINTER(Selector), vp, vp, vp, vp]
     for f in (lib.spc5_convert, lib.spc5_spmv, lib.spc5_spmv_acc, lib.spc5_export, lib.spc5_destroy, lib.spc5_set_variant,
-              lib.spc5_count_blocks, lib.spc5_csr_spmv, lib.spc5_copy, lib.spc5_fma_rate, lib.spc5_spmv_noalloc, lib.spc5_cg, lib.spc5_spmm):
+              lib.spc5_count_blocks, lib.spc5_csr_spmv, lib.spc5_copy, lib.spc5_fma_rate, lib.spc5_spmv_noalloc, lib.spc5_cg, lib.spc5_spmm, lib.spc5_features,
+              lib.spc5_time_formats, lib.spc5_mlp_train, lib.spc5_mlp_grad, lib.spc5_mlp_infer, lib.spc5_poly_fit,
+              lib.spc5_select, lib.spc5_batch_create, lib.spc5_batch_spmv, lib.spc5_batch_spmv_direct,
+              lib.spc5_batch_destroy):
         f.restype = st
     _lib = lib
     return lib
@@ -282,6 +307,117 @@ def cg(A: Matrix, b: torch.Tensor, A_inner: Matrix | None = None, x: torch.Tenso
                           ctypes.byref(info), _stream_ptr(stream)), "spc5_cg")
     return x, {"iterations": info.iterations, "outer": info.outer, "inner_total": info.inner_total,
                "converged": bool(info.converged), "rel_residual": info.rel_residual}
+
+
+def features(d: "DeviceCSR", stream=None) -> np.ndarray:
+    """The 16 selection features of a device CSR (no conversion)."""
+    out = np.zeros(NFEATURES, dtype=np.float64)
+    _check(load().spc5_features(d.n, d.m, d.nnz, _ptr(d.rowptr), _ptr(d.colidx), out.ctypes.data,
+                                _stream_ptr(stream)), "spc5_features")
+    return out
+
+
+def time_formats(d: "DeviceCSR", reps: int = 5, stream=None) -> np.ndarray:
+    """Median SpMV milliseconds for the twelve shapes (the timing recorder)."""
+    vt = _VALUE_DTYPE[d.values.dtype]
+    xdt = _VECTOR_DTYPE[vt]
+    x = torch.rand(d.m, dtype=xdt, device=d.values.device)
+    y = torch.empty(d.n, dtype=xdt, device=d.values.device)
+    out = np.zeros(NFORMATS, dtype=np.float32)
+    _check(load().spc5_time_formats(d.n, d.m, d.nnz, _ptr(d.rowptr), _ptr(d.colidx), _ptr(d.values), vt, _ptr(x),
+                                    _ptr(y), reps, out.ctypes.data, _stream_ptr(stream)), "spc5_time_formats")
+    return out
+
+
+def mlp_nparams() -> int:
+    return int(load().spc5_mlp_nparams())
+
+
+def mlp_train(params: torch.Tensor, X: torch.Tensor, Y: torch.Tensor, M: torch.Tensor, epochs: int, batch: int = 32,
+              lr: float = 1e-3, seed: int = 0, stream=None) -> np.ndarray:
+    """Train the format-scoring MLP in place on the GPU; returns the per-epoch mean loss."""
+    hist = np.zeros(max(epochs, 1), dtype=np.float32)
+    _check(load().spc5_mlp_train(_ptr(params), _ptr(X), _ptr(Y), _ptr(M), X.shape[0], epochs, batch, lr, seed,
+                                 hist.ctypes.data, _stream_ptr(stream)), "spc5_mlp_train")
+    return hist[:epochs]
+
+
+def mlp_grad(params: torch.Tensor, X: torch.Tensor, Y: torch.Tensor, M: torch.Tensor, stream=None):
+    """(loss, gradient) of the first X.shape[0] <= 32 samples."""
+    g = torch.empty(mlp_nparams(), dtype=torch.float32, device=params.device)
+    loss = ctypes.c_float()
+    _check(load().spc5_mlp_grad(_ptr(params), _ptr(X), _ptr(Y), _ptr(M), X.shape[0], ctypes.byref(loss), _ptr(g),
+                                _stream_ptr(stream)), "spc5_mlp_grad")
+    return float(loss.value), g
+
+
+def mlp_infer(params: torch.Tensor, X: torch.Tensor, stream=None) -> torch.Tensor:
+    out = torch.empty(X.shape[0], NFORMATS, dtype=torch.float32, device=params.device)
+    _check(load().spc5_mlp_infer(_ptr(params), _ptr(X), X.shape[0], _ptr(out), _stream_ptr(stream)), "spc5_mlp_infer")
+    return out
+
+
+def poly_fit(avg: np.ndarray, perf: np.ndarray, degree: int) -> np.ndarray:
+    """Per-format least-squares polynomial coefficients, shape (12, degree + 1)."""
+    avg = np.ascontiguousarray(avg, dtype=np.float64)
+    perf = np.ascontiguousarray(perf, dtype=np.float64)
+    coef = np.zeros((NFORMATS, degree + 1), dtype=np.float64)
+    _check(load().spc5_poly_fit(avg.ctypes.data, perf.ctypes.data, avg.shape[0], degree, coef.ctypes.data),
+           "spc5_poly_fit")
+    return coef
+
+
+def select(d: "DeviceCSR", method: int, poly_coef: np.ndarray | None = None, mlp_params: torch.Tensor | None = None,
+           feat_mean=None, feat_scale=None, stream=None):
+    """Pick (r, c) for a device CSR; returns (r, c, per-format scores)."""
+    sel = Selector()
+    coef = None
+    if poly_coef is not None:
+        coef = np.ascontiguousarray(poly_coef, dtype=np.float64)
+        sel.poly_degree = coef.shape[1] - 1
+        sel.poly_coef = coef.ctypes.data
+    if mlp_params is not None:
+        sel.mlp_params_d = _ptr(mlp_params)
+    if feat_mean is not None:
+        for q in range(NFEATURES):
+            sel.feat_mean[q] = float(feat_mean[q])
+            sel.feat_scale[q] = float(feat_scale[q])
+    r, c = ctypes.c_int(), ctypes.c_int()
+    score = np.zeros(NFORMATS, dtype=np.float32)
+    vt = _VALUE_DTYPE[d.values.dtype]
+    _check(load().spc5_select(d.n, d.m, d.nnz, _ptr(d.rowptr), _ptr(d.colidx), _ptr(d.values), vt, method,
+                              ctypes.byref(sel), ctypes.byref(r), ctypes.byref(c), score.ctypes.data,
+                              _stream_ptr(stream)), "spc5_select")
+    return r.value, c.value, score
+
+
+class Batch:
+    """y_j = A_j x_j for many matrices in one persistent, graph-replayed launch."""
+
+    def __init__(self, mats: list, xs: list, ys: list):
+        n = len(mats)
+        H = (ctypes.c_void_p * n)(*[m._h for m in mats])
+        X = (ctypes.c_void_p * n)(*[_ptr(x) for x in xs])
+        Y = (ctypes.c_void_p * n)(*[_ptr(y) for y in ys])
+        b = ctypes.c_void_p()
+        _check(load().spc5_batch_create(H, X, Y, n, ctypes.byref(b)), "spc5_batch_create")
+        self._b = b.value
+        self._keep = (list(mats), list(xs), list(ys))  # the batch refers to them
+
+    def run(self, graph: bool = True, stream=None):
+        f = load().spc5_batch_spmv if graph else load().spc5_batch_spmv_direct
+        _check(f(self._b, _stream_ptr(stream)), "spc5_batch_spmv")
+
+    def destroy(self):
+        if self._b is not None:
+            load().spc5_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
 
 
 def fma_rate(dtype: torch.dtype = torch.float64, iters: int = 4096, reps: int = 5) -> float:
