@@ -85,7 +85,8 @@ def profile_matrices():
     return [("stencil27_96^3", lambda: inputs.stencil3d(96, 96, 96, points=27, seed=1)),
             ("fem3x3_n1M", lambda: inputs.block_fem(333334, bs=3, bmin=9, bmax=27, band_frac=0.05, seed=1)),
             ("rmat_s20", lambda: inputs.rmat(20, 16, 0.57, 0.19, 0.19, relabel=True, seed=1)),
-            ("uniform_n1M", lambda: inputs.uniform(1000000, 1000000, 8, seed=1))]
+            ("uniform_n1M", lambda: inputs.uniform(1000000, 1000000, 8, seed=1)),
+            ("poisson7_96^3", lambda: inputs.stencil3d(96, 96, 96, points=7, normal_values=False))]
 
 
 def kernel_source_hash() -> str:

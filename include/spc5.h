@@ -239,7 +239,10 @@ typedef struct {
   double tol;              /* stop when ||b - A x||_2 <= tol ||b||_2              [1e-10] */
   int32_t max_iters;       /* CG iterations in total (inner ones when mixed)      [100000] */
   int32_t max_outer;       /* refinement steps of the mixed solver                [30] */
-  double inner_tol;        /* relative residual reduction of each inner solve     [1e-6] */
+  double inner_tol;        /* tightest relative reduction asked of an inner solve;
+                              each inner solve stops at max(inner_tol,
+                              0.5 tol ||b|| / ||r||) (no further than the final
+                              tolerance needs)                                  [1e-6] */
   int32_t inner_max_iters; /* iterations of one inner solve                       [2000] */
   int32_t check_every;     /* iterations before the first host read of the residual
                               norm; later reads are placed where the observed

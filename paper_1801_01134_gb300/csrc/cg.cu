@@ -488,6 +488,7 @@ spc5_status cg_impl(const spc5_matrix* A, const spc5_matrix* L, const double* b,
       if (e != cudaSuccess) return cuda_fail(e, "cg: residual norm");
       if (!(sqrt(hs[S_NORM]) > stop)) break;
       if (info->inner_total >= max_it) break;
+      const double hs_norm = hs[S_NORM];
       // inner CG in float32 on A_low d = r / ||r||, from d = 0
       k_inner_start<<<nb, kThreads, 0, s>>>(r, r32, p32, x32, n, scal);
       k_dot_part<float, float><<<nb, kThreads, 0, s>>>(r32, r32, n, part32);
@@ -497,8 +498,14 @@ spc5_status cg_impl(const spc5_matrix* A, const spc5_matrix* L, const double* b,
       if (e != cudaSuccess) return cuda_fail(e, "cg: inner start");
       int it = 0;
       const int budget = inner_max < max_it - info->inner_total ? inner_max : max_it - info->inner_total;
-      st = cg_loop<float, float>(L, x32, r32, p32, q32, n, scal, part32, nb, ticket, inner_tol * sqrt(hs[S_RHO]),
-                                 budget, every, use_graph, hs, s, &it);
+      // solve only as far as the final tolerance needs: a relative reduction of
+      // half of tol * ||b|| / ||r||, but never looser than inner_tol allows
+      // from below (float32 cannot reach much further than about 1e-6)
+      double itol = 0.5 * stop / sqrt(hs_norm);
+      if (itol < inner_tol) itol = inner_tol;
+      if (itol > 0.5) itol = 0.5;
+      st = cg_loop<float, float>(L, x32, r32, p32, q32, n, scal, part32, nb, ticket, itol * sqrt(hs[S_RHO]), budget,
+                                 every, use_graph, hs, s, &it);
       if (st != SPC5_OK) return st;
       info->inner_total += it;
       // x += ||r|| d; r = b - A x in float64
