@@ -54,6 +54,10 @@ def parse():
     p.add_argument("--dtype", default="f64", choices=["f64", "f32", "bf16"], help="profiling run value type")
     p.add_argument("--reps", type=int, default=3)
     p.add_argument("--variants", default="0", help="profiling run: comma list of kernel variants (0 = default)")
+    p.add_argument("--order-window", type=int, default=0, help="profiling run: rows per work-order window "
+                   "(0 = library default, negative = one window)")
+    p.add_argument("--seg-blocks", type=int, default=0, help="profiling run: blocks per long-interval segment")
+    p.add_argument("--long-blocks", type=int, default=0, help="profiling run: long-interval threshold in blocks")
     p.add_argument("--cg-profile", action="store_true", help="run the CG solvers once each with timings")
     p.add_argument("--cg-n", type=int, default=96, help="grid edge of the CG profiling matrix")
     p.add_argument("--cg-every", type=int, default=8)
@@ -441,10 +445,13 @@ def run_profile(args):
                 fmt = f"csr group={variant}"
             else:
                 r, c = (int(v) for v in shape.split("x"))
-                M = spc5.convert(d.rowptr, d.colidx, d.values, A.n, A.m, r, c, variant=variant)
+                M = spc5.convert(d.rowptr, d.colidx, d.values, A.n, A.m, r, c, variant=variant,
+                                 order_window=args.order_window, seg_blocks=args.seg_blocks,
+                                 long_blocks=args.long_blocks)
                 run = lambda: M.spmv(x, y)  # noqa: E731
-                ex = M.export()
-                fmt = f"beta({r},{c}) variant={variant} nblocks={ex['nblocks']} segments={ex['nsegments']}"
+                ar = M.arrays()
+                fmt = (f"beta({r},{c}) variant={variant} nblocks={ar.nblocks} segments={ar.nsegments}"
+                       f" order_window={args.order_window} seg_blocks={args.seg_blocks} long_blocks={args.long_blocks}")
             ts = []
             for _ in range(args.reps):
                 spc5.copy(fa, fb)

@@ -70,9 +70,17 @@ typedef struct {
    *   9 / 10  intervals taken in a work order sorted by row length inside
    *           windows of 4096 rows (2 / 4 nonzeros per trip); the order is
    *           built at conversion.
+   *   12 / 14 natural order, block masks read as 8-byte windows of 8/mb
+   *           blocks (no memory round trip per block; for low fill),
+   *           4 / 2 nonzeros per trip;
+   *   13 / 15 sorted work order with mask windows, 4 / 2 nonzeros per trip.
    * All variants compute the same sums in the same order per row. */
   int32_t variant;
-  int32_t reserved[5];
+  /* Rows per sorting window of the work order of variants 9, 10, 13, 15:
+   * 0 selects 4096; a negative value sorts all intervals together (heaviest
+   * warps first, for heavy-tailed row lengths). */
+  int32_t order_window;
+  int32_t reserved[4];
 } spc5_opts;
 
 /* Read-only device views of a handle's arrays (layout of Eq. 1 plus derived

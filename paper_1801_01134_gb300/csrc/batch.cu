@@ -9,7 +9,8 @@
 // balance themselves. Each matrix keeps its own block shape (a run-time
 // argument here), chosen per matrix by the caller's tuner or selector. Long
 // intervals are items of a second kind - one warp per segment, partials into
-// the matrix's scratch - followed by one fix-up kernel over all segments.
+// the matrix's scratch - followed by one fix-up kernel over the long
+// intervals.
 // The counter reset, the persistent kernel and the fix-up are captured once
 // into a CUDA graph at batch creation; a batched SpMV is one graph launch.
 #include <vector>
@@ -119,33 +120,42 @@ __global__ void __launch_bounds__(256) k_batch(const MatDesc* __restrict__ mats,
       const int64_t row = it * r + i;
       if (row < d.n) static_cast<X*>(d.y)[row] = acc;
     } else {
-      // one warp per segment, lane = (block slot, row), as k_spmv_segments
+      // one warp per segment, cut into 32/r contiguous runs, lane = (run,
+      // row), the same sums in the same order as k_spmv_segments
       const Segment sg = d.segs[itm.i0];
       const int S = kWarp >> d.log2r;
       const int slot = lane >> d.log2r, i = lane & (r - 1);
-      int64_t vbase = sg.v_begin;
+      const int32_t per = (sg.b_end - sg.b_begin + S - 1) / S;
+      const int32_t rb0 = min(sg.b_begin + slot * per, sg.b_end);
+      const int32_t re = min(rb0 + per, sg.b_end);
+      int cnt = 0;
+      for (int32_t b = rb0 + i; b < re; b += r) {
+        uint32_t w[4];
+        ldmask(d.bmask, b, mb, w);
+        cnt += __popc(w[0]) + __popc(w[1]) + __popc(w[2]) + __popc(w[3]);
+      }
+      for (int dd = 1; dd < r; dd <<= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, dd);
+      int incl = cnt;
+      for (int dd = r; dd < kWarp; dd <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, dd);
+        if (lane >= dd) incl += t;
+      }
+      const V* __restrict__ vrun = val + sg.v_begin + (incl - cnt);
       A acc = 0;
-      for (int32_t b0 = sg.b_begin; b0 < sg.b_end; b0 += S) {
-        const int32_t b = b0 + slot;
-        const bool valid = b < sg.b_end;
-        uint32_t w[4] = {0u, 0u, 0u, 0u};
-        if (valid) ldmask(d.bmask, b, mb, w);
-        const int cnt = __popc(w[0]) + __popc(w[1]) + __popc(w[2]) + __popc(w[3]);
-        int incl = cnt;
-        for (int dd = r; dd < kWarp; dd <<= 1) {
-          const int t = __shfl_up_sync(0xffffffffu, incl, dd);
-          if (lane >= dd) incl += t;
-        }
-        const int total = __shfl_sync(0xffffffffu, incl, kWarp - 1);
-        int64_t vo = vbase + (incl - cnt) + (valid ? pb(w, i * c) : 0);
-        uint32_t bits = valid ? rb(w, i * c, c) : 0u;
-        const int64_t col0 = valid ? __ldg(d.bcol + b) : 0;
+      int32_t vbase = 0;
+      for (int32_t b = rb0; b < re; ++b) {
+        uint32_t w[4];
+        ldmask(d.bmask, b, mb, w);
+        uint32_t bits = rb(w, i * c, c);
+        int32_t vo = vbase + pb(w, i * c);
+        vbase += __popc(w[0]) + __popc(w[1]) + __popc(w[2]) + __popc(w[3]);
+        if (!bits) continue;
+        const int64_t col0 = __ldg(d.bcol + b);
         while (bits) {
           const int kb = __ffs(bits) - 1;
           bits &= bits - 1;
-          acc = fma(T::val(val, vo++), T::xv(x, col0 + kb), acc);
+          acc = fma(T::val(vrun, vo++), T::xv(x, col0 + kb), acc);
         }
-        vbase += total;
       }
       for (int dd = kWarp / 2; dd >= r; dd >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, dd);
       if (lane < r) static_cast<A*>(d.partials)[(int64_t)itm.i0 * r + lane] = acc;
@@ -153,25 +163,31 @@ __global__ void __launch_bounds__(256) k_batch(const MatDesc* __restrict__ mats,
   }
 }
 
-// one thread per (matrix, segment, row): the first segment of each long
-// interval adds its interval's partials in order
+// one lane per long interval (matrix, first segment), long lists by the whole
+// warp: the summation order of k_spmv_fixup
 template <class T>
-__global__ void k_batch_fixup(const MatDesc* __restrict__ mats, const int2* __restrict__ segrows, int64_t nrows) {
+__global__ void __launch_bounds__(256) k_batch_fixup(const MatDesc* __restrict__ mats, const int2* __restrict__ firsts,
+                                                     int64_t nfirst) {
   using X = typename T::X;
   using A = typename T::A;
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= nrows) return;
-  const int2 e = segrows[t];  // (matrix, segment * r + row)
-  const MatDesc& d = mats[e.x];
-  const int64_t seg = e.y / d.r;
-  const int i = e.y % d.r;
-  const int32_t it = d.segs[seg].interval;
-  if (seg > 0 && d.segs[seg - 1].interval == it) return;
-  const A* part = static_cast<const A*>(d.partials);
-  A s = 0;
-  for (int64_t q = seg; q < d.nseg && d.segs[q].interval == it; ++q) s += part[q * d.r + i];
-  const int64_t row = (int64_t)it * d.r + i;
-  if (row < d.n) static_cast<X*>(d.y)[row] = s;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (((int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31)) >= nfirst) return;  // whole warp
+  const bool have = e < nfirst;
+  const int2 f = have ? firsts[e] : make_int2(0, 0);  // (matrix, first segment of the interval)
+  const MatDesc& d = mats[f.x];
+  const int32_t count = have ? d.segs[f.y].count : 0;
+  const int32_t it = have ? d.segs[f.y].interval : 0;
+  fixup_lane_interval<A, X, false>(have, f.y, count, it, d.r, d.n, static_cast<const A*>(d.partials),
+                                   static_cast<X*>(d.y));
+  unsigned big = __ballot_sync(0xffffffffu, have && count > kFixupSerial);
+  while (big) {
+    const int src = __ffs(big) - 1;
+    big &= big - 1;
+    const MatDesc& db = mats[__shfl_sync(0xffffffffu, f.x, src)];
+    fixup_warp_interval<A, X, false>(__shfl_sync(0xffffffffu, f.y, src), __shfl_sync(0xffffffffu, count, src),
+                                     __shfl_sync(0xffffffffu, it, src), db.r, db.n,
+                                     static_cast<const A*>(db.partials), static_cast<X*>(db.y));
+  }
 }
 
 }  // namespace
@@ -180,10 +196,10 @@ __global__ void k_batch_fixup(const MatDesc* __restrict__ mats, const int2* __re
 struct spc5_batch_s {
   spc5_dtype vt = SPC5_F32;
   int count = 0;
-  int64_t nitems = 0, nsegrows = 0;
+  int64_t nitems = 0, nfirst = 0;
   spc5::MatDesc* mats_d = nullptr;
   spc5::Item* items_d = nullptr;
-  int2* segrows_d = nullptr;
+  int2* firsts_d = nullptr;  // (matrix, first segment) of every long interval
   unsigned long long* counter_d = nullptr;
   cudaGraphExec_t exec = nullptr;
   int blocks = 0;
@@ -196,7 +212,7 @@ static void batch_free(spc5_batch_s* b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   cudaFree(b->mats_d);
   cudaFree(b->items_d);
-  cudaFree(b->segrows_d);
+  cudaFree(b->firsts_d);
   cudaFree(b->counter_d);
   delete b;
 }
@@ -206,8 +222,8 @@ cudaError_t batch_enqueue(spc5_batch_s* b, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(b->counter_d, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
   if (b->nitems > 0) k_batch<T><<<b->blocks, 256, 0, s>>>(b->mats_d, b->items_d, b->nitems, b->counter_d);
-  if (b->nsegrows > 0)
-    k_batch_fixup<T><<<(unsigned)((b->nsegrows + 255) / 256), 256, 0, s>>>(b->mats_d, b->segrows_d, b->nsegrows);
+  if (b->nfirst > 0)
+    k_batch_fixup<T><<<(unsigned)((b->nfirst + 255) / 256), 256, 0, s>>>(b->mats_d, b->firsts_d, b->nfirst);
   return cudaGetLastError();
 }
 
@@ -226,7 +242,8 @@ spc5_status batch_create_impl(const spc5_handle* mats, const void* const* xs, vo
   b->vt = mats[0]->vt;
   std::vector<MatDesc> md((size_t)count);
   std::vector<Item> items;
-  std::vector<int2> segrows;
+  std::vector<int2> firsts;
+  std::vector<Segment> hsegs;
   for (int j = 0; j < count; ++j) {
     const spc5_matrix* h = mats[j];
     if (h->vt != b->vt) {
@@ -255,22 +272,29 @@ spc5_status batch_create_impl(const spc5_handle* mats, const void* const* xs, vo
     d.pad = 0;
     const int S = kWarp / h->r;
     for (int64_t i0 = 0; i0 < h->I; i0 += S) items.push_back(Item{j, (int32_t)i0, 0, 0});
-    for (int64_t q = 0; q < h->nseg; ++q) {
-      items.push_back(Item{j, (int32_t)q, 1, 0});
-      for (int i = 0; i < h->r; ++i) segrows.push_back(make_int2(j, (int)(q * h->r + i)));
+    if (h->nseg > 0) {
+      hsegs.resize((size_t)h->nseg);
+      cudaError_t e = cudaMemcpy(hsegs.data(), h->segs, sizeof(Segment) * (size_t)h->nseg, cudaMemcpyDeviceToHost);
+      if (e != cudaSuccess) {
+        batch_free(b);
+        return cuda_fail(e, "batch: segment table");
+      }
     }
+    for (int64_t q = 0; q < h->nseg; ++q) items.push_back(Item{j, (int32_t)q, 1, 0});
+    for (int64_t q = 0; q < h->nseg; ++q)
+      if (hsegs[(size_t)q].count > 0) firsts.push_back(make_int2(j, (int)q));
   }
   b->nitems = (int64_t)items.size();
-  b->nsegrows = (int64_t)segrows.size();
+  b->nfirst = (int64_t)firsts.size();
   cudaError_t e = cudaMalloc((void**)&b->mats_d, sizeof(MatDesc) * (size_t)count);
   if (e == cudaSuccess) e = cudaMalloc((void**)&b->items_d, sizeof(Item) * (items.size() + 1));
-  if (e == cudaSuccess) e = cudaMalloc((void**)&b->segrows_d, sizeof(int2) * (segrows.size() + 1));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->firsts_d, sizeof(int2) * (firsts.size() + 1));
   if (e == cudaSuccess) e = cudaMalloc((void**)&b->counter_d, sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMemcpy(b->mats_d, md.data(), sizeof(MatDesc) * (size_t)count, cudaMemcpyHostToDevice);
   if (e == cudaSuccess && !items.empty())
     e = cudaMemcpy(b->items_d, items.data(), sizeof(Item) * items.size(), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess && !segrows.empty())
-    e = cudaMemcpy(b->segrows_d, segrows.data(), sizeof(int2) * segrows.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !firsts.empty())
+    e = cudaMemcpy(b->firsts_d, firsts.data(), sizeof(int2) * firsts.size(), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
     batch_free(b);
     return cuda_fail(e, "batch: descriptors");

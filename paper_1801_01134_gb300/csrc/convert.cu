@@ -118,6 +118,17 @@ __global__ void k_nseg(int64_t n, int64_t I, int r, int long_blocks, int64_t lon
   nseg[it] = lng ? (nb + seg_blocks - 1) / seg_blocks : 0;
 }
 
+__global__ void k_long_flags(int64_t I, const int32_t* __restrict__ segptr, int32_t* __restrict__ flag) {
+  const int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (it < I) flag[it] = segptr[it + 1] > segptr[it] ? 1 : 0;
+}
+
+__global__ void k_seg_first(int64_t I, const int32_t* __restrict__ segptr, const int32_t* __restrict__ flag,
+                            const int32_t* __restrict__ pos, int32_t* __restrict__ first) {
+  const int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (it < I && flag[it]) first[pos[it]] = segptr[it];
+}
+
 template <int R, class VT>
 __global__ void k_fill(int64_t n, int64_t I, int c, int mb, int seg_blocks, const int64_t* __restrict__ rowptr,
                        const int32_t* __restrict__ colidx, const VT* __restrict__ values,
@@ -140,7 +151,7 @@ __global__ void k_fill(int64_t n, int64_t I, int c, int mb, int seg_blocks, cons
       sg.interval = (int32_t)it;
       sg.b_begin = b;
       sg.b_end = min(b + seg_blocks, bend);
-      sg.pad = 0;
+      sg.count = j == 0 ? (bend - b0 + seg_blocks - 1) / seg_blocks : 0;
       sg.v_begin = vo;
       segs[seg0 + j / seg_blocks] = sg;
     }
@@ -315,6 +326,7 @@ void free_matrix(spc5_matrix* h) {
   cudaFree(h->values);
   cudaFree(h->valptr);
   cudaFree(h->segs);
+  cudaFree(h->seg_first);
   cudaFree(h->partials);
   delete h;
 }
@@ -371,11 +383,15 @@ void launch_order_key(int c, const spc5_matrix* h, int32_t* key, cudaStream_t s)
 
 }  // namespace
 
-// Work order of the lane-per-row kernel (variants 9 and 10): the short
+// Work order of the lane-per-row kernel (variants 9, 10, 13, 15): the short
 // intervals, sorted by their longest row (descending, stable) inside windows
-// of kOrderWindow rows, so that the 32/r intervals of one warp have rows of
-// similar length and the warp's multiply-adds are fully packed. The storage
-// is untouched; only the assignment of intervals to lanes changes.
+// of order_window rows (all intervals together when order_window <= 0), so
+// that the 32/r intervals of one warp have rows of similar length and the
+// warp's multiply-adds are fully packed. Small windows keep the rows that
+// neighbouring warps read close together in memory (measured: one global
+// sort, or handing whole thread blocks out heaviest first, is slower on
+// power-law graphs than 4096-row windows). The storage is untouched; only the
+// assignment of intervals to lanes changes.
 spc5_status build_order(spc5_matrix* h, cudaStream_t s) {
   if (h->order || h->I == 0) return SPC5_OK;
   const int64_t I = h->I;
@@ -396,7 +412,7 @@ spc5_status build_order(spc5_matrix* h, cudaStream_t s) {
   std::vector<int32_t> order;
   order.reserve((size_t)I);
   std::vector<std::pair<int32_t, int32_t>> win;
-  const int64_t wiv = kOrderWindow / h->r;
+  const int64_t wiv = h->order_window > 0 ? (h->order_window + h->r - 1) / h->r : I;
   for (int64_t w0 = 0; w0 < I; w0 += wiv) {
     const int64_t w1 = w0 + wiv < I ? w0 + wiv : I;
     win.clear();
@@ -442,6 +458,7 @@ spc5_status convert_impl(int64_t n, int64_t m, int64_t nnz, const int64_t* rowpt
     user_long = opt->long_blocks;
     if (opt->seg_blocks > 0) h->seg_blocks = opt->seg_blocks;
     h->variant = opt->variant;
+    if (opt->order_window != 0) h->order_window = opt->order_window;
   }
   const int64_t I = h->I;
   cudaError_t e;
@@ -530,7 +547,25 @@ spc5_status convert_impl(int64_t n, int64_t m, int64_t nnz, const int64_t* rowpt
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return bail(cuda_fail(e, "convert: fill"));
 
-  if (h->variant == 9 || h->variant == 10) {
+  // 5. first segment of every long interval, in interval order (the fix-up's work list)
+  if (ns > 0) {
+    int32_t* flag = (int32_t*)counts.p;  // free after the fill
+    int32_t* pos = (int32_t*)nseg.p;
+    k_long_flags<<<(unsigned)((I + 255) / 256), 256, 0, s>>>(I, sp, flag);
+    int64_t nlong = 0;
+    st = scan_counts(flag, I, pos, &nlong, s);
+    if (st != SPC5_OK) return bail(st);
+    e = alloc_padded((void**)&h->seg_first, sizeof(int32_t) * (size_t)nlong, s);
+    if (e == cudaSuccess) {
+      k_seg_first<<<(unsigned)((I + 255) / 256), 256, 0, s>>>(I, sp, flag, pos, h->seg_first);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "convert: long-interval list"));
+    h->nlong = nlong;
+  }
+
+  if (ordered_variant(h->variant)) {
     spc5_status st2 = build_order(h, s);
     if (st2 != SPC5_OK) return bail(st2);
   }

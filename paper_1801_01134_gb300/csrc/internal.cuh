@@ -20,11 +20,18 @@ constexpr int kWarp = 32;
 
 constexpr int kOrderWindow = 4096;  // rows per sorting window of the work order
 
+// short-interval kernel variants (spc5_opts.variant)
+inline bool valid_variant(int v) {
+  return v == 0 || v == 1 || v == 3 || v == 5 || v == 9 || v == 10 || (v >= 12 && v <= 15);
+}
+// variants that take intervals in the sorted work order
+inline bool ordered_variant(int v) { return v == 9 || v == 10 || v == 13 || v == 15; }
+
 struct Segment {  // one warp task of a long interval
   int32_t interval;
   int32_t b_begin;
   int32_t b_end;
-  int32_t pad;
+  int32_t count;    // segments of the interval, in its first segment; 0 in the others
   int64_t v_begin;  // value offset of block b_begin
 };
 static_assert(sizeof(Segment) == 24, "segment layout");
@@ -49,6 +56,8 @@ struct spc5_matrix {
   int32_t variant = 0;
   int64_t nseg = 0;
   spc5::Segment* segs = nullptr;    // [nseg]
+  int64_t nlong = 0;                // long intervals
+  int32_t* seg_first = nullptr;     // [nlong] first segment of each long interval
   void* partials = nullptr;         // [nseg * r] accumulation-type scratch
   // SpMM segment partials, grown on demand
   void* spmm_scratch = nullptr;
@@ -56,6 +65,7 @@ struct spc5_matrix {
   // work order of the lane-per-row kernel (short intervals only)
   int64_t norder = 0;
   int32_t* order = nullptr;            // [norder] interval indices
+  int32_t order_window = spc5::kOrderWindow;  // rows per sorting window; <= 0: all intervals
 };
 
 namespace spc5 {
@@ -80,9 +90,12 @@ spc5_status count_blocks_impl(int64_t n, int64_t nnz, const int64_t* rowptr, con
                               int64_t* nblocks_out, cudaStream_t s);
 
 // SpMV launchers, one per value type (spmv_f64.cu, spmv_f32.cu, spmv_bf16.cu)
-cudaError_t launch_spmv_f64(const spc5_matrix* h, const void* x, void* y, bool acc, cudaStream_t s);
-cudaError_t launch_spmv_f32(const spc5_matrix* h, const void* x, void* y, bool acc, cudaStream_t s);
-cudaError_t launch_spmv_bf16(const spc5_matrix* h, const void* x, void* y, bool acc, cudaStream_t s);
+cudaError_t launch_spmv_f64(const spc5_matrix* h, const void* x, void* y, bool acc, cudaStream_t s,
+                            void* partials = nullptr);
+cudaError_t launch_spmv_f32(const spc5_matrix* h, const void* x, void* y, bool acc, cudaStream_t s,
+                            void* partials = nullptr);
+cudaError_t launch_spmv_bf16(const spc5_matrix* h, const void* x, void* y, bool acc, cudaStream_t s,
+                            void* partials = nullptr);
 
 // CSR comparator and copy (csr.cu)
 cudaError_t launch_csr_spmv(int64_t n, int64_t nnz, const int64_t* rowptr, const int32_t* colidx,

@@ -234,10 +234,11 @@ __global__ void k_spmm_fixup(int64_t n, int64_t nseg, int r, const Segment* __re
   const int rem = (int)(t % ((int64_t)r * k));
   const int i = rem / k, j = rem % k;
   if (seg >= nseg) return;
+  const int32_t count = segs[seg].count;  // segments of the interval, in its first segment only
+  if (count == 0) return;
   const int32_t it = segs[seg].interval;
-  if (seg > 0 && segs[seg - 1].interval == it) return;
   typename T::A s = 0;
-  for (int64_t q = seg; q < nseg && segs[q].interval == it; ++q) s += part[(q * r + i) * (int64_t)k + j];
+  for (int32_t q = 0; q < count; ++q) s += part[((seg + q) * r + i) * (int64_t)k + j];
   const int64_t row = (int64_t)it * r + i;
   if (row < n) Y[row * ldy + j] = s;
 }

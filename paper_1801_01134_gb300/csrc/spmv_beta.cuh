@@ -17,10 +17,14 @@
 //     instruction slot however many lanes are active, which makes this
 //     packing the bound for float64.
 //   * long intervals: split into segments of seg_blocks blocks (built at
-//     conversion); a warp per segment, lane = (block slot, row), 32/r blocks
-//     per step; per-step value offsets come from a shuffle scan of the block
-//     popcounts. Each segment leaves r partial sums; a fix-up kernel adds the
-//     segments of one interval in order (deterministic) and writes y.
+//     conversion); a warp per segment, the segment cut into 32/r contiguous
+//     runs of blocks, lane = (run, row); run value offsets come from a
+//     shuffle scan of the runs' popcounts. Each segment leaves r partial
+//     sums; a fix-up kernel adds the segments of one interval in a fixed
+//     order (deterministic) and writes y.
+//   * mask windows (variants 12-15 and the segments): the masks of 8/mb
+//     consecutive blocks are read as one 8-byte word, so walking low-fill
+//     blocks does not wait on memory once per block.
 #pragma once
 
 #include "internal.cuh"
@@ -94,6 +98,39 @@ __device__ __forceinline__ int popc_all(const Mask<MB>& m) {
 #pragma unroll
   for (int q = 0; q < Mask<MB>::W; ++q) cnt += __popc(m.w[q]);
   return cnt;
+}
+
+// The 8 mask bytes that start at block b: blocks b .. b + 8/MB - 1 (MB <= 8),
+// bit j*8*MB + q of the result = bit q of block b + j. Reads the two aligned
+// 8-byte words around them; mask arrays carry 16 bytes of padding past their
+// end, so the second word is always inside the allocation.
+template <int MB>
+__device__ __forceinline__ uint64_t load_window(const uint8_t* __restrict__ masks, int32_t b) {
+  static_assert(MB <= 8, "a window holds at most 8 mask bytes");
+  const uint64_t o = (uint64_t)(uint32_t)b * MB;
+  const unsigned long long* p = reinterpret_cast<const unsigned long long*>(masks) + (o >> 3);
+  if constexpr (MB == 8) {
+    return __ldg(p);
+  } else {
+    const unsigned sh = (unsigned)(o & 7) * 8;
+    const uint64_t lo = __ldg(p), hi = __ldg(p + 1);
+    return sh ? (lo >> sh) | (hi << (64 - sh)) : lo;
+  }
+}
+
+// mask of block w of a window
+template <int MB>
+__device__ __forceinline__ Mask<MB> window_mask(uint64_t win, int w) {
+  Mask<MB> m;
+  if constexpr (MB == 8) {
+    m.w[0] = (uint32_t)win;
+    m.w[1] = (uint32_t)(win >> 32);
+  } else if constexpr (MB == 4) {
+    m.w[0] = (uint32_t)(win >> (32 * w));
+  } else {
+    m.w[0] = (uint32_t)(win >> (8 * MB * w)) & ((1u << (8 * MB)) - 1u);
+  }
+  return m;
 }
 
 // ---------------------------------------------------------------- types
@@ -235,6 +272,84 @@ __device__ __forceinline__ typename T::A row_sum_u(int i, int32_t b, int32_t ben
   return acc;
 }
 
+// Same sum as row_sum_u (same nonzeros, same order), decoded from mask
+// windows: the masks of 8/MB consecutive blocks arrive in one 8-byte read and
+// the next window is requested while the current one is consumed, so stepping
+// from block to block costs no global-memory round trip. The column index of
+// each decoded nonzero is loaded beside its value (one load per nonzero; the
+// indices of neighbouring blocks share sectors). For low fill (about one
+// nonzero per block, as in power-law graphs) a trip of U nonzeros then waits
+// for two memory latencies instead of one per block.
+template <int R, int C, class T, int U>
+__device__ __forceinline__ typename T::A row_sum_w(int i, int32_t b, int32_t bend,
+                                                   const typename T::V* __restrict__ vrow,
+                                                   const int32_t* __restrict__ bcol, const uint8_t* __restrict__ bmask,
+                                                   const typename T::X* __restrict__ x) {
+  constexpr int MB = (R * C + 7) / 8;
+  constexpr int K = 8 / MB;  // blocks per window
+  using A = typename T::A;
+  uint64_t cur = b < bend ? load_window<MB>(bmask, b) : 0ull;
+  uint64_t nxt = b + K < bend ? load_window<MB>(bmask, b + K) : 0ull;
+  int32_t wb = b;  // first block of the current window
+  int w = 0;       // blocks of the current window entered so far
+  int32_t vbase = 0, vo = 0, blk = 0;
+  uint32_t bits = 0;
+  A acc = 0;
+  for (;;) {
+    int32_t vi[U], bi[U], ki[U];
+    bool h[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      while (bits == 0 && wb + w < bend) {
+        if (w == K) {
+          cur = nxt;
+          wb += K;
+          w = 0;
+          nxt = wb + K < bend ? load_window<MB>(bmask, wb + K) : 0ull;
+        }
+        const Mask<MB> mk = window_mask<MB>(cur, w);
+        bits = row_bits<C>(mk, i);
+        vo = vbase + popc_below<C>(mk, i);
+        vbase += popc_all(mk);
+        blk = wb + w;
+        ++w;
+      }
+      h[u] = bits != 0;
+      ki[u] = __ffs(bits) - 1;
+      bits &= bits - 1;
+      vi[u] = vo;
+      vo += h[u] ? 1 : 0;
+      bi[u] = blk;
+    }
+    if (!h[0]) break;
+    A v[U], xx[U];
+    int32_t cc[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      v[u] = h[u] ? T::val(vrow, vi[u]) : A(0);
+      cc[u] = h[u] ? __ldg(bcol + bi[u]) : 0;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) xx[u] = h[u] ? T::xv(x, (int64_t)cc[u] + ki[u]) : A(0);
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (h[u]) acc = fmadd<T>(v[u], xx[u], acc);
+  }
+  return acc;
+}
+
+// row_sum_w where a window fits the shape's masks (up to 64 mask bits per
+// block), row_sum_u otherwise
+template <int R, int C, class T, int U, bool WIN>
+__device__ __forceinline__ typename T::A row_sum(int i, int32_t b, int32_t bend, const typename T::V* __restrict__ vrow,
+                                                 const int32_t* __restrict__ bcol, const uint8_t* __restrict__ bmask,
+                                                 const typename T::X* __restrict__ x) {
+  if constexpr (WIN && R * C <= 64)
+    return row_sum_w<R, C, T, U>(i, b, bend, vrow, bcol, bmask, x);
+  else
+    return row_sum_u<R, C, T, U>(i, b, bend, vrow, bcol, bmask, x);
+}
+
 // ------------------------------------------- short intervals, unrolled form
 // Same mapping, arithmetic and summation order as k_spmv_rows; each loop trip
 // decodes the lane's next U nonzeros first (the mask and column index of the
@@ -245,7 +360,8 @@ __device__ __forceinline__ typename T::A row_sum_u(int i, int32_t b, int32_t ben
 //
 // With ORDER, lane slot q of the warp takes interval order[q] instead of q
 // (the sorted work order built at conversion; long intervals are not in it).
-template <int R, int C, class T, bool ACCUM, int U, bool ORDER>
+// With WIN the row is decoded from mask windows (row_sum_w).
+template <int R, int C, class T, bool ACCUM, int U, bool ORDER, bool WIN>
 __global__ void __launch_bounds__(256) k_spmv_rows_u(int64_t n, int64_t I, int32_t long_blocks, int64_t long_values,
                                                      const int32_t* __restrict__ brp, const int32_t* __restrict__ bcol,
                                                      const uint8_t* __restrict__ bmask,
@@ -269,7 +385,7 @@ __global__ void __launch_bounds__(256) k_spmv_rows_u(int64_t n, int64_t I, int32
   const int32_t bend = __ldg(brp + it + 1);
   const int64_t vbase0 = __ldg(valptr + it);
   if (bend - b > long_blocks || __ldg(valptr + it + 1) - vbase0 > long_values) return;  // the segment path's
-  const typename T::A acc = row_sum_u<R, C, T, U>(i, b, bend, val + vbase0, bcol, bmask, x);
+  const typename T::A acc = row_sum<R, C, T, U, WIN>(i, b, bend, val + vbase0, bcol, bmask, x);
   const int64_t row = it * R + i;
   if (row < n) {
     if (ACCUM)
@@ -280,75 +396,134 @@ __global__ void __launch_bounds__(256) k_spmv_rows_u(int64_t n, int64_t I, int32
 }
 
 // -------------------------------------------------------- long intervals
-template <int R, int C, class T>
+// A warp per segment (at most seg_blocks blocks of one long interval). The
+// segment's blocks are cut into S = 32/r contiguous runs, one per group of r
+// lanes (lane = run slot, row i). A first pass counts the stored values of
+// each run from its masks and a shuffle scan over the slots gives every run
+// its first value; each lane then sums its row over its run with the
+// short-interval decode, and the run sums of a row are added over the slots
+// by a fixed shuffle tree. Lanes 0..r-1 store the segment's r partial sums.
+// (Measured on GB300: giving each lane a whole segment instead, like a short
+// interval, is about 1.35x slower on power-law rows; the warp's lanes then
+// stream 32 separate stretches of memory.)
+template <int R, int C, class T, int U, bool WIN>
 __global__ void __launch_bounds__(256) k_spmv_segments(int64_t nseg, const Segment* __restrict__ segs,
                                                        const int32_t* __restrict__ bcol, const uint8_t* __restrict__ bmask,
                                                        const typename T::V* __restrict__ val,
                                                        const typename T::X* __restrict__ x,
                                                        typename T::A* __restrict__ partials) {
   constexpr int MB = (R * C + 7) / 8;
-  constexpr int S = kWarp / R;  // block slots per step
+  constexpr int S = kWarp / R;  // runs per segment
   const int lane = threadIdx.x & 31;
   const int64_t seg = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (seg >= nseg) return;  // whole warp leaves together
   const int slot = lane / R, i = lane % R;
   const Segment sg = segs[seg];
-  int64_t vbase = sg.v_begin;
-  typename T::A acc = 0;
-  for (int32_t b0 = sg.b_begin; b0 < sg.b_end; b0 += S) {
-    const int32_t b = b0 + slot;
-    const bool valid = b < sg.b_end;
-    const Mask<MB> mk = valid ? load_mask<MB>(bmask, b) : zero_mask<MB>();
-    const int cnt = popc_all(mk);
-    // inclusive scan of the block popcounts over the slots (stride R lanes)
-    int incl = cnt;
-#pragma unroll
-    for (int d = R; d < kWarp; d <<= 1) {
-      const int t = __shfl_up_sync(0xffffffffu, incl, d);
-      if (lane >= d) incl += t;
+  const int32_t per = (sg.b_end - sg.b_begin + S - 1) / S;
+  const int32_t rb = min(sg.b_begin + slot * per, sg.b_end);
+  const int32_t re = min(rb + per, sg.b_end);
+  // stored values of the run (the r lanes of a slot share its blocks)
+  int cnt = 0;
+  if constexpr (MB <= 8) {
+    constexpr int K = 8 / MB;
+    for (int32_t bb = rb + i * K; bb < re; bb += R * K) {
+      uint64_t wv = load_window<MB>(bmask, bb);
+      const int nblk = re - bb;
+      if (nblk < K) wv &= (1ull << (8 * MB * nblk)) - 1ull;
+      cnt += __popcll(wv);
     }
-    const int total = __shfl_sync(0xffffffffu, incl, kWarp - 1);
-    int64_t vo = vbase + (incl - cnt) + popc_below<C>(mk, i);
-    uint32_t bits = valid ? row_bits<C>(mk, i) : 0u;
-    const int32_t col0 = valid ? __ldg(bcol + b) : 0;
-    while (bits) {
-      const int k = __ffs(bits) - 1;
-      bits &= bits - 1;
-      acc = fmadd<T>(T::val(val, vo), T::xv(x, (int64_t)col0 + k), acc);
-      ++vo;
-    }
-    vbase += total;
+  } else {
+    for (int32_t bb = rb + i; bb < re; bb += R) cnt += popc_all(load_mask<MB>(bmask, bb));
   }
-  // sum over the slots of each row (lanes i, i + R, i + 2R, ...)
+#pragma unroll
+  for (int d = 1; d < R; d <<= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, d);
+  int incl = cnt;  // inclusive scan of the run totals over the slots
+#pragma unroll
+  for (int d = R; d < kWarp; d <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, incl, d);
+    if (lane >= d) incl += t;
+  }
+  typename T::A acc = row_sum<R, C, T, U, WIN>(i, rb, re, val + sg.v_begin + (incl - cnt), bcol, bmask, x);
 #pragma unroll
   for (int d = kWarp / 2; d >= R; d >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, d);
   if (lane < R) partials[seg * R + lane] = acc;
 }
 
-// first segment of each long interval adds its interval's partials in order
+// Finishes the long intervals (list of first segments built at conversion;
+// the first segment holds the interval's segment count). One lane per long
+// interval: with at most kFixupSerial segments it adds their partials row by
+// row in segment order; longer lists are taken by the whole warp, one
+// interval after another - lane j adds segments j, j + 32, ... in order and a
+// fixed shuffle tree adds the lanes. Either way the summation order depends
+// only on the segment count.
+constexpr int kFixupSerial = 32;
+
+template <class A, class X, bool ACCUM>
+__device__ __forceinline__ void fixup_lane_interval(bool have, int64_t s0, int32_t count, int32_t it, int r, int64_t n,
+                                                    const A* __restrict__ part, X* __restrict__ y) {
+  if (have && count <= kFixupSerial) {
+    for (int i = 0; i < r; ++i) {
+      A s = 0;
+      for (int q = 0; q < count; ++q) s += part[(s0 + q) * r + i];
+      const int64_t row = (int64_t)it * r + i;
+      if (row < n) {
+        if (ACCUM)
+          y[row] = y[row] + s;
+        else
+          y[row] = s;
+      }
+    }
+  }
+}
+
+template <class A, class X, bool ACCUM>
+__device__ __forceinline__ void fixup_warp_interval(int64_t s0, int32_t count, int32_t it, int r, int64_t n,
+                                                    const A* __restrict__ part, X* __restrict__ y) {
+  const int lane = threadIdx.x & 31;
+  for (int i = 0; i < r; ++i) {
+    A s = 0;
+    for (int q = lane; q < count; q += kWarp) s += part[(s0 + q) * r + i];
+#pragma unroll
+    for (int d = kWarp / 2; d >= 1; d >>= 1) s += __shfl_xor_sync(0xffffffffu, s, d);
+    const int64_t row = (int64_t)it * r + i;
+    if (lane == 0 && row < n) {
+      if (ACCUM)
+        y[row] = y[row] + s;
+      else
+        y[row] = s;
+    }
+  }
+}
+
 template <int R, class T, bool ACCUM>
-__global__ void k_spmv_fixup(int64_t n, int64_t nseg, const Segment* __restrict__ segs,
-                             const typename T::A* __restrict__ partials, typename T::X* __restrict__ y) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t seg = t / R;
-  const int i = (int)(t % R);
-  if (seg >= nseg) return;
-  const int32_t it = segs[seg].interval;
-  if (seg > 0 && segs[seg - 1].interval == it) return;
-  typename T::A s = 0;
-  for (int64_t k = seg; k < nseg && segs[k].interval == it; ++k) s += partials[k * R + i];
-  const int64_t row = (int64_t)it * R + i;
-  if (row < n) {
-    if (ACCUM)
-      y[row] = y[row] + s;
-    else
-      y[row] = s;
+__global__ void __launch_bounds__(256) k_spmv_fixup(int64_t n, int64_t nlong, const int32_t* __restrict__ seg_first,
+                                                    const Segment* __restrict__ segs,
+                                                    const typename T::A* __restrict__ partials,
+                                                    typename T::X* __restrict__ y) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (((int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31)) >= nlong) return;  // whole warp
+  const bool have = e < nlong;
+  const int64_t s0 = have ? __ldg(seg_first + e) : 0;
+  const int32_t count = have ? segs[s0].count : 0;
+  const int32_t it = have ? segs[s0].interval : 0;
+  fixup_lane_interval<typename T::A, typename T::X, ACCUM>(have, s0, count, it, R, n, partials, y);
+  unsigned big = __ballot_sync(0xffffffffu, have && count > kFixupSerial);
+  while (big) {
+    const int src = __ffs(big) - 1;
+    big &= big - 1;
+    fixup_warp_interval<typename T::A, typename T::X, ACCUM>(__shfl_sync(0xffffffffu, s0, src),
+                                                             __shfl_sync(0xffffffffu, count, src),
+                                                             __shfl_sync(0xffffffffu, it, src), R, n, partials, y);
   }
 }
 
 // --------------------------------------------------------------- launch
+// Variants of the short-interval kernel: 1 plain; 0/5 natural order U=2;
+// 3 natural U=4; 9/10 sorted order U=2/U=4; 12/14 natural order, mask
+// windows, U=4/U=2; 13/15 sorted order, mask windows, U=4/U=2.
+// `partials` is the segment scratch (n_segments * r accumulators).
 template <int R, int C, class T>
-cudaError_t launch_beta(const spc5_matrix* h, const void* xv, void* yv, bool acc, cudaStream_t s) {
+cudaError_t launch_beta(const spc5_matrix* h, const void* xv, void* yv, bool acc, void* partials, cudaStream_t s) {
   using V = typename T::V;
   using X = typename T::X;
   using A = typename T::A;
@@ -357,60 +532,57 @@ cudaError_t launch_beta(const spc5_matrix* h, const void* xv, void* yv, bool acc
   const V* val = static_cast<const V*>(h->values);
   constexpr int S = kWarp / R;
   const int threads = 256;
+  const int v = h->variant;
+  const bool ordered = (v == 9 || v == 10 || v == 13 || v == 15) && h->norder > 0;
   if (h->I > 0) {
-    const int64_t warps = (h->I + S - 1) / S;
-    if (h->variant == 1) {
-      const unsigned grid = (unsigned)((warps * kWarp + threads - 1) / threads);
+    const int64_t warps = ordered ? (h->norder + S - 1) / S : (h->I + S - 1) / S;
+    const unsigned grid = (unsigned)((warps * kWarp + threads - 1) / threads);
+    const int32_t* order = ordered ? h->order : nullptr;
+    const int64_t norder = ordered ? h->norder : 0;
+    auto go = [&](auto kern) {
+      kern<<<grid, threads, 0, s>>>(h->n, h->I, h->long_blocks, h->long_values, h->block_rowptr, h->block_colidx,
+                                    h->block_masks, val, h->valptr, x, y, order, norder);
+    };
+#define SPC5_GO(U, ORD, WIN) \
+  (acc ? go(k_spmv_rows_u<R, C, T, true, U, ORD, WIN>) : go(k_spmv_rows_u<R, C, T, false, U, ORD, WIN>))
+    if (v == 1) {
       if (acc)
         k_spmv_rows<R, C, T, true><<<grid, threads, 0, s>>>(h->n, h->I, h->long_blocks, h->long_values, h->block_rowptr,
                                                             h->block_colidx, h->block_masks, val, h->valptr, x, y);
       else
         k_spmv_rows<R, C, T, false><<<grid, threads, 0, s>>>(h->n, h->I, h->long_blocks, h->long_values, h->block_rowptr,
                                                              h->block_colidx, h->block_masks, val, h->valptr, x, y);
-    } else if ((h->variant == 9 || h->variant == 10) && h->norder > 0) {
-      // sorted work order
-      const int64_t owarps = (h->norder + S - 1) / S;
-      const unsigned grid = (unsigned)((owarps * kWarp + threads - 1) / threads);
-      auto go = [&](auto kern) {
-        kern<<<grid, threads, 0, s>>>(h->n, h->I, h->long_blocks, h->long_values, h->block_rowptr, h->block_colidx,
-                                      h->block_masks, val, h->valptr, x, y, h->order, h->norder);
-      };
-      if (h->variant == 10) {
-        if (acc) go(k_spmv_rows_u<R, C, T, true, 4, true>); else go(k_spmv_rows_u<R, C, T, false, 4, true>);
-      } else {
-        if (acc) go(k_spmv_rows_u<R, C, T, true, 2, true>); else go(k_spmv_rows_u<R, C, T, false, 2, true>);
-      }
+    } else if (ordered) {
+      if (v == 10) SPC5_GO(4, true, false);
+      else if (v == 13) SPC5_GO(4, true, true);
+      else if (v == 15) SPC5_GO(2, true, true);
+      else SPC5_GO(2, true, false);
     } else {
-      // natural order; variant 3 unrolls by 4, the default (0 or 5) by 2
-      const unsigned grid = (unsigned)((warps * kWarp + threads - 1) / threads);
-      auto go = [&](auto kern) {
-        kern<<<grid, threads, 0, s>>>(h->n, h->I, h->long_blocks, h->long_values, h->block_rowptr, h->block_colidx,
-                                      h->block_masks, val, h->valptr, x, y, nullptr, (int64_t)0);
-      };
-      if (h->variant == 3) {
-        if (acc) go(k_spmv_rows_u<R, C, T, true, 4, false>); else go(k_spmv_rows_u<R, C, T, false, 4, false>);
-      } else {
-        if (acc) go(k_spmv_rows_u<R, C, T, true, 2, false>); else go(k_spmv_rows_u<R, C, T, false, 2, false>);
-      }
+      if (v == 3) SPC5_GO(4, false, false);
+      else if (v == 12) SPC5_GO(4, false, true);
+      else if (v == 14) SPC5_GO(2, false, true);
+      else SPC5_GO(2, false, false);
     }
+#undef SPC5_GO
   }
   if (h->nseg > 0) {
-    A* part = static_cast<A*>(h->partials);
+    A* part = static_cast<A*>(partials);
     const unsigned grid = (unsigned)((h->nseg * kWarp + threads - 1) / threads);
-    k_spmv_segments<R, C, T><<<grid, threads, 0, s>>>(h->nseg, h->segs, h->block_colidx, h->block_masks, val, x, part);
-    const unsigned g2 = (unsigned)((h->nseg * R + 255) / 256);
+    k_spmv_segments<R, C, T, 4, true><<<grid, threads, 0, s>>>(h->nseg, h->segs, h->block_colidx, h->block_masks, val,
+                                                               x, part);
+    const unsigned g2 = (unsigned)((h->nlong + 255) / 256);
     if (acc)
-      k_spmv_fixup<R, T, true><<<g2, 256, 0, s>>>(h->n, h->nseg, h->segs, part, y);
+      k_spmv_fixup<R, T, true><<<g2, 256, 0, s>>>(h->n, h->nlong, h->seg_first, h->segs, part, y);
     else
-      k_spmv_fixup<R, T, false><<<g2, 256, 0, s>>>(h->n, h->nseg, h->segs, part, y);
+      k_spmv_fixup<R, T, false><<<g2, 256, 0, s>>>(h->n, h->nlong, h->seg_first, h->segs, part, y);
   }
   return cudaGetLastError();
 }
 
 template <class T>
-cudaError_t dispatch_beta(const spc5_matrix* h, const void* x, void* y, bool acc, cudaStream_t s) {
+cudaError_t dispatch_beta(const spc5_matrix* h, const void* x, void* y, bool acc, void* partials, cudaStream_t s) {
 #define SPC5_CASE(RR, CC) \
-  if (h->r == RR && h->c == CC) return launch_beta<RR, CC, T>(h, x, y, acc, s);
+  if (h->r == RR && h->c == CC) return launch_beta<RR, CC, T>(h, x, y, acc, partials, s);
   SPC5_CASE(1, 4) SPC5_CASE(1, 8) SPC5_CASE(1, 16)
   SPC5_CASE(2, 4) SPC5_CASE(2, 8) SPC5_CASE(2, 16)
   SPC5_CASE(4, 4) SPC5_CASE(4, 8) SPC5_CASE(4, 16)

@@ -3,8 +3,8 @@
 
 namespace spc5 {
 
-cudaError_t launch_spmv_bf16(const spc5_matrix* h, const void* x, void* y, bool acc, cudaStream_t s) {
-  return dispatch_beta<BF16>(h, x, y, acc, s);
+cudaError_t launch_spmv_bf16(const spc5_matrix* h, const void* x, void* y, bool acc, cudaStream_t s, void* partials) {
+  return dispatch_beta<BF16>(h, x, y, acc, partials ? partials : h->partials, s);
 }
 
 }  // namespace spc5

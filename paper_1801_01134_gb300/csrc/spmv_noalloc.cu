@@ -24,7 +24,7 @@
 //     that first call before any stream capture begins.
 #include <mutex>
 
-#include "spmv_beta.cuh"
+#include "internal.cuh"
 
 namespace spc5 {
 namespace {
@@ -54,69 +54,6 @@ cudaError_t noalloc_scratch(void** out) {
   return cudaSuccess;
 }
 
-// Same kernels and launch shapes as launch_beta; only the segment scratch
-// differs (the fixed array instead of the handle's buffer).
-template <int R, int C, class T>
-cudaError_t launch_beta_noalloc(const spc5_matrix* h, const void* xv, void* yv, void* scratch, cudaStream_t s) {
-  using V = typename T::V;
-  using X = typename T::X;
-  using A = typename T::A;
-  const X* x = static_cast<const X*>(xv);
-  X* y = static_cast<X*>(yv);
-  const V* val = static_cast<const V*>(h->values);
-  constexpr int S = kWarp / R;
-  const int threads = 256;
-  if (h->I > 0) {
-    const int64_t warps = (h->I + S - 1) / S;
-    if (h->variant == 1) {
-      const unsigned grid = (unsigned)((warps * kWarp + threads - 1) / threads);
-      k_spmv_rows<R, C, T, false><<<grid, threads, 0, s>>>(h->n, h->I, h->long_blocks, h->long_values, h->block_rowptr,
-                                                           h->block_colidx, h->block_masks, val, h->valptr, x, y);
-    } else if ((h->variant == 9 || h->variant == 10) && h->norder > 0) {
-      const int64_t owarps = (h->norder + S - 1) / S;
-      const unsigned grid = (unsigned)((owarps * kWarp + threads - 1) / threads);
-      auto go = [&](auto kern) {
-        kern<<<grid, threads, 0, s>>>(h->n, h->I, h->long_blocks, h->long_values, h->block_rowptr, h->block_colidx,
-                                      h->block_masks, val, h->valptr, x, y, h->order, h->norder);
-      };
-      if (h->variant == 10)
-        go(k_spmv_rows_u<R, C, T, false, 4, true>);
-      else
-        go(k_spmv_rows_u<R, C, T, false, 2, true>);
-    } else {
-      const unsigned grid = (unsigned)((warps * kWarp + threads - 1) / threads);
-      auto go = [&](auto kern) {
-        kern<<<grid, threads, 0, s>>>(h->n, h->I, h->long_blocks, h->long_values, h->block_rowptr, h->block_colidx,
-                                      h->block_masks, val, h->valptr, x, y, nullptr, (int64_t)0);
-      };
-      if (h->variant == 3)
-        go(k_spmv_rows_u<R, C, T, false, 4, false>);
-      else
-        go(k_spmv_rows_u<R, C, T, false, 2, false>);
-    }
-  }
-  if (h->nseg > 0) {
-    A* part = static_cast<A*>(scratch);
-    const unsigned grid = (unsigned)((h->nseg * kWarp + threads - 1) / threads);
-    k_spmv_segments<R, C, T><<<grid, threads, 0, s>>>(h->nseg, h->segs, h->block_colidx, h->block_masks, val, x, part);
-    const unsigned g2 = (unsigned)((h->nseg * R + 255) / 256);
-    k_spmv_fixup<R, T, false><<<g2, 256, 0, s>>>(h->n, h->nseg, h->segs, part, y);
-  }
-  return cudaGetLastError();
-}
-
-template <class T>
-cudaError_t dispatch_noalloc(const spc5_matrix* h, const void* x, void* y, void* scratch, cudaStream_t s) {
-#define SPC5_CASE(RR, CC) \
-  if (h->r == RR && h->c == CC) return launch_beta_noalloc<RR, CC, T>(h, x, y, scratch, s);
-  SPC5_CASE(1, 4) SPC5_CASE(1, 8) SPC5_CASE(1, 16)
-  SPC5_CASE(2, 4) SPC5_CASE(2, 8) SPC5_CASE(2, 16)
-  SPC5_CASE(4, 4) SPC5_CASE(4, 8) SPC5_CASE(4, 16)
-  SPC5_CASE(8, 4) SPC5_CASE(8, 8) SPC5_CASE(8, 16)
-#undef SPC5_CASE
-  return cudaErrorInvalidValue;
-}
-
 }  // namespace
 }  // namespace spc5
 
@@ -133,11 +70,12 @@ extern "C" spc5_status spc5_spmv_noalloc(spc5_handle h, const void* x_d, void* y
   void* scratch = nullptr;
   cudaError_t e = noalloc_scratch(&scratch);
   if (e != cudaSuccess) return cuda_fail(e, "spmv_noalloc: scratch address");
+  // the kernels of spc5_spmv; only the segment scratch differs
   const cudaStream_t s = (cudaStream_t)stream;
   switch (h->vt) {
-    case SPC5_F64: e = dispatch_noalloc<F64>(h, x_d, y_d, scratch, s); break;
-    case SPC5_F32: e = dispatch_noalloc<F32>(h, x_d, y_d, scratch, s); break;
-    case SPC5_BF16: e = dispatch_noalloc<BF16>(h, x_d, y_d, scratch, s); break;
+    case SPC5_F64: e = launch_spmv_f64(h, x_d, y_d, false, s, scratch); break;
+    case SPC5_F32: e = launch_spmv_f32(h, x_d, y_d, false, s, scratch); break;
+    case SPC5_BF16: e = launch_spmv_bf16(h, x_d, y_d, false, s, scratch); break;
     default: return fail(SPC5_EUNSUPPORTED, "spmv_noalloc: value type");
   }
   if (e != cudaSuccess) return cuda_fail(e, "spmv_noalloc launch");

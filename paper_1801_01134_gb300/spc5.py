@@ -34,7 +34,7 @@ class Spc5Error(RuntimeError):
 
 class Opts(ctypes.Structure):
     _fields_ = [("long_blocks", ctypes.c_int32), ("seg_blocks", ctypes.c_int32), ("variant", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 5)]
+                ("order_window", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
 
 
 class CgOpts(ctypes.Structure):
@@ -251,7 +251,8 @@ class Matrix:
 
 
 def convert(rowptr: torch.Tensor, colidx: torch.Tensor, values: torch.Tensor, n: int, m: int, r: int, c: int,
-            long_blocks: int = 0, seg_blocks: int = 0, variant: int = 0, stream=None) -> Matrix:
+            long_blocks: int = 0, seg_blocks: int = 0, variant: int = 0, order_window: int = 0,
+            stream=None) -> Matrix:
     """CSR (device tensors: int64 rowptr, int32 colidx, values) -> beta(r,c)."""
     if rowptr.dtype != torch.int64 or colidx.dtype != torch.int32:
         raise TypeError("rowptr must be int64 and colidx int32")
@@ -259,7 +260,7 @@ def convert(rowptr: torch.Tensor, colidx: torch.Tensor, values: torch.Tensor, n:
         raise TypeError("values must be float64, float32 or bfloat16")
     vt = _VALUE_DTYPE[values.dtype]
     nnz = values.numel()
-    opts = Opts(long_blocks, seg_blocks, variant)
+    opts = Opts(long_blocks, seg_blocks, variant, order_window)
     h = ctypes.c_void_p()
     _check(load().spc5_convert(n, m, nnz, _ptr(rowptr), _ptr(colidx), _ptr(values), vt, r, c, ctypes.byref(opts),
                                _stream_ptr(stream), ctypes.byref(h)), "spc5_convert")

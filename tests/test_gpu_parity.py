@@ -100,9 +100,12 @@ def test_spmv_f64(cuda_device, name, r, c):
     M.destroy()
 
 
-@pytest.mark.parametrize("variant", [1, 3, 5, 9, 10])
+VARIANTS = [1, 3, 5, 9, 10, 12, 13, 14, 15]
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
 @pytest.mark.parametrize("name", ["st27_ragged", "rmat11", "fem", "sparse_rows"])
-@pytest.mark.parametrize("r,c", [(1, 4), (2, 8), (4, 16), (8, 8)])
+@pytest.mark.parametrize("r,c", [(1, 4), (1, 8), (2, 8), (4, 4), (4, 16), (8, 8), (8, 16)])
 def test_spmv_variants(cuda_device, variant, name, r, c):
     A = get(name)
     x = inputs.vec_uniform(A.m, seed=0)
@@ -111,6 +114,34 @@ def test_spmv_variants(cuda_device, variant, name, r, c):
     M = spc5.convert(d.rowptr, d.colidx, d.values, A.n, A.m, r, c, variant=variant)
     check64(M.spmv(torch.from_numpy(x).cuda()).cpu().numpy(), y_ref, absy)
     M.destroy()
+
+
+@pytest.mark.parametrize("name", ["st27_ragged", "rmat11", "fem", "uniform"])
+@pytest.mark.parametrize("r,c", spc5.SHAPES)
+def test_variants_sum_in_the_same_order(cuda_device, name, r, c):
+    # every short-interval variant adds a row's products in storage order, so
+    # all of them give the same bits; the segment path (its own fixed order)
+    # is the same in all variants
+    A = get(name)
+    d = dev_csr(A)
+    xd = torch.from_numpy(inputs.vec_normal(A.m, seed=3)).cuda()
+    M = spc5.convert(d.rowptr, d.colidx, d.values, A.n, A.m, r, c, long_blocks=8)
+    ref = M.spmv(xd).clone()
+    for v in VARIANTS:
+        M.set_variant(v)
+        assert torch.equal(M.spmv(xd), ref), v
+    M.destroy()
+    # one sorting window over all intervals, and larger segments
+    for v, sb in [(10, 0), (13, 0), (15, 64), (13, 3)]:
+        M = spc5.convert(d.rowptr, d.colidx, d.values, A.n, A.m, r, c, long_blocks=8, seg_blocks=sb, variant=v,
+                         order_window=-1)
+        y = M.spmv(xd)
+        if sb == 0:
+            assert torch.equal(y, ref), v
+        else:  # other segment boundaries: same values up to the summation order
+            y_ref, absy = oracle.csr_spmv_dot2(A, xd.cpu().numpy())
+            check64(y.cpu().numpy(), y_ref, absy)
+        M.destroy()
 
 
 @pytest.mark.parametrize("r,c", spc5.SHAPES)
