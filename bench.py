@@ -37,7 +37,7 @@ sys.path.insert(0, ROOT)
 METRIC = "SpMV GFLOP/s & HBM GB/s (% of peak), selected β(r,c) vs CSR, 1 GB300"
 L2_FLUSH_BYTES = 512 << 20
 FP64_PEAK_GFLOPS = 1250.0  # nominal GB300 float64 rate (2 FMA lanes/clk/SM x 152 SMs x 2.07 GHz x 2)
-VARIANTS = (5, 10)  # short-interval kernel variants the tuner tries per shape
+VARIANTS = (5, 10, 13, 15)  # short-interval kernel variants the tuner tries per shape
 
 
 def parse():
@@ -102,8 +102,14 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def profile_traffic(kernel: str, workload_name: str):
-    """DRAM bytes per launch from a committed ncu summary, if its source hash matches."""
+def traffic_key(r: int, c: int, variant: int, dtype: str, workload_name: str) -> str:
+    return f"beta({r},{c}) variant {variant} {dtype}|{workload_name}"
+
+
+def profile_traffic(key: str):
+    """DRAM bytes (read + write) of one SpMV from the committed ncu summary
+    profiles/traffic.json, or None when the kernels changed since it was taken
+    (the entry's source hash no longer matches)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
@@ -111,10 +117,10 @@ def profile_traffic(kernel: str, workload_name: str):
         rec = json.load(open(path))
     except Exception:
         return None
-    ent = rec.get(f"{kernel}|{workload_name}")
-    if not ent or ent.get("source_hash") != kernel_source_hash():
+    ent = rec.get("entries", {}).get(key)
+    if not ent or rec.get("source_hash") != kernel_source_hash():
         return None
-    return ent.get("dram_bytes_per_launch")
+    return ent.get("dram_bytes_per_spmv")
 
 
 class ClockSampler:
@@ -647,7 +653,7 @@ def main():
     roofline = {
         "bound": "alu", "achieved": round(dom_flops / dom_t / 1e6, 1), "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
         "frac": round(dom_flops / dom_t / 1e6 / FP64_PEAK_GFLOPS, 4),
-        "traffic": profile_traffic(kname, dom["name"]),
+        "traffic": profile_traffic(traffic_key(dom["r"], dom["c"], dom["variant"], "f64", dom["name"])),
         "kernel": f"{kname}<{dom['r']},{dom['c']},f64> on {dom['name']}",
         "peak_source": "nominal float64 rate (2 FMA lanes/clk/SM x 152 SMs x 2.07 GHz x 2 = 1.25 TFLOP/s)",
         "peak_measured": round(fp64_measured, 1), "frac_of_measured": round(dom_flops / dom_t / 1e6 / fp64_measured, 4),
