@@ -62,6 +62,8 @@ def parse():
     p.add_argument("--cg-n", type=int, default=96, help="grid edge of the CG profiling matrix")
     p.add_argument("--cg-every", type=int, default=8)
     p.add_argument("--cg-graph", type=int, default=1)
+    p.add_argument("--cg-variant", type=int, default=0, help="kernel variant of the CG profiling handles")
+    p.add_argument("--cg-shape", default="2x4", help="block shape of the CG profiling handles")
     return p.parse_args()
 
 
@@ -497,7 +499,8 @@ def main():
         hs = {}
         for name, dt in (("f64", torch.float64), ("f32", torch.float32)):
             d = spc5.upload_csr(A, dt, dev)
-            hs[name] = spc5.convert(d.rowptr, d.colidx, d.values, A.n, A.m, 2, 4)
+            r, c = (int(v) for v in args.cg_shape.split("x"))
+            hs[name] = spc5.convert(d.rowptr, d.colidx, d.values, A.n, A.m, r, c, variant=args.cg_variant)
         for label, inner in (("fp64_cg", None), ("mixed_f32", hs["f32"])):
             for rep in range(2):
                 t0 = time.perf_counter()

@@ -10,13 +10,18 @@
 // per ~16 SM cycles), so moving the bulk of the work to float32 pays twice:
 // half the bytes per SpMV and no float64 pipe in the inner loop.
 //
+// The iteration is ordered so that it takes two kernels. With beta from the
+// previous iteration (0 at the start, p = q = 0):
+//     q = A r + beta q,  p = r + beta p,  alpha = rho / (p.q)     (kernel 1)
+//     x += alpha p,  r -= alpha q,  rho' = r.r,  beta = rho'/rho  (kernel 2)
+// which is Hestenes-Stiefel CG with A p_k formed as A r_k + beta A p_{k-1}
+// (equal in exact arithmetic), so the SpMV reads r and the p update rides in
+// its epilogue instead of a third pass.
 // Scalars (rho, p.q, alpha, beta) never leave the device inside an iteration:
 // dot products reduce to per-block partials that the last block to finish
 // sums in a fixed order (so results repeat run to run), writing the derived
-// scalar too. When the matrix has no long intervals an iteration is three
-// kernels - the SpMV with the p.q epilogue, the x / r update with r.r, the p
-// update - and it can be captured once into a CUDA graph and replayed. The
-// host reads the residual norm every `check_every` iterations.
+// scalar too. The iteration can be captured once into a CUDA graph and
+// replayed. The host reads the residual norm every `check_every` iterations.
 #include <cmath>
 #include <vector>
 
@@ -26,6 +31,13 @@ namespace spc5 {
 namespace {
 
 constexpr int kThreads = 256;
+// Grid caps (beyond them, warps stride over the work). Every block adds one
+// same-address atomic to the reduction ticket, and those serialise at about
+// 2.5 ns each on GB300, so a smaller grid finishes the reduction sooner:
+// measured best at 4 blocks per SM for the fused SpMV, 2 for the vector
+// updates (7-point Poisson 96^3, float64 CG 21.7 -> 17.4 ms).
+constexpr int kSpmvBlocksPerSm = 4;
+constexpr int kVecBlocksPerSm = 2;
 enum { S_RHO = 0, S_PQ, S_ALPHA, S_BETA, S_RHONEW, S_NORM, S_COUNT = 8 };
 
 template <class A>
@@ -81,32 +93,6 @@ __global__ void __launch_bounds__(kThreads) k_dot_final(const A* __restrict__ pa
   }
 }
 
-// x += alpha p; r -= alpha q; part[block] = partial of r.r
-template <class T, class A>
-__global__ void __launch_bounds__(kThreads) k_cg_xr(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p,
-                                                    const T* __restrict__ q, int64_t n, const double* __restrict__ scal,
-                                                    A* __restrict__ part) {
-  const T alpha = (T)scal[S_ALPHA];
-  A s = 0;
-  for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads) {
-    x[i] = fma(alpha, p[i], x[i]);
-    const T ri = fma(-alpha, q[i], r[i]);
-    r[i] = ri;
-    s = fma((A)ri, (A)ri, s);
-  }
-  s = block_sum<A>(s);
-  if (threadIdx.x == 0) part[blockIdx.x] = s;
-}
-
-// p = r + beta p
-template <class T>
-__global__ void __launch_bounds__(kThreads) k_cg_p(T* __restrict__ p, const T* __restrict__ r, int64_t n,
-                                                   const double* __restrict__ scal) {
-  const T beta = (T)scal[S_BETA];
-  for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads)
-    p[i] = fma(beta, p[i], r[i]);
-}
-
 // r = b - t (float64) and its partial r.r
 __global__ void __launch_bounds__(kThreads) k_residual(double* __restrict__ r, const double* __restrict__ b,
                                                        const double* __restrict__ t, int64_t n,
@@ -121,17 +107,18 @@ __global__ void __launch_bounds__(kThreads) k_residual(double* __restrict__ r, c
   if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
-// start of an inner solve: r32 = r64 / ||r64||, p32 = r32, x32 = 0
+// start of an inner solve: r32 = r64 / ||r64||, p32 = q32 = x32 = 0, beta = 0
 __global__ void __launch_bounds__(kThreads) k_inner_start(const double* __restrict__ r64, float* __restrict__ r32,
-                                                          float* __restrict__ p32, float* __restrict__ x32, int64_t n,
-                                                          const double* __restrict__ scal) {
+                                                          float* __restrict__ p32, float* __restrict__ q32,
+                                                          float* __restrict__ x32, int64_t n, double* __restrict__ scal) {
   const double inv = scal[S_NORM] > 0.0 ? 1.0 / sqrt(scal[S_NORM]) : 0.0;
   for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads) {
-    const float v = (float)(r64[i] * inv);
-    r32[i] = v;
-    p32[i] = v;
+    r32[i] = (float)(r64[i] * inv);
+    p32[i] = 0.0f;
+    q32[i] = 0.0f;
     x32[i] = 0.0f;
   }
+  if (blockIdx.x == 0 && threadIdx.x == 0) scal[S_BETA] = 0.0;
 }
 
 // x64 += ||r|| * x32
@@ -177,35 +164,41 @@ __device__ __forceinline__ bool finish_last_block(A* part, A mine, unsigned* tic
   return true;
 }
 
-// q = A p over the short intervals, one lane per row (the SpMV kernel's row
-// sum), fused with p.q; the last block writes scal[PQ] and scal[ALPHA].
-template <int R, int C, class T, int U>
+// q = A r + beta q and p = r + beta p over the short intervals, one lane per
+// row (the SpMV kernel's row sum applied to r), fused with p.q; the last
+// block writes scal[PQ] and scal[ALPHA].
+template <int R, int C, class T, int U, bool WIN>
 __global__ void __launch_bounds__(kThreads) k_cg_spmv_dot(int64_t n, int64_t I, const int32_t* __restrict__ brp,
                                                           const int32_t* __restrict__ bcol,
                                                           const uint8_t* __restrict__ bmask,
                                                           const typename T::V* __restrict__ val,
                                                           const int64_t* __restrict__ valptr,
-                                                          const typename T::X* __restrict__ p,
-                                                          typename T::X* __restrict__ q, typename T::A* part,
-                                                          unsigned* ticket, double* __restrict__ scal) {
+                                                          const typename T::X* __restrict__ r,
+                                                          typename T::X* __restrict__ p, typename T::X* __restrict__ q,
+                                                          typename T::A* part, unsigned* ticket,
+                                                          double* __restrict__ scal) {
   using A = typename T::A;
+  using X = typename T::X;
   constexpr int S = kWarp / R;
   const int lane = threadIdx.x & 31;
   const int i = lane % R;
+  const X beta = (X)scal[S_BETA];
   const int64_t nwarps = (int64_t)gridDim.x * (kThreads / kWarp);
   const int64_t ntasks = (I + S - 1) / S;
   A prod = 0;
-  // warps stride over the tasks (32/r intervals each) so that the grid, and
-  // with it the number of partials and tickets, stays a few CTAs per SM
+  // warps stride over the tasks (32/r intervals each) when the grid is capped
   for (int64_t task = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; task < ntasks; task += nwarps) {
     const int64_t it = task * S + lane / R;
     if (it < I) {
       const int32_t b = __ldg(brp + it), bend = __ldg(brp + it + 1);
-      const A acc = row_sum_u<R, C, T, U>(i, b, bend, val + __ldg(valptr + it), bcol, bmask, p);
+      const A acc = row_sum<R, C, T, U, WIN>(i, b, bend, val + __ldg(valptr + it), bcol, bmask, r);
       const int64_t row = it * R + i;
       if (row < n) {
-        q[row] = acc;
-        prod = fma(acc, (A)p[row], prod);
+        const X qn = fma(beta, q[row], (X)acc);
+        const X pn = fma(beta, p[row], r[row]);
+        q[row] = qn;
+        p[row] = pn;
+        prod = fma((A)pn, (A)qn, prod);
       }
     }
   }
@@ -217,15 +210,77 @@ __global__ void __launch_bounds__(kThreads) k_cg_spmv_dot(int64_t n, int64_t I, 
   }
 }
 
+// 16-byte vector of T (float4 / double2) for the streaming kernels
+template <class T>
+struct Vec16;
+template <>
+struct Vec16<float> {
+  using type = float4;
+  static constexpr int N = 4;
+};
+template <>
+struct Vec16<double> {
+  using type = double2;
+  static constexpr int N = 2;
+};
+
+template <class T>
+__device__ __forceinline__ T& lane_of(typename Vec16<T>::type& v, int k) {
+  return reinterpret_cast<T*>(&v)[k];
+}
+
+// Non-fused epilogue (matrices with long intervals): w = A r came from the
+// SpMV; q = w + beta q, p = r + beta p, p.q finished by the last block.
+template <class T, class A>
+__global__ void __launch_bounds__(kThreads) k_cg_pq(T* __restrict__ p, T* __restrict__ q, const T* __restrict__ r,
+                                                    const T* __restrict__ w, int64_t n, double* __restrict__ scal,
+                                                    A* part, unsigned* ticket) {
+  const T beta = (T)scal[S_BETA];
+  A prod = 0;
+  for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads) {
+    const T qn = fma(beta, q[i], w[i]);
+    const T pn = fma(beta, p[i], r[i]);
+    q[i] = qn;
+    p[i] = pn;
+    prod = fma((A)pn, (A)qn, prod);
+  }
+  prod = block_sum<A>(prod);
+  double tot;
+  if (finish_last_block<A>(part, prod, ticket, &tot) && threadIdx.x == 0) {
+    scal[S_PQ] = tot;
+    scal[S_ALPHA] = tot != 0.0 ? scal[S_RHO] / tot : 0.0;
+  }
+}
+
 // x += alpha p; r -= alpha q; r.r finished by the last block, which writes
-// rhonew, beta = rhonew / rho and rho = rhonew.
+// rhonew, beta = rhonew / rho and rho = rhonew. 16-byte loads and stores;
+// element i's arithmetic is the same whichever thread does it.
 template <class T, class A>
 __global__ void __launch_bounds__(kThreads) k_cg_xr_fused(T* __restrict__ x, T* __restrict__ r,
                                                           const T* __restrict__ p, const T* __restrict__ q, int64_t n,
                                                           double* __restrict__ scal, A* part, unsigned* ticket) {
+  using V = typename Vec16<T>::type;
+  constexpr int N = Vec16<T>::N;
   const T alpha = (T)scal[S_ALPHA];
   A s = 0;
-  for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads) {
+  const bool aligned = ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(r) |
+                         reinterpret_cast<uintptr_t>(p) | reinterpret_cast<uintptr_t>(q)) & 15u) == 0;
+  const int64_t nv = aligned ? n / N : 0;  // a caller's x may start anywhere: then all scalar
+  const int64_t stride = (int64_t)gridDim.x * kThreads;
+  for (int64_t v = (int64_t)blockIdx.x * kThreads + threadIdx.x; v < nv; v += stride) {
+    V xv = reinterpret_cast<const V*>(x)[v], rv = reinterpret_cast<const V*>(r)[v];
+    const V pv = reinterpret_cast<const V*>(p)[v], qv = reinterpret_cast<const V*>(q)[v];
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      lane_of<T>(xv, k) = fma(alpha, lane_of<T>(const_cast<V&>(pv), k), lane_of<T>(xv, k));
+      const T ri = fma(-alpha, lane_of<T>(const_cast<V&>(qv), k), lane_of<T>(rv, k));
+      lane_of<T>(rv, k) = ri;
+      s = fma((A)ri, (A)ri, s);
+    }
+    reinterpret_cast<V*>(x)[v] = xv;
+    reinterpret_cast<V*>(r)[v] = rv;
+  }
+  for (int64_t i = nv * N + (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += stride) {
     x[i] = fma(alpha, p[i], x[i]);
     const T ri = fma(-alpha, q[i], r[i]);
     r[i] = ri;
@@ -241,7 +296,7 @@ __global__ void __launch_bounds__(kThreads) k_cg_xr_fused(T* __restrict__ x, T* 
 }
 
 template <class T>
-cudaError_t launch_fused_spmv_dot(const spc5_matrix* M, const void* p, void* q, void* part, unsigned* ticket,
+cudaError_t launch_fused_spmv_dot(const spc5_matrix* M, const void* r, void* p, void* q, void* part, unsigned* ticket,
                                   double* scal, cudaStream_t s) {
   using V = typename T::V;
   using X = typename T::X;
@@ -251,11 +306,14 @@ cudaError_t launch_fused_spmv_dot(const spc5_matrix* M, const void* p, void* q, 
     constexpr int S = kWarp / RR;                                                                                 \
     const int64_t warps = (M->I + S - 1) / S;                                                                     \
     int64_t blocks = (warps * kWarp + kThreads - 1) / kThreads;                                                   \
-    if (blocks > (int64_t)sm_count() * 8) blocks = (int64_t)sm_count() * 8;                                       \
+    if (blocks > (int64_t)sm_count() * kSpmvBlocksPerSm) blocks = (int64_t)sm_count() * kSpmvBlocksPerSm;         \
     const unsigned grid = (unsigned)blocks;                                                                        \
-    k_cg_spmv_dot<RR, CC, T, 2><<<grid, kThreads, 0, s>>>(M->n, M->I, M->block_rowptr, M->block_colidx,           \
-                                                          M->block_masks, (const V*)M->values, M->valptr,         \
-                                                          (const X*)p, (X*)q, (A*)part, ticket, scal);            \
+    auto go = [&](auto kern) {                                                                                    \
+      kern<<<grid, kThreads, 0, s>>>(M->n, M->I, M->block_rowptr, M->block_colidx, M->block_masks,               \
+                                     (const V*)M->values, M->valptr, (const X*)r, (X*)p, (X*)q, (A*)part, ticket,  \
+                                     scal);                                                                        \
+    };                                                                                                            \
+    go(k_cg_spmv_dot<RR, CC, T, 2, false>);                                                                       \
     return cudaGetLastError();                                                                                    \
   }
   SPC5_CASE(1, 4) SPC5_CASE(1, 8) SPC5_CASE(1, 16)
@@ -282,40 +340,35 @@ cudaError_t spmv_any(const spc5_matrix* h, const void* x, void* y, cudaStream_t 
   }
 }
 
-// One CG iteration on the stream (vector type T, accumulation type A):
-// q = A p; pq; x, r update with r.r; p update. When the matrix has no long
-// intervals the iteration is three kernels (SpMV fused with p.q, the x / r
-// update fused with r.r, the p update), the scalars finished on the device.
+// One CG iteration on the stream (vector type T, accumulation type A), in
+// the order of the file comment: q = A r + beta q, p = r + beta p, p.q; then
+// x, r update with r.r. Two kernels when the matrix has no long intervals
+// (the SpMV carries the p / q update and p.q); otherwise the SpMV into w and
+// an update kernel, then the x / r kernel.
 template <class T, class A>
-cudaError_t cg_iteration(const spc5_matrix* M, T* x, T* r, T* p, T* q, int64_t n, double* scal, A* part, int nb,
-                         unsigned* ticket, cudaStream_t s) {
+cudaError_t cg_iteration(const spc5_matrix* M, T* x, T* r, T* p, T* q, T* w, int64_t n, double* scal, A* part,
+                         int nb, unsigned* ticket, cudaStream_t s) {
+  cudaError_t e;
   if (M->nseg == 0 && M->I > 0) {
-    cudaError_t e;
     if (M->vt == SPC5_F64)
-      e = launch_fused_spmv_dot<F64>(M, p, q, part, ticket, scal, s);
+      e = launch_fused_spmv_dot<F64>(M, r, p, q, part, ticket, scal, s);
     else if (M->vt == SPC5_F32)
-      e = launch_fused_spmv_dot<F32>(M, p, q, part, ticket, scal, s);
+      e = launch_fused_spmv_dot<F32>(M, r, p, q, part, ticket, scal, s);
     else
-      e = launch_fused_spmv_dot<BF16>(M, p, q, part, ticket, scal, s);
-    if (e != cudaSuccess) return e;
-    k_cg_xr_fused<T, A><<<nb, kThreads, 0, s>>>(x, r, p, q, n, scal, part, ticket);
-    k_cg_p<T><<<nb, kThreads, 0, s>>>(p, r, n, scal);
-    return cudaGetLastError();
+      e = launch_fused_spmv_dot<BF16>(M, r, p, q, part, ticket, scal, s);
+  } else {
+    e = spmv_any(M, r, w, s);
+    if (e == cudaSuccess) k_cg_pq<T, A><<<nb, kThreads, 0, s>>>(p, q, r, w, n, scal, part, ticket);
   }
-  cudaError_t e = spmv_any(M, p, q, s);
   if (e != cudaSuccess) return e;
-  k_dot_part<T, A><<<nb, kThreads, 0, s>>>(p, q, n, part);
-  k_dot_final<A><<<1, kThreads, 0, s>>>(part, nb, scal, S_PQ);
-  k_cg_xr<T, A><<<nb, kThreads, 0, s>>>(x, r, p, q, n, scal, part);
-  k_dot_final<A><<<1, kThreads, 0, s>>>(part, nb, scal, S_RHONEW);
-  k_cg_p<T><<<nb, kThreads, 0, s>>>(p, r, n, scal);
+  k_cg_xr_fused<T, A><<<nb, kThreads, 0, s>>>(x, r, p, q, n, scal, part, ticket);
   return cudaGetLastError();
 }
 
 // Runs CG iterations until sqrt(rho) <= stop or max_it; iteration body
 // replayed from a CUDA graph when use_graph. Returns iterations done.
 template <class T, class A>
-spc5_status cg_loop(const spc5_matrix* M, T* x, T* r, T* p, T* q, int64_t n, double* scal, A* part, int nb,
+spc5_status cg_loop(const spc5_matrix* M, T* x, T* r, T* p, T* q, T* w, int64_t n, double* scal, A* part, int nb,
                     unsigned* ticket, double stop, int max_it, int check_every, bool use_graph, double* host_scal,
                     cudaStream_t s, int* iters) {
   cudaGraphExec_t exec = nullptr;
@@ -323,7 +376,7 @@ spc5_status cg_loop(const spc5_matrix* M, T* x, T* r, T* p, T* q, int64_t n, dou
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(e, "cg: begin capture");
-    cudaError_t e2 = cg_iteration<T, A>(M, x, r, p, q, n, scal, part, nb, ticket, s);
+    cudaError_t e2 = cg_iteration<T, A>(M, x, r, p, q, w, n, scal, part, nb, ticket, s);
     e = cudaStreamEndCapture(s, &g);
     if (e2 != cudaSuccess) {
       if (g) cudaGraphDestroy(g);
@@ -346,7 +399,7 @@ spc5_status cg_loop(const spc5_matrix* M, T* x, T* r, T* p, T* q, int64_t n, dou
     if (batch > max_it - k) batch = max_it - k;
     cudaError_t e = cudaSuccess;
     for (int j = 0; j < batch && e == cudaSuccess; ++j)
-      e = use_graph ? cudaGraphLaunch(exec, s) : cg_iteration<T, A>(M, x, r, p, q, n, scal, part, nb, ticket, s);
+      e = use_graph ? cudaGraphLaunch(exec, s) : cg_iteration<T, A>(M, x, r, p, q, w, n, scal, part, nb, ticket, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(host_scal, scal, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
@@ -377,10 +430,10 @@ spc5_status cg_loop(const spc5_matrix* M, T* x, T* r, T* p, T* q, int64_t n, dou
 spc5_status cg_impl(const spc5_matrix* A, const spc5_matrix* L, const double* b, double* x, const spc5_cg_opts* o,
                     spc5_cg_info* info, cudaStream_t user) {
   const int64_t n = A->n;
-  // vector kernels: grid-stride, at most 8 CTAs per SM (each CTA adds one
-  // partial and one ticket to the reductions)
+  // vector kernels: grid-stride, at most kVecBlocksPerSm CTAs per SM (each
+  // CTA adds one partial and one ticket to the reductions)
   int64_t nb64 = (n + kThreads - 1) / kThreads;
-  if (nb64 > (int64_t)sm_count() * 8) nb64 = (int64_t)sm_count() * 8;
+  if (nb64 > (int64_t)sm_count() * kVecBlocksPerSm) nb64 = (int64_t)sm_count() * kVecBlocksPerSm;
   const int nb = nb64 > 0 ? (int)nb64 : 1;
   const double tol = o->tol > 0 ? o->tol : 1e-10;
   const int max_it = o->max_iters > 0 ? o->max_iters : 100000;
@@ -456,19 +509,21 @@ spc5_status cg_impl(const spc5_matrix* A, const spc5_matrix* L, const double* b,
   const double stop = tol * bnorm;
   spc5_status st = SPC5_OK;
   if (!L) {
-    // float64 CG from x = 0: r = p = b, rho = b.b
+    // float64 CG from x = 0: r = b, p = q = 0, beta = 0 (scal cleared), rho = b.b
     k_copy_vec<double><<<nb, kThreads, 0, s>>>(r, b, n);
-    k_copy_vec<double><<<nb, kThreads, 0, s>>>(p, b, n);
+    k_zero_vec<double><<<nb, kThreads, 0, s>>>(p, n);
+    k_zero_vec<double><<<nb, kThreads, 0, s>>>(q, n);
     k_dot_part<double, double><<<nb, kThreads, 0, s>>>(r, r, n, part);
     k_dot_final<double><<<1, kThreads, 0, s>>>(part, nb, scal, S_RHO);
     int it = 0;
-    st = cg_loop<double, double>(A, x, r, p, q, n, scal, part, nb, ticket, stop, max_it, every, use_graph, hs, s,
+    st = cg_loop<double, double>(A, x, r, p, q, t, n, scal, part, nb, ticket, stop, max_it, every, use_graph, hs, s,
                                  &it);
     info->iterations = it;
   } else {
-    Buf r32_b, p32_b, q32_b, x32_b, part32_b;
+    Buf r32_b, p32_b, q32_b, x32_b, w32_b, part32_b;
     e = r32_b.alloc(sizeof(float) * (size_t)n);
     if (e == cudaSuccess) e = p32_b.alloc(sizeof(float) * (size_t)n);
+    if (e == cudaSuccess) e = w32_b.alloc(sizeof(float) * (size_t)n);
     if (e == cudaSuccess) e = q32_b.alloc(sizeof(float) * (size_t)n);
     if (e == cudaSuccess) e = x32_b.alloc(sizeof(float) * (size_t)n);
     if (e == cudaSuccess) e = part32_b.alloc(sizeof(float) * (size_t)nparts);
@@ -477,6 +532,7 @@ spc5_status cg_impl(const spc5_matrix* A, const spc5_matrix* L, const double* b,
     float* p32 = (float*)p32_b.p;
     float* q32 = (float*)q32_b.p;
     float* x32 = (float*)x32_b.p;
+    float* w32 = (float*)w32_b.p;
     float* part32 = (float*)part32_b.p;
     // r = b (x = 0)
     k_copy_vec<double><<<nb, kThreads, 0, s>>>(r, b, n);
@@ -490,7 +546,7 @@ spc5_status cg_impl(const spc5_matrix* A, const spc5_matrix* L, const double* b,
       if (info->inner_total >= max_it) break;
       const double hs_norm = hs[S_NORM];
       // inner CG in float32 on A_low d = r / ||r||, from d = 0
-      k_inner_start<<<nb, kThreads, 0, s>>>(r, r32, p32, x32, n, scal);
+      k_inner_start<<<nb, kThreads, 0, s>>>(r, r32, p32, q32, x32, n, scal);
       k_dot_part<float, float><<<nb, kThreads, 0, s>>>(r32, r32, n, part32);
       k_dot_final<float><<<1, kThreads, 0, s>>>(part32, nb, scal, S_RHO);
       e = cudaMemcpyAsync(hs, scal, sizeof(hs), cudaMemcpyDeviceToHost, s);
@@ -504,7 +560,7 @@ spc5_status cg_impl(const spc5_matrix* A, const spc5_matrix* L, const double* b,
       double itol = 0.5 * stop / sqrt(hs_norm);
       if (itol < inner_tol) itol = inner_tol;
       if (itol > 0.5) itol = 0.5;
-      st = cg_loop<float, float>(L, x32, r32, p32, q32, n, scal, part32, nb, ticket, itol * sqrt(hs[S_RHO]), budget,
+      st = cg_loop<float, float>(L, x32, r32, p32, q32, w32, n, scal, part32, nb, ticket, itol * sqrt(hs[S_RHO]), budget,
                                  every, use_graph, hs, s, &it);
       if (st != SPC5_OK) return st;
       info->inner_total += it;

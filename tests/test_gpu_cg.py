@@ -87,6 +87,25 @@ def test_cg_full_size_poisson96(cuda_device):
     assert im["converged"] and true_residual(A, xm.cpu().numpy(), b) <= 1e-10
 
 
+def test_cg_with_long_interval_segments(cuda_device):
+    # every interval with more than 2 blocks on the segment path: the iteration
+    # then runs the SpMV and the p / q update as separate kernels
+    A = poisson(16)
+    b = inputs.vec_uniform(A.n, seed=5)
+    d64 = spc5.upload_csr(A, torch.float64, "cuda")
+    d32 = spc5.upload_csr(A, torch.float32, "cuda")
+    M64 = spc5.convert(d64.rowptr, d64.colidx, d64.values, A.n, A.m, 2, 4, long_blocks=2, seg_blocks=3)
+    M32 = spc5.convert(d32.rowptr, d32.colidx, d32.values, A.n, A.m, 2, 4, long_blocks=2, seg_blocks=3)
+    assert M64.export()["nsegments"] > 0
+    bd = torch.from_numpy(b).cuda()
+    x, info = spc5.cg(M64, bd, tol=1e-10, use_graph=True)
+    _, k_ref, _ = ocg.cg(A, b, tol=1e-10)
+    assert info["converged"] and abs(info["iterations"] - k_ref) <= 8
+    assert true_residual(A, x.cpu().numpy(), b) <= 1.05e-10
+    xm, im = spc5.cg(M64, bd, A_inner=M32, tol=1e-10, use_graph=True)
+    assert im["converged"] and true_residual(A, xm.cpu().numpy(), b) <= 1e-10
+
+
 def test_cg_rejects_bad_handles(cuda_device):
     A = poisson(6)
     M64, M32 = handles(A)
