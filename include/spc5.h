@@ -73,7 +73,11 @@ typedef struct {
    *   12 / 14 natural order, block masks read as 8-byte windows of 8/mb
    *           blocks (no memory round trip per block; for low fill),
    *           4 / 2 nonzeros per trip;
-   *   13 / 15 sorted work order with mask windows, 4 / 2 nonzeros per trip.
+   *   13 / 15 sorted work order with mask windows, 4 / 2 nonzeros per trip;
+   *   16 / 17 natural / sorted order, the c bit positions of a block row
+   *           unrolled (fewest instructions for well-filled blocks; the
+   *           float32 / bfloat16 choice). spc5_cg uses 16's decode too when
+   *           its handle has variant 16, the flattened one otherwise.
    * All variants compute the same sums in the same order per row. */
   int32_t variant;
   /* Rows per sorting window of the work order of variants 9, 10, 13, 15:
@@ -133,7 +137,7 @@ spc5_status spc5_spmv_acc(spc5_handle h, const void* x_d, void* y_d, spc5_stream
 
 /*
  * spc5_set_variant - switch the short-interval kernel variant of a handle
- * (values as in spc5_opts.variant). Selecting 9 or 10 builds the sorted work
+ * (values as in spc5_opts.variant). Selecting 9, 10, 13, 15 or 17 builds the sorted work
  * order if the handle has none yet (synchronises `stream`); the other values
  * take effect with no device work. SPC5_EINVAL for an unknown variant.
  */

@@ -167,7 +167,7 @@ __device__ __forceinline__ bool finish_last_block(A* part, A mine, unsigned* tic
 // q = A r + beta q and p = r + beta p over the short intervals, one lane per
 // row (the SpMV kernel's row sum applied to r), fused with p.q; the last
 // block writes scal[PQ] and scal[ALPHA].
-template <int R, int C, class T, int U, bool WIN>
+template <int R, int C, class T, int U, int DEC>
 __global__ void __launch_bounds__(kThreads) k_cg_spmv_dot(int64_t n, int64_t I, const int32_t* __restrict__ brp,
                                                           const int32_t* __restrict__ bcol,
                                                           const uint8_t* __restrict__ bmask,
@@ -191,7 +191,7 @@ __global__ void __launch_bounds__(kThreads) k_cg_spmv_dot(int64_t n, int64_t I, 
     const int64_t it = task * S + lane / R;
     if (it < I) {
       const int32_t b = __ldg(brp + it), bend = __ldg(brp + it + 1);
-      const A acc = row_sum<R, C, T, U, WIN>(i, b, bend, val + __ldg(valptr + it), bcol, bmask, r);
+      const A acc = row_sum<R, C, T, U, DEC>(i, b, bend, val + __ldg(valptr + it), bcol, bmask, r);
       const int64_t row = it * R + i;
       if (row < n) {
         const X qn = fma(beta, q[row], (X)acc);
@@ -313,7 +313,10 @@ cudaError_t launch_fused_spmv_dot(const spc5_matrix* M, const void* r, void* p, 
                                      (const V*)M->values, M->valptr, (const X*)r, (X*)p, (X*)q, (A*)part, ticket,  \
                                      scal);                                                                        \
     };                                                                                                            \
-    go(k_cg_spmv_dot<RR, CC, T, 2, false>);                                                                       \
+    if (M->variant == 16)                                                                                         \
+      go(k_cg_spmv_dot<RR, CC, T, 1, 2>);                                                                         \
+    else                                                                                                          \
+      go(k_cg_spmv_dot<RR, CC, T, 2, 0>);                                                                         \
     return cudaGetLastError();                                                                                    \
   }
   SPC5_CASE(1, 4) SPC5_CASE(1, 8) SPC5_CASE(1, 16)

@@ -338,13 +338,57 @@ __device__ __forceinline__ typename T::A row_sum_w(int i, int32_t b, int32_t ben
   return acc;
 }
 
+// Same sum again, block by block with the C bit positions of the block row
+// unrolled at compile time (the column of position k is col0 + k, an
+// immediate offset from the block's x window). No per-nonzero bit search or
+// loop trip: fewer instructions per stored value when blocks are well filled
+// and multiply-adds are cheap (float32 / bfloat16), but every position costs
+// a predicated slot, so float64 - where a multiply-add occupies the float64
+// pipe whatever the active lanes - usually prefers the flattened forms.
+template <int R, int C, class T>
+__device__ __forceinline__ typename T::A row_sum_e(int i, int32_t b, int32_t bend,
+                                                   const typename T::V* __restrict__ vrow,
+                                                   const int32_t* __restrict__ bcol, const uint8_t* __restrict__ bmask,
+                                                   const typename T::X* __restrict__ x) {
+  constexpr int MB = (R * C + 7) / 8;
+  using A = typename T::A;
+  A acc = 0;
+  int32_t vbase = 0;
+  Mask<MB> nmk = b < bend ? load_mask<MB>(bmask, b) : zero_mask<MB>();
+  int32_t ncol = b < bend ? __ldg(bcol + b) : 0;
+  for (; b < bend; ++b) {
+    const Mask<MB> mk = nmk;
+    const int32_t col0 = ncol;
+    if (b + 1 < bend) {  // next block's mask and column one block ahead
+      nmk = load_mask<MB>(bmask, b + 1);
+      ncol = __ldg(bcol + b + 1);
+    }
+    const uint32_t rbits = row_bits<C>(mk, i);
+    int32_t vo = vbase + popc_below<C>(mk, i);
+    vbase += popc_all(mk);
+    const typename T::X* __restrict__ xw = x + col0;
+#pragma unroll
+    for (int k = 0; k < C; ++k) {
+      if (rbits & (1u << k)) {
+        acc = fmadd<T>(T::val(vrow, vo), T::xv(xw, k), acc);
+        ++vo;
+      }
+    }
+  }
+  return acc;
+}
+
 // row_sum_w where a window fits the shape's masks (up to 64 mask bits per
 // block), row_sum_u otherwise
-template <int R, int C, class T, int U, bool WIN>
+// DEC selects the decode: 0 row_sum_u, 1 row_sum_w (row_sum_u where a window
+// cannot hold a block's masks, above 64 mask bits), 2 row_sum_e.
+template <int R, int C, class T, int U, int DEC>
 __device__ __forceinline__ typename T::A row_sum(int i, int32_t b, int32_t bend, const typename T::V* __restrict__ vrow,
                                                  const int32_t* __restrict__ bcol, const uint8_t* __restrict__ bmask,
                                                  const typename T::X* __restrict__ x) {
-  if constexpr (WIN && R * C <= 64)
+  if constexpr (DEC == 2)
+    return row_sum_e<R, C, T>(i, b, bend, vrow, bcol, bmask, x);
+  else if constexpr (DEC == 1 && R * C <= 64)
     return row_sum_w<R, C, T, U>(i, b, bend, vrow, bcol, bmask, x);
   else
     return row_sum_u<R, C, T, U>(i, b, bend, vrow, bcol, bmask, x);
@@ -360,8 +404,8 @@ __device__ __forceinline__ typename T::A row_sum(int i, int32_t b, int32_t bend,
 //
 // With ORDER, lane slot q of the warp takes interval order[q] instead of q
 // (the sorted work order built at conversion; long intervals are not in it).
-// With WIN the row is decoded from mask windows (row_sum_w).
-template <int R, int C, class T, bool ACCUM, int U, bool ORDER, bool WIN>
+// DEC picks the row decode (see row_sum).
+template <int R, int C, class T, bool ACCUM, int U, bool ORDER, int DEC>
 __global__ void __launch_bounds__(256) k_spmv_rows_u(int64_t n, int64_t I, int32_t long_blocks, int64_t long_values,
                                                      const int32_t* __restrict__ brp, const int32_t* __restrict__ bcol,
                                                      const uint8_t* __restrict__ bmask,
@@ -385,7 +429,7 @@ __global__ void __launch_bounds__(256) k_spmv_rows_u(int64_t n, int64_t I, int32
   const int32_t bend = __ldg(brp + it + 1);
   const int64_t vbase0 = __ldg(valptr + it);
   if (bend - b > long_blocks || __ldg(valptr + it + 1) - vbase0 > long_values) return;  // the segment path's
-  const typename T::A acc = row_sum<R, C, T, U, WIN>(i, b, bend, val + vbase0, bcol, bmask, x);
+  const typename T::A acc = row_sum<R, C, T, U, DEC>(i, b, bend, val + vbase0, bcol, bmask, x);
   const int64_t row = it * R + i;
   if (row < n) {
     if (ACCUM)
@@ -406,7 +450,7 @@ __global__ void __launch_bounds__(256) k_spmv_rows_u(int64_t n, int64_t I, int32
 // (Measured on GB300: giving each lane a whole segment instead, like a short
 // interval, is about 1.35x slower on power-law rows; the warp's lanes then
 // stream 32 separate stretches of memory.)
-template <int R, int C, class T, int U, bool WIN>
+template <int R, int C, class T, int U, int DEC>
 __global__ void __launch_bounds__(256) k_spmv_segments(int64_t nseg, const Segment* __restrict__ segs,
                                                        const int32_t* __restrict__ bcol, const uint8_t* __restrict__ bmask,
                                                        const typename T::V* __restrict__ val,
@@ -443,7 +487,7 @@ __global__ void __launch_bounds__(256) k_spmv_segments(int64_t nseg, const Segme
     const int t = __shfl_up_sync(0xffffffffu, incl, d);
     if (lane >= d) incl += t;
   }
-  typename T::A acc = row_sum<R, C, T, U, WIN>(i, rb, re, val + sg.v_begin + (incl - cnt), bcol, bmask, x);
+  typename T::A acc = row_sum<R, C, T, U, DEC>(i, rb, re, val + sg.v_begin + (incl - cnt), bcol, bmask, x);
 #pragma unroll
   for (int d = kWarp / 2; d >= R; d >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, d);
   if (lane < R) partials[seg * R + lane] = acc;
@@ -520,7 +564,8 @@ __global__ void __launch_bounds__(256) k_spmv_fixup(int64_t n, int64_t nlong, co
 // --------------------------------------------------------------- launch
 // Variants of the short-interval kernel: 1 plain; 0/5 natural order U=2;
 // 3 natural U=4; 9/10 sorted order U=2/U=4; 12/14 natural order, mask
-// windows, U=4/U=2; 13/15 sorted order, mask windows, U=4/U=2. (Measured:
+// windows, U=4/U=2; 13/15 sorted order, mask windows, U=4/U=2; 16/17
+// natural / sorted order, bit positions unrolled (row_sum_e). (Measured:
 // 8 nonzeros per trip is slower than 2 or 4 on every test matrix.)
 // `partials` is the segment scratch (n_segments * r accumulators).
 template <int R, int C, class T>
@@ -544,8 +589,8 @@ cudaError_t launch_beta(const spc5_matrix* h, const void* xv, void* yv, bool acc
       kern<<<grid, threads, 0, s>>>(h->n, h->I, h->long_blocks, h->long_values, h->block_rowptr, h->block_colidx,
                                     h->block_masks, val, h->valptr, x, y, order, norder);
     };
-#define SPC5_GO(U, ORD, WIN) \
-  (acc ? go(k_spmv_rows_u<R, C, T, true, U, ORD, WIN>) : go(k_spmv_rows_u<R, C, T, false, U, ORD, WIN>))
+#define SPC5_GO(U, ORD, DEC) \
+  (acc ? go(k_spmv_rows_u<R, C, T, true, U, ORD, DEC>) : go(k_spmv_rows_u<R, C, T, false, U, ORD, DEC>))
     if (v == 1) {
       if (acc)
         k_spmv_rows<R, C, T, true><<<grid, threads, 0, s>>>(h->n, h->I, h->long_blocks, h->long_values, h->block_rowptr,
@@ -554,23 +599,25 @@ cudaError_t launch_beta(const spc5_matrix* h, const void* xv, void* yv, bool acc
         k_spmv_rows<R, C, T, false><<<grid, threads, 0, s>>>(h->n, h->I, h->long_blocks, h->long_values, h->block_rowptr,
                                                              h->block_colidx, h->block_masks, val, h->valptr, x, y);
     } else if (ordered) {
-      if (v == 10) SPC5_GO(4, true, false);
-      else if (v == 13) SPC5_GO(4, true, true);
-      else if (v == 15) SPC5_GO(2, true, true);
-      else SPC5_GO(2, true, false);
+      if (v == 10) SPC5_GO(4, true, 0);
+      else if (v == 13) SPC5_GO(4, true, 1);
+      else if (v == 15) SPC5_GO(2, true, 1);
+      else if (v == 17) SPC5_GO(1, true, 2);
+      else SPC5_GO(2, true, 0);
     } else {
-      if (v == 3) SPC5_GO(4, false, false);
-      else if (v == 12) SPC5_GO(4, false, true);
-      else if (v == 14) SPC5_GO(2, false, true);
-      else SPC5_GO(2, false, false);
+      if (v == 3) SPC5_GO(4, false, 0);
+      else if (v == 12) SPC5_GO(4, false, 1);
+      else if (v == 14) SPC5_GO(2, false, 1);
+      else if (v == 16) SPC5_GO(1, false, 2);
+      else SPC5_GO(2, false, 0);
     }
 #undef SPC5_GO
   }
   if (h->nseg > 0) {
     A* part = static_cast<A*>(partials);
     const unsigned grid = (unsigned)((h->nseg * kWarp + threads - 1) / threads);
-    k_spmv_segments<R, C, T, 4, true><<<grid, threads, 0, s>>>(h->nseg, h->segs, h->block_colidx, h->block_masks, val,
-                                                               x, part);
+    k_spmv_segments<R, C, T, 4, 1><<<grid, threads, 0, s>>>(h->nseg, h->segs, h->block_colidx, h->block_masks, val, x,
+                                                            part);
     const unsigned g2 = (unsigned)((h->nlong + 255) / 256);
     if (acc)
       k_spmv_fixup<R, T, true><<<g2, 256, 0, s>>>(h->n, h->nlong, h->seg_first, h->segs, part, y);
