@@ -39,7 +39,8 @@ L2_FLUSH_BYTES = 512 << 20
 FP64_PEAK_GFLOPS = 1250.0  # nominal GB300 float64 rate (2 FMA lanes/clk/SM x 152 SMs x 2.07 GHz x 2)
 # short-interval kernel variants the tuner tries per shape: float64 keeps to the
 # flattened decodes (16's unrolled positions cost float64 pipe slots when empty)
-VARIANTS = {"f64": (5, 10, 13, 15), "f32": (5, 10, 13, 15, 16)}
+VARIANTS = {"f64": (5, 10, 13, 15), "f32": (5, 10, 13, 15, 16, 18)}
+CG_INNER_VARIANT = 18  # decode of the float32 / bfloat16 inner CG handle (unrolled positions, two blocks a trip)
 
 
 def parse():
@@ -61,10 +62,12 @@ def parse():
     p.add_argument("--seg-blocks", type=int, default=0, help="profiling run: blocks per long-interval segment")
     p.add_argument("--long-blocks", type=int, default=0, help="profiling run: long-interval threshold in blocks")
     p.add_argument("--cg-profile", action="store_true", help="run the CG solvers once each with timings")
+    p.add_argument("--unit-rates", action="store_true",
+                   help="measure the float64 / float32 multiply-add rates (1..32 active lanes) and the copy ceiling")
     p.add_argument("--cg-n", type=int, default=96, help="grid edge of the CG profiling matrix")
     p.add_argument("--cg-every", type=int, default=8)
     p.add_argument("--cg-graph", type=int, default=1)
-    p.add_argument("--cg-variant", type=int, default=0, help="kernel variant of the CG profiling handles")
+    p.add_argument("--cg-variant", type=int, default=18, help="kernel variant of the inner (float32) CG handle")
     p.add_argument("--cg-shape", default="2x4", help="block shape of the CG profiling handles")
     return p.parse_args()
 
@@ -406,9 +409,10 @@ def run_cg_section(dev, reps: int = 3):
     hs = {}
     for name, dt in (("f64", torch.float64), ("f32", torch.float32), ("bf16", torch.bfloat16)):
         d = spc5.upload_csr(A, dt, dev)
-        hs[name] = spc5.convert(d.rowptr, d.colidx, d.values, A.n, A.m, 2, 4)
+        hs[name] = spc5.convert(d.rowptr, d.colidx, d.values, A.n, A.m, 2, 4,
+                                variant=0 if name == "f64" else CG_INNER_VARIANT)
     out = {"workload": "7-point Poisson 96^3 (n=884,736, nnz=6,137,856), b uniform[-1,1] seed 0, tol 1e-10",
-           "format": "beta(2,4)"}
+           "format": f"beta(2,4); float64 handle variant 5, inner handles variant {CG_INNER_VARIANT}"}
     for label, inner in (("fp64_cg", None), ("mixed_f32", hs["f32"]), ("mixed_bf16", hs["bf16"])):
         ts, info = [], None
         for _ in range(reps):
@@ -480,6 +484,34 @@ def run_profile(args):
     return 0
 
 
+def run_unit_rates():
+    """Arithmetic and copy rates of this GPU through the library's probe kernels:
+    multiply-add rate with 1, 8, 16 and 32 active lanes per warp (only active
+    lanes' FMAs counted), and the streaming copy (read + write bytes)."""
+    import torch
+
+    from paper_1801_01134_gb300 import spc5
+
+    spc5.load()
+    out = {"gpu": torch.cuda.get_device_name(0)}
+    for name, dt in (("f64", torch.float64), ("f32", torch.float32)):
+        out[f"fma_{name}_gflops"] = {str(ln): round(spc5.fma_rate(dt, lanes=ln), 1) for ln in (1, 8, 16, 32)}
+    n = 1 << 28  # 1 GiB of int32 per buffer
+    a = torch.empty(n, dtype=torch.int32, device="cuda")
+    b = torch.empty_like(a)
+    ts = []
+    for _ in range(6):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        spc5.copy(a, b)
+        e1.record()
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    out["copy_gbs"] = round(2 * 4 * n / (min(ts[1:]) * 1e-3) / 1e9, 1)
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 # ------------------------------------------------------------------------ ours
 
 def main():
@@ -488,6 +520,8 @@ def main():
         return run_reference(args)
     if args.profile:
         return run_profile(args)
+    if args.unit_rates:
+        return run_unit_rates()
     if args.cg_profile:
         import torch
 
@@ -502,7 +536,9 @@ def main():
         for name, dt in (("f64", torch.float64), ("f32", torch.float32)):
             d = spc5.upload_csr(A, dt, dev)
             r, c = (int(v) for v in args.cg_shape.split("x"))
-            hs[name] = spc5.convert(d.rowptr, d.colidx, d.values, A.n, A.m, r, c, variant=args.cg_variant)
+            # --cg-variant sets the inner (float32) handle; the float64 handle keeps the default
+            hs[name] = spc5.convert(d.rowptr, d.colidx, d.values, A.n, A.m, r, c,
+                                    variant=0 if name == "f64" else args.cg_variant)
         for label, inner in (("fp64_cg", None), ("mixed_f32", hs["f32"])):
             for rep in range(2):
                 t0 = time.perf_counter()

@@ -76,8 +76,10 @@ typedef struct {
    *   13 / 15 sorted work order with mask windows, 4 / 2 nonzeros per trip;
    *   16 / 17 natural / sorted order, the c bit positions of a block row
    *           unrolled (fewest instructions for well-filled blocks; the
-   *           float32 / bfloat16 choice). spc5_cg uses 16's decode too when
-   *           its handle has variant 16, the flattened one otherwise.
+   *           float32 / bfloat16 choice);
+   *   18 / 19 as 16 / 17 with two blocks per loop trip (c <= 8).
+   * spc5_cg uses the decode of 16 or 18 when its handle has that variant,
+   * the flattened one otherwise.
    * All variants compute the same sums in the same order per row. */
   int32_t variant;
   /* Rows per sorting window of the work order of variants 9, 10, 13, 15:
@@ -137,7 +139,7 @@ spc5_status spc5_spmv_acc(spc5_handle h, const void* x_d, void* y_d, spc5_stream
 
 /*
  * spc5_set_variant - switch the short-interval kernel variant of a handle
- * (values as in spc5_opts.variant). Selecting 9, 10, 13, 15 or 17 builds the sorted work
+ * (values as in spc5_opts.variant). Selecting 9, 10, 13, 15, 17 or 19 builds the sorted work
  * order if the handle has none yet (synchronises `stream`); the other values
  * take effect with no device work. SPC5_EINVAL for an unknown variant.
  */
@@ -391,6 +393,16 @@ spc5_status spc5_select(int64_t n, int64_t m, int64_t nnz, const int64_t* rowptr
  * of at least 256 elements of the type (written only in an impossible case).
  */
 spc5_status spc5_fma_rate(spc5_dtype vt, int64_t iters, void* sink_d, int64_t* fmas_out, spc5_stream_t stream);
+
+/*
+ * spc5_fma_rate_lanes - the same probe with only lanes 0..lanes-1 of every
+ * warp doing arithmetic (1 <= lanes <= 32; the others skip the loop while
+ * their warp issues it). *fmas_out counts the active lanes' multiply-adds
+ * only, so the rate shows what a partly filled warp instruction costs.
+ * SPC5_EINVAL for lanes outside [1, 32] or the errors of spc5_fma_rate.
+ */
+spc5_status spc5_fma_rate_lanes(spc5_dtype vt, int64_t iters, int lanes, void* sink_d, int64_t* fmas_out,
+                                spc5_stream_t stream);
 
 #ifdef __cplusplus
 }

@@ -77,7 +77,7 @@ spc5_status spc5_convert(int64_t n, int64_t m, int64_t nnz, const int64_t* rowpt
   if (vt != SPC5_F64 && vt != SPC5_F32 && vt != SPC5_BF16) return fail(SPC5_EUNSUPPORTED, "convert: value type");
   if (opt && (opt->long_blocks < 0 || opt->seg_blocks < 0)) return fail(SPC5_EINVAL, "convert: negative option");
   if (opt && !valid_variant(opt->variant))
-    return fail(SPC5_EINVAL, "convert: variant must be 0, 1, 3, 5, 9, 10 or 12..17");
+    return fail(SPC5_EINVAL, "convert: variant must be 0, 1, 3, 5, 9, 10 or 12..19");
   spc5_matrix* h = nullptr;
   st = convert_impl(n, m, nnz, rowptr_d, colidx_d, values_d, vt, r, c, opt, (cudaStream_t)stream, &h);
   if (st != SPC5_OK) return st;
@@ -96,7 +96,7 @@ spc5_status spc5_spmv_acc(spc5_handle h, const void* x_d, void* y_d, spc5_stream
 spc5_status spc5_set_variant(spc5_handle h, int variant, spc5_stream_t stream) {
   if (!h) return fail(SPC5_EINVAL, "set_variant: NULL handle");
   if (!valid_variant(variant))
-    return fail(SPC5_EINVAL, "set_variant: variant must be 0, 1, 3, 5, 9, 10 or 12..17");
+    return fail(SPC5_EINVAL, "set_variant: variant must be 0, 1, 3, 5, 9, 10 or 12..19");
   if (ordered_variant(variant)) {
     spc5_status st = build_order(h, (cudaStream_t)stream);
     if (st != SPC5_OK) return st;
@@ -339,9 +339,14 @@ spc5_status spc5_select(int64_t n, int64_t m, int64_t nnz, const int64_t* rowptr
 }
 
 spc5_status spc5_fma_rate(spc5_dtype vt, int64_t iters, void* sink_d, int64_t* fmas_out, spc5_stream_t stream) {
-  if ((vt != SPC5_F64 && vt != SPC5_F32) || iters < 0 || !sink_d || !fmas_out)
+  return spc5_fma_rate_lanes(vt, iters, 32, sink_d, fmas_out, stream);
+}
+
+spc5_status spc5_fma_rate_lanes(spc5_dtype vt, int64_t iters, int lanes, void* sink_d, int64_t* fmas_out,
+                                spc5_stream_t stream) {
+  if ((vt != SPC5_F64 && vt != SPC5_F32) || iters < 0 || lanes < 1 || lanes > 32 || !sink_d || !fmas_out)
     return fail(SPC5_EINVAL, "fma_rate: bad argument");
-  cudaError_t e = launch_fma_rate(vt, iters, sink_d, fmas_out, (cudaStream_t)stream);
+  cudaError_t e = launch_fma_rate(vt, iters, lanes, sink_d, fmas_out, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "fma_rate launch");
   return SPC5_OK;
 }

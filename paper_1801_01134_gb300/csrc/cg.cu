@@ -315,6 +315,8 @@ cudaError_t launch_fused_spmv_dot(const spc5_matrix* M, const void* r, void* p, 
     };                                                                                                            \
     if (M->variant == 16)                                                                                         \
       go(k_cg_spmv_dot<RR, CC, T, 1, 2>);                                                                         \
+    else if (M->variant == 18)                                                                                    \
+      go(k_cg_spmv_dot<RR, CC, T, 1, 3>);                                                                         \
     else                                                                                                          \
       go(k_cg_spmv_dot<RR, CC, T, 2, 0>);                                                                         \
     return cudaGetLastError();                                                                                    \

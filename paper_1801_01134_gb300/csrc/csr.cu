@@ -69,10 +69,12 @@ __global__ void __launch_bounds__(512) k_copy(const int4* __restrict__ src, int4
 // path). The result is stored only if it hits an impossible value, so the
 // chains are not removed by the compiler.
 template <class A>
-__global__ void __launch_bounds__(256) k_fma_rate(int64_t iters, A a, A b, A* sink) {
+__global__ void __launch_bounds__(256) k_fma_rate(int64_t iters, int lanes, A a, A b, A* sink) {
   A c0 = (A)threadIdx.x * (A)1e-3, c1 = c0 + 1, c2 = c0 + 2, c3 = c0 + 3, c4 = c0 + 4, c5 = c0 + 5, c6 = c0 + 6,
     c7 = c0 + 7;
-  for (int64_t i = 0; i < iters; ++i) {
+  // lanes >= `lanes` of every warp skip the arithmetic (their warps still issue it)
+  const int64_t my_iters = (int)(threadIdx.x & 31) < lanes ? iters : 0;
+  for (int64_t i = 0; i < my_iters; ++i) {
     c0 = fma(c0, a, b); c1 = fma(c1, a, b); c2 = fma(c2, a, b); c3 = fma(c3, a, b);
     c4 = fma(c4, a, b); c5 = fma(c5, a, b); c6 = fma(c6, a, b); c7 = fma(c7, a, b);
   }
@@ -82,13 +84,13 @@ __global__ void __launch_bounds__(256) k_fma_rate(int64_t iters, A a, A b, A* si
 
 }  // namespace
 
-cudaError_t launch_fma_rate(spc5_dtype vt, int64_t iters, void* sink, int64_t* fmas, cudaStream_t s) {
+cudaError_t launch_fma_rate(spc5_dtype vt, int64_t iters, int lanes, void* sink, int64_t* fmas, cudaStream_t s) {
   const unsigned grid = (unsigned)(sm_count() * 8);
-  *fmas = (int64_t)grid * 256 * iters * 8;
+  *fmas = (int64_t)grid * 8 * lanes * iters * 8;  // 8 warps per CTA, `lanes` active lanes, 8 chains
   if (vt == SPC5_F64)
-    k_fma_rate<double><<<grid, 256, 0, s>>>(iters, 0.999, 1e-4, (double*)sink);
+    k_fma_rate<double><<<grid, 256, 0, s>>>(iters, lanes, 0.999, 1e-4, (double*)sink);
   else
-    k_fma_rate<float><<<grid, 256, 0, s>>>(iters, 0.999f, 1e-4f, (float*)sink);
+    k_fma_rate<float><<<grid, 256, 0, s>>>(iters, lanes, 0.999f, 1e-4f, (float*)sink);
   return cudaGetLastError();
 }
 

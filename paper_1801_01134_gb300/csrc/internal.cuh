@@ -22,10 +22,10 @@ constexpr int kOrderWindow = 4096;  // rows per sorting window of the work order
 
 // short-interval kernel variants (spc5_opts.variant)
 inline bool valid_variant(int v) {
-  return v == 0 || v == 1 || v == 3 || v == 5 || v == 9 || v == 10 || (v >= 12 && v <= 17);
+  return v == 0 || v == 1 || v == 3 || v == 5 || v == 9 || v == 10 || (v >= 12 && v <= 19);
 }
 // variants that take intervals in the sorted work order
-inline bool ordered_variant(int v) { return v == 9 || v == 10 || v == 13 || v == 15 || v == 17; }
+inline bool ordered_variant(int v) { return v == 9 || v == 10 || v == 13 || v == 15 || v == 17 || v == 19; }
 
 struct Segment {  // one warp task of a long interval
   int32_t interval;
@@ -105,7 +105,7 @@ cudaError_t launch_csr_spmv_group(int group, int64_t n, int64_t nnz, const int64
 int csr_auto_group(int64_t n, int64_t nnz, spc5_dtype vt);
 void destroy_matrix(spc5_matrix* h);
 cudaError_t launch_copy(const void* src, void* dst, int64_t bytes, cudaStream_t s);
-cudaError_t launch_fma_rate(spc5_dtype vt, int64_t iters, void* sink, int64_t* fmas, cudaStream_t s);
+cudaError_t launch_fma_rate(spc5_dtype vt, int64_t iters, int lanes, void* sink, int64_t* fmas, cudaStream_t s);
 
 // multi-RHS SpMM (spmm.cu)
 spc5_status spmm_impl(spc5_matrix* h, int k, const void* X, int64_t ldx, void* Y, int64_t ldy, int ktile,

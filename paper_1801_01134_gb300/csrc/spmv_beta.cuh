@@ -378,15 +378,82 @@ __device__ __forceinline__ typename T::A row_sum_e(int i, int32_t b, int32_t ben
   return acc;
 }
 
+// row_sum_e taking two blocks per trip (c <= 8): the value and x loads of
+// both blocks are issued before the first multiply-add, halving the memory
+// round trips per row; the products are still added block by block, bits
+// ascending.
+template <int R, int C, class T>
+__device__ __forceinline__ typename T::A row_sum_e2(int i, int32_t b, int32_t bend,
+                                                    const typename T::V* __restrict__ vrow,
+                                                    const int32_t* __restrict__ bcol, const uint8_t* __restrict__ bmask,
+                                                    const typename T::X* __restrict__ x) {
+  constexpr int MB = (R * C + 7) / 8;
+  using A = typename T::A;
+  A acc = 0;
+  int32_t vbase = 0;
+  Mask<MB> m0 = b < bend ? load_mask<MB>(bmask, b) : zero_mask<MB>();
+  Mask<MB> m1 = b + 1 < bend ? load_mask<MB>(bmask, b + 1) : zero_mask<MB>();
+  int32_t c0 = b < bend ? __ldg(bcol + b) : 0;
+  int32_t c1 = b + 1 < bend ? __ldg(bcol + b + 1) : 0;
+  for (; b < bend; b += 2) {
+    const Mask<MB> mk0 = m0, mk1 = m1;
+    const int32_t col0 = c0, col1 = c1;
+    const bool two = b + 1 < bend;
+    if (b + 2 < bend) {  // the next pair's masks and columns one trip ahead
+      m0 = load_mask<MB>(bmask, b + 2);
+      c0 = __ldg(bcol + b + 2);
+    }
+    if (b + 3 < bend) {
+      m1 = load_mask<MB>(bmask, b + 3);
+      c1 = __ldg(bcol + b + 3);
+    }
+    const uint32_t rb0 = row_bits<C>(mk0, i);
+    const uint32_t rb1 = two ? row_bits<C>(mk1, i) : 0u;
+    int32_t vo0 = vbase + popc_below<C>(mk0, i);
+    vbase += popc_all(mk0);
+    int32_t vo1 = vbase + popc_below<C>(mk1, i);
+    vbase += two ? popc_all(mk1) : 0;
+    const typename T::X* __restrict__ xw0 = x + col0;
+    const typename T::X* __restrict__ xw1 = x + col1;
+    A v0[C], a0[C], v1[C], a1[C];
+#pragma unroll
+    for (int k = 0; k < C; ++k) {
+      if (rb0 & (1u << k)) {
+        v0[k] = T::val(vrow, vo0);
+        a0[k] = T::xv(xw0, k);
+        ++vo0;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < C; ++k) {
+      if (rb1 & (1u << k)) {
+        v1[k] = T::val(vrow, vo1);
+        a1[k] = T::xv(xw1, k);
+        ++vo1;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < C; ++k)
+      if (rb0 & (1u << k)) acc = fmadd<T>(v0[k], a0[k], acc);
+#pragma unroll
+    for (int k = 0; k < C; ++k)
+      if (rb1 & (1u << k)) acc = fmadd<T>(v1[k], a1[k], acc);
+  }
+  return acc;
+}
+
 // row_sum_w where a window fits the shape's masks (up to 64 mask bits per
 // block), row_sum_u otherwise
 // DEC selects the decode: 0 row_sum_u, 1 row_sum_w (row_sum_u where a window
-// cannot hold a block's masks, above 64 mask bits), 2 row_sum_e.
+// cannot hold a block's masks, above 64 mask bits), 2 row_sum_e, 3 row_sum_e2
+// (row_sum_e for c = 16).
 template <int R, int C, class T, int U, int DEC>
 __device__ __forceinline__ typename T::A row_sum(int i, int32_t b, int32_t bend, const typename T::V* __restrict__ vrow,
                                                  const int32_t* __restrict__ bcol, const uint8_t* __restrict__ bmask,
                                                  const typename T::X* __restrict__ x) {
-  if constexpr (DEC == 2)
+  if constexpr (DEC == 3 && C <= 8)
+    return row_sum_e2<R, C, T>(i, b, bend, vrow, bcol, bmask, x);
+  else if constexpr (DEC == 2 || DEC == 3)
     return row_sum_e<R, C, T>(i, b, bend, vrow, bcol, bmask, x);
   else if constexpr (DEC == 1 && R * C <= 64)
     return row_sum_w<R, C, T, U>(i, b, bend, vrow, bcol, bmask, x);
@@ -565,7 +632,8 @@ __global__ void __launch_bounds__(256) k_spmv_fixup(int64_t n, int64_t nlong, co
 // Variants of the short-interval kernel: 1 plain; 0/5 natural order U=2;
 // 3 natural U=4; 9/10 sorted order U=2/U=4; 12/14 natural order, mask
 // windows, U=4/U=2; 13/15 sorted order, mask windows, U=4/U=2; 16/17
-// natural / sorted order, bit positions unrolled (row_sum_e). (Measured:
+// natural / sorted order, bit positions unrolled (row_sum_e); 18/19 the same
+// two blocks per trip (row_sum_e2). (Measured:
 // 8 nonzeros per trip is slower than 2 or 4 on every test matrix.)
 // `partials` is the segment scratch (n_segments * r accumulators).
 template <int R, int C, class T>
@@ -603,12 +671,14 @@ cudaError_t launch_beta(const spc5_matrix* h, const void* xv, void* yv, bool acc
       else if (v == 13) SPC5_GO(4, true, 1);
       else if (v == 15) SPC5_GO(2, true, 1);
       else if (v == 17) SPC5_GO(1, true, 2);
+      else if (v == 19) SPC5_GO(1, true, 3);
       else SPC5_GO(2, true, 0);
     } else {
       if (v == 3) SPC5_GO(4, false, 0);
       else if (v == 12) SPC5_GO(4, false, 1);
       else if (v == 14) SPC5_GO(2, false, 1);
       else if (v == 16) SPC5_GO(1, false, 2);
+      else if (v == 18) SPC5_GO(1, false, 3);
       else SPC5_GO(2, false, 0);
     }
 #undef SPC5_GO

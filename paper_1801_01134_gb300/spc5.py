@@ -96,6 +96,7 @@ def load(build_if_missing: bool = False):
     lib.spc5_csr_spmv.argtypes = [i64, i64, i64, vp, vp, vp, i32, vp, vp, i32, vp]
     lib.spc5_copy.argtypes = [vp, vp, i64, vp]
     lib.spc5_fma_rate.argtypes = [i32, i64, vp, vp, vp]
+    lib.spc5_fma_rate_lanes.argtypes = [i32, i64, i32, vp, vp, vp]
     lib.spc5_spmv_noalloc.argtypes = [vp, vp, vp, vp]
     lib.spc5_cg.argtypes = [vp, vp, vp, vp, ctypes.POINTER(CgOpts), ctypes.POINTER(CgInfo), vp]
     lib.spc5_spmm.argtypes = [vp, i32, vp, i64, vp, i64, i32, vp]
@@ -113,7 +114,8 @@ def load(build_if_missing: bool = False):
     lib.spc5_poly_fit.argtypes = [vp, vp, i32, i32, vp]
     lib.spc5_select.argtypes = [i64, i64, i64, vp, vp, vp, i32, i32, ctypes.POINTER(Selector), vp, vp, vp, vp]
     for f in (lib.spc5_convert, lib.spc5_spmv, lib.spc5_spmv_acc, lib.spc5_export, lib.spc5_destroy, lib.spc5_set_variant,
-              lib.spc5_count_blocks, lib.spc5_csr_spmv, lib.spc5_copy, lib.spc5_fma_rate, lib.spc5_spmv_noalloc, lib.spc5_cg, lib.spc5_spmm, lib.spc5_features,
+              lib.spc5_count_blocks, lib.spc5_csr_spmv, lib.spc5_copy, lib.spc5_fma_rate, lib.spc5_fma_rate_lanes,
+              lib.spc5_spmv_noalloc, lib.spc5_cg, lib.spc5_spmm, lib.spc5_features,
               lib.spc5_time_formats, lib.spc5_mlp_train, lib.spc5_mlp_grad, lib.spc5_mlp_infer, lib.spc5_poly_fit,
               lib.spc5_select, lib.spc5_batch_create, lib.spc5_batch_spmv, lib.spc5_batch_spmv_direct,
               lib.spc5_batch_destroy):
@@ -421,17 +423,20 @@ class Batch:
             pass
 
 
-def fma_rate(dtype: torch.dtype = torch.float64, iters: int = 4096, reps: int = 5) -> float:
-    """Measured multiply-add rate of the library's probe kernel, in GFLOP/s (2 flops per FMA)."""
+def fma_rate(dtype: torch.dtype = torch.float64, iters: int = 4096, reps: int = 5, lanes: int = 32) -> float:
+    """Measured multiply-add rate of the library's probe kernel, in GFLOP/s (2 flops per FMA),
+    with `lanes` active lanes per warp (counting only their FMAs)."""
     vt = {torch.float64: SPC5_F64, torch.float32: SPC5_F32}[dtype]
     sink = torch.empty(256, dtype=dtype, device="cuda")
     fmas = ctypes.c_int64()
-    _check(load().spc5_fma_rate(vt, 16, _ptr(sink), ctypes.byref(fmas), _stream_ptr(None)), "spc5_fma_rate")
+    _check(load().spc5_fma_rate_lanes(vt, 16, lanes, _ptr(sink), ctypes.byref(fmas), _stream_ptr(None)),
+           "spc5_fma_rate_lanes")
     best = None
     for _ in range(reps):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        _check(load().spc5_fma_rate(vt, iters, _ptr(sink), ctypes.byref(fmas), _stream_ptr(None)), "spc5_fma_rate")
+        _check(load().spc5_fma_rate_lanes(vt, iters, lanes, _ptr(sink), ctypes.byref(fmas), _stream_ptr(None)),
+               "spc5_fma_rate_lanes")
         e1.record()
         e1.synchronize()
         t = e0.elapsed_time(e1)

@@ -100,7 +100,7 @@ def test_spmv_f64(cuda_device, name, r, c):
     M.destroy()
 
 
-VARIANTS = [1, 3, 5, 9, 10, 12, 13, 14, 15, 16, 17]
+VARIANTS = [1, 3, 5, 9, 10, 12, 13, 14, 15, 16, 17, 18, 19]
 
 
 @pytest.mark.parametrize("variant", VARIANTS)
