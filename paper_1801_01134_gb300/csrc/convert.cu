@@ -3,17 +3,24 @@
 // sequential SpMVs, section "Test matrices").
 //
 // Pipeline, all on the caller's stream:
-//   1. k_validate   one thread per row: columns ascending, unique, in [0, m).
-//   2. k_count      one thread per interval: greedy leftmost cover of the
-//                   merged columns of the interval's r rows -> blocks per
+//   1. k_validate_rows / k_validate_cols: row pointers, then every entry
+//                   (in range, ascending, unique within its row), the work
+//                   spread over the entries; on any error the row-by-row
+//                   k_validate names the first bad row.
+//   2. k_count      (r > 1) one thread per interval: greedy leftmost cover of
+//                   the merged columns of the interval's r rows -> blocks per
 //                   interval, and the number of warp segments of long ones.
+//      k_r1_flags   (r = 1) block starts marked over the entries (see there).
 //   3. scan         exclusive prefix sums -> block_rowptr, segment pointers.
-//   4. k_fill       one thread per interval: the same cover again, emitting
-//                   block_colidx, the r*c-bit masks, the values in block
-//                   order (row-major inside a block) and the segment table.
+//   4. k_fill       (r > 1) one thread per interval: the same cover again,
+//                   emitting block_colidx, the r*c-bit masks, each block's
+//                   value offset and the segments; k_fill_values then moves
+//                   the values to block order (row-major inside a block),
+//                   the work spread over the entries.
+//      k_r1_fill    (r = 1) the same from the marks; values copied as-is.
 //   5. k_valptr     first value of each interval = rowptr[min(r*i, n)].
-// Steps 2 and 4 run the same device function, so the block decisions of the
-// two passes are identical by construction.
+// Steps 2 and 4 decide blocks with the same rule (the same device function
+// for r > 1, the same marks for r = 1), so the two passes agree.
 #include <algorithm>
 #include <climits>
 #include <vector>
@@ -50,6 +57,179 @@ __global__ void k_validate(int64_t n, int64_t m, int64_t nnz, const int64_t* __r
     }
   }
   if (code) atomicMin(status, (unsigned long long)i * 8ull + (unsigned long long)code);
+}
+
+// Fast validation, work spread over the entries instead of the rows (one
+// thread per row serialises on power-law hubs): k_validate_rows checks the
+// row pointer, k_validate_cols (below) every entry's range and its order
+// against the previous entry of its row. Both only detect; when either flags
+// anything the caller reruns k_validate for the canonical first bad row and
+// code.
+__global__ void k_validate_rows(int64_t n, int64_t nnz, const int64_t* __restrict__ rowptr,
+                                unsigned long long* __restrict__ status) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t a = rowptr[i], b = rowptr[i + 1];
+  if (a < 0 || b < a || b > nnz || (i == 0 && a != 0) || (i == n - 1 && b != nnz))
+    atomicMin(status, (unsigned long long)i * 8ull + (unsigned long long)SPC5_EINVAL);
+}
+
+constexpr int kEntriesPerThread = 8;  // entries per thread of the entry-parallel passes (one row search each; 32 measured slower: the walks stop coalescing)
+
+// the row holding entry j (0 <= j < rowptr[n]): the last row whose pointer is
+// <= j, which skips empty rows; stays inside [0, n-1] whatever rowptr holds
+__device__ __forceinline__ int64_t row_of_entry(const int64_t* __restrict__ rowptr, int64_t n, int64_t j) {
+  int64_t lo = 0, hi = n;
+  while (hi - lo > 1) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (rowptr[mid] <= j) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// A warp checks 2048 consecutive entries with coalesced loads: the rows that
+// start inside the chunk become a bitmap (from the row pointers), then each
+// entry is checked for range and, unless it starts a row, against its left
+// neighbour. Detection only (status set to 0 on any error).
+constexpr int kValChunk = 2048;
+
+__global__ void __launch_bounds__(256) k_validate_cols(int64_t n, int64_t m, int64_t nnz,
+                                                       const int64_t* __restrict__ rowptr,
+                                                       const int32_t* __restrict__ colidx,
+                                                       unsigned long long* __restrict__ status) {
+  __shared__ uint32_t starts[8][kValChunk / 32];
+  const int lane = threadIdx.x & 31, wb = threadIdx.x >> 5;
+  const int64_t base = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * kValChunk;
+  if (base >= nnz) return;  // whole warp
+  const int64_t end = base + kValChunk < nnz ? base + kValChunk : nnz;
+  uint32_t* st = starts[wb];
+  for (int q = lane; q < kValChunk / 32; q += 32) st[q] = 0u;
+  __syncwarp();
+  // first row whose pointer is >= base
+  int64_t lo = 0, hi = n + 1;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (rowptr[mid] < base) lo = mid + 1; else hi = mid;
+  }
+  for (int64_t q0 = lo;; q0 += 32) {
+    const int64_t q = q0 + lane;
+    const int64_t v = q <= n ? rowptr[q] : LLONG_MAX;
+    const bool in = v >= base && v < end;
+    if (in) atomicOr(&st[(v - base) >> 5], 1u << ((v - base) & 31));
+    if (!__any_sync(0xffffffffu, v < end)) break;
+  }
+  __syncwarp();
+  bool bad = false;
+#pragma unroll 4
+  for (int k = 0; k < kValChunk / 32; ++k) {
+    const int64_t j = base + k * 32 + lane;
+    const int32_t col = j < end ? colidx[j] : 0;
+    int32_t prev = __shfl_up_sync(0xffffffffu, col, 1);
+    if (lane == 0) prev = j > 0 ? colidx[j - 1] : 0;
+    if (j < end) {
+      const int o = (int)(j - base);
+      const bool row_start = (st[o >> 5] >> (o & 31)) & 1u;
+      if (col < 0 || col >= m) bad = true;
+      if (!row_start && j > 0 && col <= prev) bad = true;
+    }
+  }
+  if (__any_sync(0xffffffffu, bad) && lane == 0) atomicMin(status, 0ull);
+}
+
+// ------------------------------------------------------ one-row intervals
+// For r = 1 the cover splits at every gap of at least c between neighbouring
+// columns of a row: whichever block holds the left column ends before the
+// right one, so the right column starts a block in any cover. The runs
+// between such gaps are covered independently, so the work spreads over the
+// entries (one thread per kEntriesPerThread entries, each walking the runs
+// that start in its range) instead of one thread per row. Pass 1 marks the
+// entries that start a block; an exclusive scan of the marks numbers the
+// blocks in storage order (rows in order, blocks by column); pass 2 writes
+// each block's column, mask and, for long rows, its segment record. With one
+// row per interval the values keep CSR order and are copied as they are.
+__global__ void k_r1_flags(int64_t n, int64_t nnz, int c, const int64_t* __restrict__ rowptr,
+                           const int32_t* __restrict__ colidx, int32_t* __restrict__ flags) {
+  const int64_t j0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * kEntriesPerThread;
+  if (j0 >= nnz) return;
+  const int64_t j1 = j0 + kEntriesPerThread < nnz ? j0 + kEntriesPerThread : nnz;
+  int64_t row = row_of_entry(rowptr, n, j0);
+  int64_t rs = rowptr[row], re = rowptr[row + 1];
+  int32_t prev = j0 > rs ? colidx[j0 - 1] : 0;
+  for (int64_t j = j0; j < j1; ++j) {
+    while (j >= re) {
+      ++row;
+      rs = rowptr[row];
+      re = rowptr[row + 1];
+    }
+    const int32_t col = colidx[j];
+    const bool run_start = j == rs || col - prev >= c;
+    prev = col;
+    if (!run_start) continue;
+    // greedy cover of the run that starts here
+    int32_t s0 = col, last = col;
+    flags[j] = 1;
+    for (int64_t k = j + 1; k < re; ++k) {
+      const int32_t ck = colidx[k];
+      if (ck - last >= c) break;  // the next run
+      if (ck - s0 >= c) {
+        s0 = ck;
+        flags[k] = 1;
+      }
+      last = ck;
+    }
+  }
+}
+
+// block_rowptr[i] = blocks before row i; counts[i] = blocks of row i
+__global__ void k_r1_rowptr(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ bidx,
+                            int32_t* __restrict__ brp, int32_t* __restrict__ counts) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i > n) return;
+  const int32_t b = bidx[rowptr[i]];
+  brp[i] = b;
+  if (i < n) counts[i] = bidx[rowptr[i + 1]] - b;
+}
+
+__global__ void k_r1_fill(int64_t n, int64_t nnz, int c, int mb, int seg_blocks, const int64_t* __restrict__ rowptr,
+                          const int32_t* __restrict__ colidx, const int32_t* __restrict__ flags,
+                          const int32_t* __restrict__ bidx, const int32_t* __restrict__ brp,
+                          const int32_t* __restrict__ segptr, int32_t* __restrict__ bcol,
+                          uint8_t* __restrict__ bmask, Segment* __restrict__ segs) {
+  const int64_t j0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * kEntriesPerThread;
+  if (j0 >= nnz) return;
+  const int64_t j1 = j0 + kEntriesPerThread < nnz ? j0 + kEntriesPerThread : nnz;
+  int64_t row = row_of_entry(rowptr, n, j0);
+  int64_t re = rowptr[row + 1];
+  for (int64_t j = j0; j < j1; ++j) {
+    while (j >= re) {
+      ++row;
+      re = rowptr[row + 1];
+    }
+    if (!flags[j]) continue;
+    const int32_t b = bidx[j];
+    const int32_t s0 = colidx[j];
+    uint32_t mask = 0u;
+    for (int64_t k = j; k < re; ++k) {
+      const int32_t d = colidx[k] - s0;
+      if (d >= c) break;
+      mask |= 1u << d;
+    }
+    bcol[b] = s0;
+    bmask[(int64_t)b * mb] = (uint8_t)mask;
+    if (mb > 1) bmask[(int64_t)b * mb + 1] = (uint8_t)(mask >> 8);
+    if (segptr != nullptr && segptr[row + 1] > segptr[row]) {
+      const int32_t jb = b - brp[row];
+      if (jb % seg_blocks == 0) {
+        Segment sg;
+        sg.interval = (int32_t)row;
+        sg.b_begin = b;
+        sg.b_end = min(b + seg_blocks, brp[row + 1]);
+        sg.count = jb == 0 ? segptr[row + 1] - segptr[row] : 0;
+        sg.v_begin = j;
+        segs[segptr[row] + jb / seg_blocks] = sg;
+      }
+    }
+  }
 }
 
 // ------------------------------------------------------------ block cover
@@ -129,12 +309,14 @@ __global__ void k_seg_first(int64_t I, const int32_t* __restrict__ segptr, const
   if (it < I && flag[it]) first[pos[it]] = segptr[it];
 }
 
-template <int R, class VT>
+// Structure pass for r > 1: one thread per interval walks the cover again and
+// writes each block's column, mask, value offset inside the interval (bvo)
+// and the segment records. The values move in k_fill_values.
+template <int R>
 __global__ void k_fill(int64_t n, int64_t I, int c, int mb, int seg_blocks, const int64_t* __restrict__ rowptr,
-                       const int32_t* __restrict__ colidx, const VT* __restrict__ values,
-                       const int32_t* __restrict__ block_rowptr, const int32_t* __restrict__ segptr,
-                       int32_t* __restrict__ bcol, uint8_t* __restrict__ bmask, VT* __restrict__ bval,
-                       Segment* __restrict__ segs) {
+                       const int32_t* __restrict__ colidx, const int32_t* __restrict__ block_rowptr,
+                       const int32_t* __restrict__ segptr, int32_t* __restrict__ bcol, uint8_t* __restrict__ bmask,
+                       int32_t* __restrict__ bvo, Segment* __restrict__ segs) {
   int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (it >= I) return;
   int64_t row0 = it * R;
@@ -143,7 +325,8 @@ __global__ void k_fill(int64_t n, int64_t I, int c, int mb, int seg_blocks, cons
   int32_t bend = block_rowptr[it + 1];
   bool is_long = segptr != nullptr && segptr[it + 1] > segptr[it];
   int32_t seg0 = is_long ? segptr[it] : 0;
-  int64_t vo = rowptr[row0];  // the interval's values start where its first row starts in CSR
+  const int64_t v0 = rowptr[row0];  // the interval's values start where its first row starts in CSR
+  int64_t vo = v0;
   cover_interval<R>(rowptr, colidx, row0, rows, c, [&](int64_t s, int32_t j, const int64_t* lo, const int64_t* hi) {
     int32_t b = b0 + j;
     if (is_long && j % seg_blocks == 0) {
@@ -155,19 +338,74 @@ __global__ void k_fill(int64_t n, int64_t I, int c, int mb, int seg_blocks, cons
       sg.v_begin = vo;
       segs[seg0 + j / seg_blocks] = sg;
     }
+    bvo[b] = (int32_t)(vo - v0);
     uint32_t mw[4] = {0u, 0u, 0u, 0u};  // up to 128 mask bits
 #pragma unroll
     for (int i = 0; i < R; ++i) {
       for (int64_t p = lo[i]; p < hi[i]; ++p) {
         int bit = i * c + (int)(colidx[p] - s);
         mw[bit >> 5] |= 1u << (bit & 31);
-        bval[vo++] = values[p];
       }
+      vo += hi[i] - lo[i];
     }
     bcol[b] = (int32_t)s;
     uint8_t* dst = bmask + (int64_t)b * mb;
     for (int q = 0; q < mb; ++q) dst[q] = (uint8_t)(mw[q >> 2] >> (8 * (q & 3)));
   });
+}
+
+// Value pass for r > 1, spread over the entries (kEntriesPerThread consecutive
+// CSR entries per thread, walking rows): entry (row i of interval it, column
+// col) lies in the interval's last block starting at or before col, and its
+// place in block order is the interval's first value + the block's offset +
+// the mask bits before (i, col - start). Consecutive entries of a row move
+// through the interval's blocks in order, so only the first needs a search.
+template <int R, class VT>
+__global__ void k_fill_values(int64_t n, int64_t nnz, int c, int mb, const int64_t* __restrict__ rowptr,
+                              const int32_t* __restrict__ colidx, const VT* __restrict__ values,
+                              const int32_t* __restrict__ brp, const int32_t* __restrict__ bcol,
+                              const uint8_t* __restrict__ bmask, const int32_t* __restrict__ bvo,
+                              VT* __restrict__ bval) {
+  const int64_t j0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * kEntriesPerThread;
+  if (j0 >= nnz) return;
+  const int64_t j1 = j0 + kEntriesPerThread < nnz ? j0 + kEntriesPerThread : nnz;
+  int64_t row = row_of_entry(rowptr, n, j0);
+  int64_t re = rowptr[row + 1];
+  int64_t it = row / R, vstart = rowptr[it * R];
+  int i = (int)(row - it * R);
+  int32_t bb = brp[it], be = brp[it + 1];
+  bool fresh = true;  // block of the first entry of this row still to search
+  int32_t b = bb;
+  for (int64_t j = j0; j < j1; ++j) {
+    while (j >= re) {
+      ++row;
+      re = rowptr[row + 1];
+      it = row / R;
+      i = (int)(row - it * R);
+      vstart = rowptr[it * R];
+      bb = brp[it];
+      be = brp[it + 1];
+      fresh = true;
+    }
+    const int32_t col = colidx[j];
+    if (fresh) {  // last block of the interval starting at or before col
+      int32_t lo = bb, hi = be;
+      while (hi - lo > 1) {
+        const int32_t mid = (lo + hi) >> 1;
+        if (bcol[mid] <= col) lo = mid; else hi = mid;
+      }
+      b = lo;
+      fresh = false;
+    } else {
+      while (b + 1 < be && bcol[b + 1] <= col) ++b;
+    }
+    const int bit = i * c + (col - bcol[b]);
+    const uint8_t* mk = bmask + (int64_t)b * mb;
+    int below = 0;
+    for (int q = 0; q < (bit >> 3); ++q) below += __popc((uint32_t)mk[q]);
+    below += __popc((uint32_t)mk[bit >> 3] & ((1u << (bit & 7)) - 1u));
+    bval[vstart + bvo[b] + below] = values[j];
+  }
 }
 
 __global__ void k_valptr(int64_t n, int64_t I, int r, const int64_t* __restrict__ rowptr, int64_t* __restrict__ valptr) {
@@ -207,53 +445,119 @@ __device__ __forceinline__ int64_t block_exclusive_scan(int64_t v, int64_t* tota
   return r;
 }
 
-__global__ void k_scan_tiles(const int32_t* __restrict__ in, int64_t L, int64_t* __restrict__ out,
-                             int64_t* __restrict__ tile_sums) {
+// sum of each tile of kScanTile counts (coalesced loads)
+__global__ void k_scan_reduce(const int32_t* __restrict__ in, int64_t L, int64_t* __restrict__ tile_sums) {
   __shared__ int64_t tot;
-  int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
-  int64_t v[kScanItems];
-  int64_t s = 0;
+  const int64_t base = (int64_t)blockIdx.x * kScanTile;
+  int64_t sum = 0;
 #pragma unroll
   for (int k = 0; k < kScanItems; ++k) {
-    v[k] = base + k < L ? (int64_t)in[base + k] : 0;
-    s += v[k];
+    const int64_t i = base + k * kScanThreads + threadIdx.x;
+    sum += i < L ? (int64_t)in[i] : 0;
   }
-  int64_t pre = block_exclusive_scan(s, &tot);
-#pragma unroll
-  for (int k = 0; k < kScanItems; ++k) {
-    if (base + k < L) out[base + k] = pre;
-    pre += v[k];
-  }
+  block_exclusive_scan(sum, &tot);
   if (threadIdx.x == 0) tile_sums[blockIdx.x] = tot;
 }
 
-// one CTA: exclusive scan of the tile sums, in chunks, with a running carry
-__global__ void k_scan_tile_sums(int64_t* __restrict__ tile_sums, int64_t ntiles, int64_t* __restrict__ grand_total) {
-  __shared__ int64_t tot;
+// one CTA of 1024 threads: exclusive scan of the tile sums, 4096 per step
+// (4 consecutive per thread), with a running carry
+constexpr int kSumThreads = 1024;
+__global__ void __launch_bounds__(kSumThreads) k_scan_tile_sums(int64_t* __restrict__ tile_sums, int64_t ntiles,
+                                                               int64_t* __restrict__ grand_total) {
+  __shared__ int64_t warp_sums[kSumThreads / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   int64_t carry = 0;
-  for (int64_t base = 0; base < ntiles; base += kScanThreads) {
-    int64_t i = base + threadIdx.x;
-    int64_t v = i < ntiles ? tile_sums[i] : 0;
-    int64_t pre = block_exclusive_scan(v, &tot);
-    if (i < ntiles) tile_sums[i] = carry + pre;
-    carry += tot;
+  for (int64_t base = 0; base < ntiles; base += 4 * kSumThreads) {
+    const int64_t i0 = base + 4 * (int64_t)threadIdx.x;
+    int64_t v[4], sum = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      v[k] = i0 + k < ntiles ? tile_sums[i0 + k] : 0;
+      sum += v[k];
+    }
+    int64_t incl = sum;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int64_t t = __shfl_up_sync(0xffffffffu, incl, d);
+      if (lane >= d) incl += t;
+    }
+    if (lane == 31) warp_sums[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+      const int64_t ws = warp_sums[lane];
+      int64_t wi = ws;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const int64_t t = __shfl_up_sync(0xffffffffu, wi, d);
+        if (lane >= d) wi += t;
+      }
+      warp_sums[lane] = wi - ws;  // exclusive warp offsets; lane 31's wi is the step total
+    }
+    __syncthreads();
+    int64_t pre = carry + warp_sums[w] + (incl - sum);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      if (i0 + k < ntiles) tile_sums[i0 + k] = pre;
+      pre += v[k];
+    }
+    // the step total: the last thread's running prefix
+    __shared__ int64_t step_end;
+    if (threadIdx.x == kSumThreads - 1) step_end = pre;
+    __syncthreads();
+    carry = step_end;
     __syncthreads();
   }
   if (threadIdx.x == 0) *grand_total = carry;
 }
 
-// add tile offsets; write int32 results (caller checked the total) and the total at index L
-__global__ void k_scan_finish(const int64_t* __restrict__ part, const int64_t* __restrict__ tile_sums, int64_t L,
-                              const int64_t* __restrict__ grand_total, int32_t* __restrict__ out) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < L) out[i] = (int32_t)(part[i] + tile_sums[i / kScanTile]);
-  if (i == L) out[L] = (int32_t)*grand_total;
+// exclusive scan of each tile (coalesced loads through shared memory) plus
+// the tile's offset; int32 results (the caller checked the total), the total
+// at index L
+__global__ void k_scan_apply(const int32_t* __restrict__ in, int64_t L, const int64_t* __restrict__ tile_sums,
+                             const int64_t* __restrict__ grand_total, int32_t* __restrict__ out) {
+  __shared__ int64_t tot;
+  __shared__ int32_t tile[kScanTile];
+  const int64_t base = (int64_t)blockIdx.x * kScanTile;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    const int64_t i = base + k * kScanThreads + threadIdx.x;
+    tile[k * kScanThreads + threadIdx.x] = i < L ? in[i] : 0;
+  }
+  __syncthreads();
+  int32_t v[kScanItems];
+  int64_t sum = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    v[k] = tile[threadIdx.x * kScanItems + k];
+    sum += v[k];
+  }
+  int64_t pre = block_exclusive_scan(sum, &tot) + tile_sums[blockIdx.x];
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    tile[threadIdx.x * kScanItems + k] = (int32_t)pre;
+    pre += v[k];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    const int64_t i = base + k * kScanThreads + threadIdx.x;
+    if (i < L) out[i] = tile[k * kScanThreads + threadIdx.x];
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) out[L] = (int32_t)*grand_total;
 }
 
+// Scratch memory taken from the device's stream-ordered pool: allocation and
+// release are queued on the conversion stream, so neither waits for the GPU.
 struct DeviceBuf {
   void* p = nullptr;
+  cudaStream_t s = nullptr;
+  cudaError_t alloc(size_t bytes, cudaStream_t st) {
+    s = st;
+    return cudaMallocAsync(&p, bytes > 0 ? bytes : 16, st);
+  }
   ~DeviceBuf() {
-    if (p) cudaFree(p);
+    if (p) cudaFreeAsync(p, s);
   }
 };
 
@@ -262,24 +566,20 @@ struct DeviceBuf {
 spc5_status scan_counts(const int32_t* in, int64_t L, int32_t* out, int64_t* total_host, cudaStream_t s) {
   int64_t ntiles = (L + kScanTile - 1) / kScanTile;
   if (ntiles < 1) ntiles = 1;
-  DeviceBuf part, sums;
-  cudaError_t e = cudaMalloc(&part.p, sizeof(int64_t) * (size_t)(L > 0 ? L : 1));
+  DeviceBuf sums;
+  cudaError_t e = sums.alloc(sizeof(int64_t) * (size_t)(ntiles + 1), s);
   if (e != cudaSuccess) return cuda_fail(e, "scan scratch");
-  e = cudaMalloc(&sums.p, sizeof(int64_t) * (size_t)(ntiles + 1));
-  if (e != cudaSuccess) return cuda_fail(e, "scan scratch");
-  int64_t* p64 = (int64_t*)part.p;
   int64_t* t64 = (int64_t*)sums.p;
-  k_scan_tiles<<<(unsigned)ntiles, kScanThreads, 0, s>>>(in, L, p64, t64);
-  k_scan_tile_sums<<<1, kScanThreads, 0, s>>>(t64, ntiles, t64 + ntiles);
+  k_scan_reduce<<<(unsigned)ntiles, kScanThreads, 0, s>>>(in, L, t64);
+  k_scan_tile_sums<<<1, kSumThreads, 0, s>>>(t64, ntiles, t64 + ntiles);
   int64_t tot = 0;
   e = cudaMemcpyAsync(&tot, t64 + ntiles, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(e, "scan");
   *total_host = tot;
   if (tot > INT_MAX) return fail(SPC5_ERANGE, "prefix sum exceeds int32 (too many blocks)");
-  k_scan_finish<<<(unsigned)((L + 1 + 255) / 256), 256, 0, s>>>(p64, t64, L, t64 + ntiles, out);
+  k_scan_apply<<<(unsigned)ntiles, kScanThreads, 0, s>>>(in, L, t64, t64 + ntiles, out);
   e = cudaGetLastError();
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // scratch is freed on return
   if (e != cudaSuccess) return cuda_fail(e, "scan");
   return SPC5_OK;
 }
@@ -291,18 +591,29 @@ void launch_count(int64_t n, int64_t I, int c, const int64_t* rowptr, const int3
   k_count<R><<<(unsigned)((I + 127) / 128), 128, 0, s>>>(n, I, c, rowptr, colidx, counts);
 }
 
-template <class VT>
 void launch_fill_r(int r, int64_t n, int64_t I, int c, int mb, int sb, const int64_t* rowptr, const int32_t* colidx,
-                   const void* values, const int32_t* brp, const int32_t* segptr, spc5_matrix* h, cudaStream_t s) {
+                   const int32_t* brp, const int32_t* segptr, int32_t* bvo, spc5_matrix* h, cudaStream_t s) {
   if (I == 0) return;
   unsigned grid = (unsigned)((I + 127) / 128);
+  switch (r) {
+    case 2: k_fill<2><<<grid, 128, 0, s>>>(n, I, c, mb, sb, rowptr, colidx, brp, segptr, h->block_colidx, h->block_masks, bvo, h->segs); break;
+    case 4: k_fill<4><<<grid, 128, 0, s>>>(n, I, c, mb, sb, rowptr, colidx, brp, segptr, h->block_colidx, h->block_masks, bvo, h->segs); break;
+    default: k_fill<8><<<grid, 128, 0, s>>>(n, I, c, mb, sb, rowptr, colidx, brp, segptr, h->block_colidx, h->block_masks, bvo, h->segs); break;
+  }
+}
+
+template <class VT>
+void launch_fill_values(int r, int64_t n, int64_t nnz, int c, int mb, const int64_t* rowptr, const int32_t* colidx,
+                        const void* values, const int32_t* bvo, spc5_matrix* h, cudaStream_t s) {
+  const int64_t th = (nnz + kEntriesPerThread - 1) / kEntriesPerThread;
+  if (th == 0) return;
+  const unsigned grid = (unsigned)((th + 255) / 256);
   const VT* v = (const VT*)values;
   VT* bv = (VT*)h->values;
   switch (r) {
-    case 1: k_fill<1, VT><<<grid, 128, 0, s>>>(n, I, c, mb, sb, rowptr, colidx, v, brp, segptr, h->block_colidx, h->block_masks, bv, h->segs); break;
-    case 2: k_fill<2, VT><<<grid, 128, 0, s>>>(n, I, c, mb, sb, rowptr, colidx, v, brp, segptr, h->block_colidx, h->block_masks, bv, h->segs); break;
-    case 4: k_fill<4, VT><<<grid, 128, 0, s>>>(n, I, c, mb, sb, rowptr, colidx, v, brp, segptr, h->block_colidx, h->block_masks, bv, h->segs); break;
-    default: k_fill<8, VT><<<grid, 128, 0, s>>>(n, I, c, mb, sb, rowptr, colidx, v, brp, segptr, h->block_colidx, h->block_masks, bv, h->segs); break;
+    case 2: k_fill_values<2, VT><<<grid, 256, 0, s>>>(n, nnz, c, mb, rowptr, colidx, v, h->block_rowptr, h->block_colidx, h->block_masks, bvo, bv); break;
+    case 4: k_fill_values<4, VT><<<grid, 256, 0, s>>>(n, nnz, c, mb, rowptr, colidx, v, h->block_rowptr, h->block_colidx, h->block_masks, bvo, bv); break;
+    default: k_fill_values<8, VT><<<grid, 256, 0, s>>>(n, nnz, c, mb, rowptr, colidx, v, h->block_rowptr, h->block_colidx, h->block_masks, bvo, bv); break;
   }
 }
 
@@ -396,7 +707,7 @@ spc5_status build_order(spc5_matrix* h, cudaStream_t s) {
   if (h->order || h->I == 0) return SPC5_OK;
   const int64_t I = h->I;
   DeviceBuf keyd;
-  cudaError_t e = cudaMalloc(&keyd.p, sizeof(int32_t) * (size_t)I);
+  cudaError_t e = keyd.alloc(sizeof(int32_t) * (size_t)I, s);
   if (e != cudaSuccess) return cuda_fail(e, "work order: scratch");
   switch (h->r) {
     case 1: launch_order_key<1>(h->c, h, (int32_t*)keyd.p, s); break;
@@ -469,19 +780,32 @@ spc5_status convert_impl(int64_t n, int64_t m, int64_t nnz, const int64_t* rowpt
 
   // 1. validate
   DeviceBuf status, counts, nseg;
-  e = cudaMalloc(&status.p, sizeof(unsigned long long));
+  e = status.alloc(sizeof(unsigned long long), s);
   if (e != cudaSuccess) return bail(cuda_fail(e, "convert: status word"));
   e = cudaMemsetAsync(status.p, 0xff, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return bail(cuda_fail(e, "convert: status word"));
-  if (n > 0)
-    k_validate<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, m, nnz, rowptr, colidx, (unsigned long long*)status.p);
+  if (n > 0) {
+    k_validate_rows<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, nnz, rowptr, (unsigned long long*)status.p);
+    const int64_t warps = (nnz + kValChunk - 1) / kValChunk;
+    if (warps > 0)
+      k_validate_cols<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(n, m, nnz, rowptr, colidx,
+                                                                          (unsigned long long*)status.p);
+  }
   // 2. count
-  e = cudaMalloc(&counts.p, sizeof(int32_t) * (size_t)(I + 1));
-  if (e == cudaSuccess) e = cudaMalloc(&nseg.p, sizeof(int32_t) * (size_t)(I + 1));
+  e = counts.alloc(sizeof(int32_t) * (size_t)(I + 1), s);
+  if (e == cudaSuccess) e = nseg.alloc(sizeof(int32_t) * (size_t)(I + 1), s);
   if (e != cudaSuccess) return bail(cuda_fail(e, "convert: counts"));
   unsigned long long st_host = ~0ull;
   e = cudaMemcpyAsync(&st_host, status.p, sizeof(st_host), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess && st_host != ~0ull) {
+    // something is wrong: the row-by-row check names the first bad row and its code
+    e = cudaMemsetAsync(status.p, 0xff, sizeof(unsigned long long), s);
+    if (e == cudaSuccess)
+      k_validate<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, m, nnz, rowptr, colidx, (unsigned long long*)status.p);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&st_host, status.p, sizeof(st_host), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  }
   if (e != cudaSuccess) return bail(cuda_fail(e, "convert: validation"));
   if (st_host != ~0ull) {
     int code = (int)(st_host & 7ull);
@@ -490,16 +814,36 @@ spc5_status convert_impl(int64_t n, int64_t m, int64_t nnz, const int64_t* rowpt
                        : code == SPC5_ERANGE  ? "column index out of range" : "bad row pointer";
     return bail(fail((spc5_status)code, std::string("convert: CSR row ") + std::to_string(row) + ": " + what));
   }
-  count_r(r, n, I, c, rowptr, colidx, (int32_t*)counts.p, s);
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return bail(cuda_fail(e, "convert: count kernel"));
-
-  // 3. scans
   e = alloc_padded((void**)&h->block_rowptr, sizeof(int32_t) * (size_t)(I + 1), s);
   if (e != cudaSuccess) return bail(cuda_fail(e, "convert: block_rowptr"));
   int64_t nb = 0, ns = 0;
-  spc5_status st = scan_counts((const int32_t*)counts.p, I, h->block_rowptr, &nb, s);
-  if (st != SPC5_OK) return bail(st);
+  spc5_status st = SPC5_OK;
+  DeviceBuf flags, bidx;  // r = 1: block-start marks over the entries and their scan
+  const int64_t eth = (nnz + kEntriesPerThread - 1) / kEntriesPerThread;
+  if (r == 1) {
+    e = flags.alloc(sizeof(int32_t) * (size_t)(nnz + 1), s);
+    if (e == cudaSuccess) e = bidx.alloc(sizeof(int32_t) * (size_t)(nnz + 1), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(flags.p, 0, sizeof(int32_t) * (size_t)(nnz + 1), s);
+    if (e != cudaSuccess)
+      return bail(e == cudaErrorMemoryAllocation ? fail(SPC5_ENOMEM, "convert: out of device memory")
+                                                 : cuda_fail(e, "convert: block marks"));
+    if (eth > 0)
+      k_r1_flags<<<(unsigned)((eth + 255) / 256), 256, 0, s>>>(n, nnz, c, rowptr, colidx, (int32_t*)flags.p);
+    st = scan_counts((const int32_t*)flags.p, nnz, (int32_t*)bidx.p, &nb, s);
+    if (st != SPC5_OK) return bail(st);
+    if (n > 0)
+      k_r1_rowptr<<<(unsigned)((n + 1 + 255) / 256), 256, 0, s>>>(n, rowptr, (const int32_t*)bidx.p, h->block_rowptr,
+                                                                  (int32_t*)counts.p);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return bail(cuda_fail(e, "convert: block numbering"));
+  } else {
+    // 3. count, then scan
+    count_r(r, n, I, c, rowptr, colidx, (int32_t*)counts.p, s);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return bail(cuda_fail(e, "convert: count kernel"));
+    st = scan_counts((const int32_t*)counts.p, I, h->block_rowptr, &nb, s);
+    if (st != SPC5_OK) return bail(st);
+  }
   // An interval goes to the warp-segment path when it is much longer than
   // the mean (lane-per-row warps then idle behind it) or than the absolute
   // floor; the caller may fix the threshold instead.
@@ -520,7 +864,7 @@ spc5_status convert_impl(int64_t n, int64_t m, int64_t nnz, const int64_t* rowpt
     k_nseg<<<(unsigned)((I + 255) / 256), 256, 0, s>>>(n, I, r, h->long_blocks, h->long_values, h->seg_blocks,
                                                       (const int32_t*)counts.p, rowptr, (int32_t*)nseg.p);
   DeviceBuf segptr;
-  e = cudaMalloc(&segptr.p, sizeof(int32_t) * (size_t)(I + 1));
+  e = segptr.alloc(sizeof(int32_t) * (size_t)(I + 1), s);
   if (e != cudaSuccess) return bail(cuda_fail(e, "convert: segment pointers"));
   st = scan_counts((const int32_t*)nseg.p, I, (int32_t*)segptr.p, &ns, s);
   if (st != SPC5_OK) return bail(st);
@@ -537,10 +881,32 @@ spc5_status convert_impl(int64_t n, int64_t m, int64_t nnz, const int64_t* rowpt
   if (e != cudaSuccess) return bail(e == cudaErrorMemoryAllocation ? fail(SPC5_ENOMEM, "convert: out of device memory")
                                                                     : cuda_fail(e, "convert: allocation"));
   const int32_t* sp = ns > 0 ? (const int32_t*)segptr.p : nullptr;
-  switch (vt) {
-    case SPC5_F64: launch_fill_r<uint64_t>(r, n, I, c, h->mb, h->seg_blocks, rowptr, colidx, values, h->block_rowptr, sp, h, s); break;
-    case SPC5_F32: launch_fill_r<uint32_t>(r, n, I, c, h->mb, h->seg_blocks, rowptr, colidx, values, h->block_rowptr, sp, h, s); break;
-    default: launch_fill_r<uint16_t>(r, n, I, c, h->mb, h->seg_blocks, rowptr, colidx, values, h->block_rowptr, sp, h, s); break;
+  if (r == 1) {
+    if (eth > 0)
+      k_r1_fill<<<(unsigned)((eth + 255) / 256), 256, 0, s>>>(n, nnz, c, h->mb, h->seg_blocks, rowptr, colidx,
+                                                              (const int32_t*)flags.p, (const int32_t*)bidx.p,
+                                                              h->block_rowptr, sp, h->block_colidx, h->block_masks,
+                                                              h->segs);
+    if (nnz > 0) {
+      e = cudaGetLastError();
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->values, values, value_size(vt) * (size_t)nnz, cudaMemcpyDeviceToDevice, s);
+      if (e != cudaSuccess) return bail(cuda_fail(e, "convert: values"));
+    }
+  } else {
+    DeviceBuf bvo;  // value offset of each block inside its interval
+    e = bvo.alloc(sizeof(int32_t) * (size_t)(nb > 0 ? nb : 1), s);
+    if (e != cudaSuccess)
+      return bail(e == cudaErrorMemoryAllocation ? fail(SPC5_ENOMEM, "convert: out of device memory")
+                                                 : cuda_fail(e, "convert: block offsets"));
+    launch_fill_r(r, n, I, c, h->mb, h->seg_blocks, rowptr, colidx, h->block_rowptr, sp, (int32_t*)bvo.p, h, s);
+    switch (vt) {
+      case SPC5_F64: launch_fill_values<uint64_t>(r, n, nnz, c, h->mb, rowptr, colidx, values, (const int32_t*)bvo.p, h, s); break;
+      case SPC5_F32: launch_fill_values<uint32_t>(r, n, nnz, c, h->mb, rowptr, colidx, values, (const int32_t*)bvo.p, h, s); break;
+      default: launch_fill_values<uint16_t>(r, n, nnz, c, h->mb, rowptr, colidx, values, (const int32_t*)bvo.p, h, s); break;
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return bail(cuda_fail(e, "convert: fill"));
   }
   if (n > 0) k_valptr<<<(unsigned)((I + 1 + 255) / 256), 256, 0, s>>>(n, I, r, rowptr, h->valptr);
   e = cudaGetLastError();
@@ -576,17 +942,34 @@ spc5_status convert_impl(int64_t n, int64_t m, int64_t nnz, const int64_t* rowpt
 // N_blocks for the twelve shapes (r outer in {1,2,4,8}, c inner in {4,8,16}).
 spc5_status count_blocks_impl(int64_t n, int64_t nnz, const int64_t* rowptr, const int32_t* colidx,
                               int64_t* nblocks_out, cudaStream_t s) {
-  (void)nnz;
   const int rs[4] = {1, 2, 4, 8};
   const int cs[3] = {4, 8, 16};
   DeviceBuf counts;
   int64_t I1 = n;  // r = 1 has the most intervals
-  cudaError_t e = cudaMalloc(&counts.p, sizeof(int32_t) * (size_t)(I1 + 1));
+  cudaError_t e = counts.alloc(sizeof(int32_t) * (size_t)(I1 + 1), s);
   if (e != cudaSuccess) return cuda_fail(e, "count_blocks: scratch");
   DeviceBuf out;
-  e = cudaMalloc(&out.p, sizeof(int32_t) * (size_t)(I1 + 1));
+  e = out.alloc(sizeof(int32_t) * (size_t)(I1 + 1), s);
   if (e != cudaSuccess) return cuda_fail(e, "count_blocks: scratch");
-  for (int a = 0; a < 4; ++a)
+  // r = 1: block starts marked over the entries (as in the conversion), then summed
+  DeviceBuf marks, marks_scan;
+  e = marks.alloc(sizeof(int32_t) * (size_t)(nnz + 1), s);
+  if (e == cudaSuccess) e = marks_scan.alloc(sizeof(int32_t) * (size_t)(nnz + 1), s);
+  if (e != cudaSuccess) return cuda_fail(e, "count_blocks: scratch");
+  const int64_t eth = (nnz + kEntriesPerThread - 1) / kEntriesPerThread;
+  for (int b = 0; b < 3; ++b) {
+    e = cudaMemsetAsync(marks.p, 0, sizeof(int32_t) * (size_t)(nnz + 1), s);
+    if (e != cudaSuccess) return cuda_fail(e, "count_blocks: scratch");
+    if (eth > 0)
+      k_r1_flags<<<(unsigned)((eth + 255) / 256), 256, 0, s>>>(n, nnz, cs[b], rowptr, colidx, (int32_t*)marks.p);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "count_blocks: mark kernel");
+    int64_t tot = 0;
+    spc5_status st = scan_counts((const int32_t*)marks.p, nnz, (int32_t*)marks_scan.p, &tot, s);
+    if (st != SPC5_OK) return st;
+    nblocks_out[b] = tot;
+  }
+  for (int a = 1; a < 4; ++a)
     for (int b = 0; b < 3; ++b) {
       int64_t I = (n + rs[a] - 1) / rs[a];
       count_r(rs[a], n, I, cs[b], rowptr, colidx, (int32_t*)counts.p, s);

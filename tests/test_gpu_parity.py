@@ -232,16 +232,23 @@ def test_csr_kernel(cuda_device, name, group):
     assert np.all(np.abs(y - y_ref32) <= (L + 1) * u / (1 - (L + 1) * u) * absy32 + 1e-45)
 
 
-def test_invalid_csr_is_rejected_with_codes(cuda_device):
+@pytest.mark.parametrize("r", [1, 2])
+def test_invalid_csr_is_rejected_with_codes(cuda_device, r):
     def attempt(rowptr, colidx, m):
         rp = torch.tensor(rowptr, dtype=torch.int64, device="cuda")
         ci = torch.tensor(colidx, dtype=torch.int32, device="cuda")
         v = torch.ones(len(colidx), dtype=torch.float64, device="cuda")
         try:
-            spc5.convert(rp, ci, v, len(rowptr) - 1, m, 2, 4)
+            spc5.convert(rp, ci, v, len(rowptr) - 1, m, r, 4)
         except spc5.Spc5Error as e:
             return e.status
         return spc5.OK
+
+    assert attempt([0, 3, 2], [0, 1, 2], 4) == spc5.EINVAL  # row pointer going backwards
+    assert attempt([0, 2, 2], [0, 1, 2], 4) == spc5.EINVAL  # last pointer is not nnz
+    # errors past the first entries of long rows are found too
+    assert attempt([0, 40, 41], list(range(20)) + list(range(21, 41)) + [7], 64) == spc5.OK
+    assert attempt([0, 40, 41], list(range(20)) + [30] + list(range(21, 40)) + [7], 64) == spc5.EUNSORTED
 
     assert attempt([0, 2, 3], [1, 2, 0], 4) == spc5.OK
     assert attempt([0, 2, 3], [2, 1, 0], 4) == spc5.EUNSORTED
