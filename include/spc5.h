@@ -125,6 +125,27 @@ spc5_status spc5_convert(int64_t n, int64_t m, int64_t nnz, const int64_t* rowpt
                          spc5_stream_t stream, spc5_handle* out);
 
 /*
+ * spc5_assemble - a handle from beta(r,c) arrays the caller built directly,
+ * without a CSR (section "Block-based storage without zero padding": the
+ * format is four arrays, Eq. 1, and the conclusion asks for producing it
+ * natively). Device arrays, copied into the handle (the caller keeps its own):
+ *   block_rowptr_d  int32[ceil(n/r)+1], rising from 0 to nblocks;
+ *   block_colidx_d  int32[nblocks], first column of each block;
+ *   block_masks_d   uint8[nblocks * ceil(r*c/8)], bit i*c+k = (row i, column
+ *                   colidx+k), least significant bit first;
+ *   values_d        nnz values of type vt in block order, row-major in a block.
+ * Checked on the device: block_rowptr (SPC5_EINVAL); every block's column in
+ * [0, m) and no set bit past column m-1 or row n-1 (SPC5_ERANGE); inside an
+ * interval each block starts at or after the previous block's column + c
+ * (SPC5_EUNSORTED); the masks hold exactly nnz bits (SPC5_EINVAL). The
+ * message names the first bad block or interval. Sizes must fit int32
+ * (SPC5_ERANGE). Options and variants as spc5_convert. Synchronises `stream`.
+ */
+spc5_status spc5_assemble(int64_t n, int64_t m, int64_t nnz, int64_t nblocks, const int32_t* block_rowptr_d,
+                          const int32_t* block_colidx_d, const uint8_t* block_masks_d, const void* values_d,
+                          spc5_dtype vt, int r, int c, const spc5_opts* opt, spc5_stream_t stream, spc5_handle* out);
+
+/*
  * spc5_spmv - y = A x over the beta(r,c) storage (Algorithm 1; Code 1 shows
  * the paper's beta(1,8) kernel). x_d has m entries, y_d has n entries, both of
  * the handle's vector type; y is overwritten. x and y must not overlap.

@@ -85,6 +85,29 @@ spc5_status spc5_convert(int64_t n, int64_t m, int64_t nnz, const int64_t* rowpt
   return SPC5_OK;
 }
 
+spc5_status spc5_assemble(int64_t n, int64_t m, int64_t nnz, int64_t nblocks, const int32_t* block_rowptr_d,
+                          const int32_t* block_colidx_d, const uint8_t* block_masks_d, const void* values_d,
+                          spc5_dtype vt, int r, int c, const spc5_opts* opt, spc5_stream_t stream, spc5_handle* out) {
+  if (!out) return fail(SPC5_EINVAL, "assemble: out is NULL");
+  *out = nullptr;
+  if (n < 0 || m < 0 || nnz < 0 || nblocks < 0) return fail(SPC5_EINVAL, "assemble: negative size");
+  if (n > INT32_MAX || m > INT32_MAX || nnz > INT32_MAX || nblocks > INT32_MAX)
+    return fail(SPC5_ERANGE, "assemble: sizes must fit int32 (int32 column indices and block pointers)");
+  if (!shape_supported(r, c)) return fail(SPC5_EUNSUPPORTED, "assemble: block shape must be r in {1,2,4,8}, c in {4,8,16}");
+  if (vt != SPC5_F64 && vt != SPC5_F32 && vt != SPC5_BF16) return fail(SPC5_EUNSUPPORTED, "assemble: value type");
+  if (!block_rowptr_d || (nblocks > 0 && (!block_colidx_d || !block_masks_d)) || (nnz > 0 && !values_d))
+    return fail(SPC5_EINVAL, "assemble: NULL array");
+  if (opt && (opt->long_blocks < 0 || opt->seg_blocks < 0)) return fail(SPC5_EINVAL, "assemble: negative option");
+  if (opt && !valid_variant(opt->variant))
+    return fail(SPC5_EINVAL, "assemble: variant must be 0, 1, 3, 5, 9, 10 or 12..19");
+  spc5_matrix* h = nullptr;
+  spc5_status st = assemble_impl(n, m, nnz, nblocks, r, c, vt, block_rowptr_d, block_colidx_d, block_masks_d, values_d,
+                                 opt, (cudaStream_t)stream, &h);
+  if (st != SPC5_OK) return st;
+  *out = h;
+  return SPC5_OK;
+}
+
 spc5_status spc5_spmv(spc5_handle h, const void* x_d, void* y_d, spc5_stream_t stream) {
   return spmv_common(h, x_d, y_d, false, (cudaStream_t)stream);
 }

@@ -749,7 +749,232 @@ spc5_status build_order(spc5_matrix* h, cudaStream_t s) {
   return SPC5_OK;
 }
 
+// ------------------------------------------------------------ assembly
+// Checks of caller-built beta(r,c) arrays. status = min over bad items of
+// (item * 8 + code); item = interval for the row pointer, block otherwise.
+__global__ void k_asm_intervals(int64_t I, int64_t nb, const int32_t* __restrict__ brp,
+                                unsigned long long* __restrict__ status) {
+  const int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (it >= I) return;
+  const int64_t a = brp[it], b = brp[it + 1];
+  if (a < 0 || b < a || b > nb || (it == 0 && a != 0) || (it == I - 1 && b != nb))
+    atomicMin(status, (unsigned long long)it * 8ull + (unsigned long long)SPC5_EINVAL);
+}
+
+// per block: column in range, no bit past column m - 1 or row n - 1, the next
+// block of the interval starting at or after this one's window; cnt[b] = the
+// block's stored values
+template <int R>
+__global__ void k_asm_blocks(int64_t n, int64_t m, int64_t I, int64_t nb, int c, int mb,
+                             const int32_t* __restrict__ brp, const int32_t* __restrict__ bcol,
+                             const uint8_t* __restrict__ bmask, int32_t* __restrict__ cnt,
+                             unsigned long long* __restrict__ status) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nb) return;
+  // interval of block b: the last interval whose first block is <= b
+  int64_t lo = 0, hi = I;
+  while (hi - lo > 1) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (brp[mid] <= b) lo = mid; else hi = mid;
+  }
+  const int64_t it = lo;
+  const int32_t col = bcol[b];
+  uint32_t w[4] = {0u, 0u, 0u, 0u};
+  for (int q = 0; q < mb; ++q) w[q >> 2] |= (uint32_t)bmask[b * mb + q] << (8 * (q & 3));
+  int code = 0, pc = 0;
+  for (int i = 0; i < R; ++i) {
+    const int p = i * c;
+    const uint32_t bits = (w[p >> 5] >> (p & 31)) & (c == 32 ? 0xffffffffu : ((1u << c) - 1u));
+    pc += __popc(bits);
+    if (bits && it * R + i >= n) code = SPC5_ERANGE;                         // a row past n - 1
+    if (bits && (int64_t)col + (31 - __clz(bits)) >= m) code = SPC5_ERANGE;  // a column past m - 1
+  }
+  if (col < 0 || col >= m) code = SPC5_ERANGE;
+  if (b + 1 < brp[it + 1] && (int64_t)bcol[b + 1] < (int64_t)col + c) code = SPC5_EUNSORTED;  // windows overlap or go back
+  cnt[b] = pc;
+  if (code) atomicMin(status, (unsigned long long)b * 8ull + (unsigned long long)code);
+}
+
+// valptr[it] = values before interval it (from the block value prefix)
+__global__ void k_asm_valptr(int64_t I, const int32_t* __restrict__ brp, const int32_t* __restrict__ bval,
+                             int64_t* __restrict__ valptr, int32_t* __restrict__ counts) {
+  const int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (it > I) return;
+  valptr[it] = bval[brp[it]];
+  if (it < I) counts[it] = brp[it + 1] - brp[it];
+}
+
+// segments of long intervals (blocks or values above the thresholds)
+__global__ void k_asm_segments(int64_t I, int32_t long_blocks, int64_t long_values, int seg_blocks,
+                               const int32_t* __restrict__ brp, const int32_t* __restrict__ bval,
+                               const int64_t* __restrict__ valptr, int32_t* __restrict__ nseg) {
+  const int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (it >= I) return;
+  const int32_t nbk = brp[it + 1] - brp[it];
+  const bool lng = nbk > long_blocks || valptr[it + 1] - valptr[it] > long_values;
+  nseg[it] = lng ? (nbk + seg_blocks - 1) / seg_blocks : 0;
+}
+
+__global__ void k_asm_seg_fill(int64_t I, int seg_blocks, const int32_t* __restrict__ brp,
+                               const int32_t* __restrict__ bval, const int32_t* __restrict__ segptr,
+                               Segment* __restrict__ segs) {
+  const int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (it >= I) return;
+  const int32_t s0 = segptr[it], ns = segptr[it + 1] - s0;
+  for (int32_t q = 0; q < ns; ++q) {
+    Segment sg;
+    sg.interval = (int32_t)it;
+    sg.b_begin = brp[it] + q * seg_blocks;
+    sg.b_end = min(sg.b_begin + seg_blocks, brp[it + 1]);
+    sg.count = q == 0 ? ns : 0;
+    sg.v_begin = bval[sg.b_begin];
+    segs[s0 + q] = sg;
+  }
+}
+
 void destroy_matrix(spc5_matrix* h) { free_matrix(h); }
+
+spc5_status assemble_impl(int64_t n, int64_t m, int64_t nnz, int64_t nb, int r, int c, spc5_dtype vt,
+                          const int32_t* brp_in, const int32_t* bcol_in, const uint8_t* bmask_in, const void* vals_in,
+                          const spc5_opts* opt, cudaStream_t s, spc5_matrix** out) {
+  *out = nullptr;
+  spc5_matrix* h = new spc5_matrix();
+  h->n = n;
+  h->m = m;
+  h->nnz = nnz;
+  h->r = r;
+  h->c = c;
+  h->mb = mask_bytes(r, c);
+  h->vt = vt;
+  h->I = (n + r - 1) / r;
+  h->nb = nb;
+  int32_t user_long = 0;
+  if (opt) {
+    user_long = opt->long_blocks;
+    if (opt->seg_blocks > 0) h->seg_blocks = opt->seg_blocks;
+    h->variant = opt->variant;
+    if (opt->order_window != 0) h->order_window = opt->order_window;
+  }
+  const int64_t I = h->I;
+  auto bail = [&](spc5_status st) {
+    free_matrix(h);
+    return st;
+  };
+  cudaError_t e = alloc_padded((void**)&h->block_rowptr, sizeof(int32_t) * (size_t)(I + 1), s);
+  if (e == cudaSuccess) e = alloc_padded((void**)&h->block_colidx, sizeof(int32_t) * (size_t)nb, s);
+  if (e == cudaSuccess) e = alloc_padded((void**)&h->block_masks, (size_t)nb * (size_t)h->mb, s);
+  if (e == cudaSuccess) e = alloc_padded(&h->values, value_size(vt) * (size_t)nnz, s);
+  if (e == cudaSuccess) e = alloc_padded((void**)&h->valptr, sizeof(int64_t) * (size_t)(I + 1), s);
+  if (e != cudaSuccess)
+    return bail(e == cudaErrorMemoryAllocation ? fail(SPC5_ENOMEM, "assemble: out of device memory")
+                                               : cuda_fail(e, "assemble: allocation"));
+  e = cudaMemcpyAsync(h->block_rowptr, brp_in, sizeof(int32_t) * (size_t)(I + 1), cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess && nb > 0)
+    e = cudaMemcpyAsync(h->block_colidx, bcol_in, sizeof(int32_t) * (size_t)nb, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess && nb > 0)
+    e = cudaMemcpyAsync(h->block_masks, bmask_in, (size_t)nb * (size_t)h->mb, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess && nnz > 0)
+    e = cudaMemcpyAsync(h->values, vals_in, value_size(vt) * (size_t)nnz, cudaMemcpyDeviceToDevice, s);
+  if (e != cudaSuccess) return bail(cuda_fail(e, "assemble: copy"));
+  // 1. checks
+  DeviceBuf status, cnt, bval, counts, nseg, segptr;
+  e = status.alloc(sizeof(unsigned long long), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(status.p, 0xff, sizeof(unsigned long long), s);
+  if (e == cudaSuccess) e = cnt.alloc(sizeof(int32_t) * (size_t)(nb + 1), s);
+  if (e == cudaSuccess) e = bval.alloc(sizeof(int32_t) * (size_t)(nb + 1), s);
+  if (e != cudaSuccess) return bail(cuda_fail(e, "assemble: scratch"));
+  unsigned long long* sw = (unsigned long long*)status.p;
+  if (I > 0) k_asm_intervals<<<(unsigned)((I + 255) / 256), 256, 0, s>>>(I, nb, h->block_rowptr, sw);
+  unsigned long long st_host = ~0ull;
+  e = cudaMemcpyAsync(&st_host, sw, sizeof(st_host), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return bail(cuda_fail(e, "assemble: checks"));
+  if (st_host != ~0ull)
+    return bail(fail(SPC5_EINVAL, "assemble: block_rowptr entry " + std::to_string(st_host >> 3) +
+                                      " (must rise from 0 to n_blocks)"));
+  if (nb > 0) {
+    const unsigned g = (unsigned)((nb + 255) / 256);
+    switch (r) {
+      case 1: k_asm_blocks<1><<<g, 256, 0, s>>>(n, m, I, nb, c, h->mb, h->block_rowptr, h->block_colidx, h->block_masks, (int32_t*)cnt.p, sw); break;
+      case 2: k_asm_blocks<2><<<g, 256, 0, s>>>(n, m, I, nb, c, h->mb, h->block_rowptr, h->block_colidx, h->block_masks, (int32_t*)cnt.p, sw); break;
+      case 4: k_asm_blocks<4><<<g, 256, 0, s>>>(n, m, I, nb, c, h->mb, h->block_rowptr, h->block_colidx, h->block_masks, (int32_t*)cnt.p, sw); break;
+      default: k_asm_blocks<8><<<g, 256, 0, s>>>(n, m, I, nb, c, h->mb, h->block_rowptr, h->block_colidx, h->block_masks, (int32_t*)cnt.p, sw); break;
+    }
+  }
+  e = cudaMemcpyAsync(&st_host, sw, sizeof(st_host), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return bail(cuda_fail(e, "assemble: checks"));
+  if (st_host != ~0ull) {
+    const int code = (int)(st_host & 7ull);
+    const std::string what = code == SPC5_ERANGE ? "a column or row outside the matrix"
+                                                 : "overlaps or precedes the previous block of its interval";
+    return bail(fail((spc5_status)code, "assemble: block " + std::to_string(st_host >> 3) + ": " + what));
+  }
+  // 2. value offsets
+  int64_t total = 0;
+  spc5_status st = scan_counts((const int32_t*)cnt.p, nb, (int32_t*)bval.p, &total, s);
+  if (st != SPC5_OK) return bail(st);
+  if (total != nnz)
+    return bail(fail(SPC5_EINVAL, "assemble: the masks hold " + std::to_string(total) + " entries, nnz is " +
+                                      std::to_string(nnz)));
+  e = counts.alloc(sizeof(int32_t) * (size_t)(I + 1), s);
+  if (e == cudaSuccess) e = nseg.alloc(sizeof(int32_t) * (size_t)(I + 1), s);
+  if (e == cudaSuccess) e = segptr.alloc(sizeof(int32_t) * (size_t)(I + 1), s);
+  if (e != cudaSuccess) return bail(cuda_fail(e, "assemble: scratch"));
+  k_asm_valptr<<<(unsigned)((I + 1 + 255) / 256), 256, 0, s>>>(I, h->block_rowptr, (const int32_t*)bval.p, h->valptr,
+                                                               (int32_t*)counts.p);
+  // 3. long intervals (same thresholds as the conversion)
+  if (user_long > 0) {
+    h->long_blocks = user_long;
+  } else {
+    const double mean = I > 0 ? (double)nb / (double)I : 0.0;
+    const double lim = 4.0 * mean;
+    h->long_blocks = lim > kLongBlocks ? (lim < (double)INT_MAX ? (int32_t)lim : INT_MAX) : kLongBlocks;
+  }
+  {
+    const double mean_v = I > 0 ? (double)nnz / (double)I : 0.0;
+    const double lv = 8.0 * mean_v;
+    h->long_values = lv > 2048.0 * r ? (int64_t)lv : (int64_t)2048 * r;
+  }
+  int64_t ns = 0;
+  if (I > 0)
+    k_asm_segments<<<(unsigned)((I + 255) / 256), 256, 0, s>>>(I, h->long_blocks, h->long_values, h->seg_blocks,
+                                                               h->block_rowptr, (const int32_t*)bval.p, h->valptr,
+                                                               (int32_t*)nseg.p);
+  st = scan_counts((const int32_t*)nseg.p, I, (int32_t*)segptr.p, &ns, s);
+  if (st != SPC5_OK) return bail(st);
+  h->nseg = ns;
+  e = alloc_padded((void**)&h->segs, sizeof(Segment) * (size_t)ns, s);
+  if (e == cudaSuccess) e = alloc_padded(&h->partials, (vt == SPC5_F64 ? 8 : 4) * (size_t)ns * (size_t)r, s);
+  if (e != cudaSuccess) return bail(cuda_fail(e, "assemble: segments"));
+  if (ns > 0) {
+    k_asm_seg_fill<<<(unsigned)((I + 255) / 256), 256, 0, s>>>(I, h->seg_blocks, h->block_rowptr,
+                                                               (const int32_t*)bval.p, (const int32_t*)segptr.p,
+                                                               h->segs);
+    int32_t* flag = (int32_t*)counts.p;
+    int32_t* pos = (int32_t*)nseg.p;
+    k_long_flags<<<(unsigned)((I + 255) / 256), 256, 0, s>>>(I, (const int32_t*)segptr.p, flag);
+    int64_t nlong = 0;
+    st = scan_counts(flag, I, pos, &nlong, s);
+    if (st != SPC5_OK) return bail(st);
+    e = alloc_padded((void**)&h->seg_first, sizeof(int32_t) * (size_t)nlong, s);
+    if (e == cudaSuccess) {
+      k_seg_first<<<(unsigned)((I + 255) / 256), 256, 0, s>>>(I, (const int32_t*)segptr.p, flag, pos, h->seg_first);
+      e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return bail(cuda_fail(e, "assemble: long-interval list"));
+    h->nlong = nlong;
+  }
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return bail(cuda_fail(e, "assemble"));
+  if (ordered_variant(h->variant)) {
+    spc5_status st2 = build_order(h, s);
+    if (st2 != SPC5_OK) return bail(st2);
+  }
+  *out = h;
+  return SPC5_OK;
+}
 
 spc5_status convert_impl(int64_t n, int64_t m, int64_t nnz, const int64_t* rowptr, const int32_t* colidx,
                          const void* values, spc5_dtype vt, int r, int c, const spc5_opts* opt, cudaStream_t s,

@@ -95,6 +95,8 @@ def load(build_if_missing: bool = False):
     lib.spc5_count_blocks.argtypes = [i64, i64, i64, vp, vp, vp, vp]
     lib.spc5_csr_spmv.argtypes = [i64, i64, i64, vp, vp, vp, i32, vp, vp, i32, vp]
     lib.spc5_copy.argtypes = [vp, vp, i64, vp]
+    lib.spc5_assemble.argtypes = [i64, i64, i64, i64, vp, vp, vp, vp, i32, i32, i32, ctypes.POINTER(Opts), vp,
+                                  ctypes.POINTER(vp)]
     lib.spc5_fma_rate.argtypes = [i32, i64, vp, vp, vp]
     lib.spc5_fma_rate_lanes.argtypes = [i32, i64, i32, vp, vp, vp]
     lib.spc5_spmv_noalloc.argtypes = [vp, vp, vp, vp]
@@ -113,7 +115,7 @@ def load(build_if_missing: bool = False):
     lib.spc5_mlp_infer.argtypes = [vp, vp, i32, vp, vp]
     lib.spc5_poly_fit.argtypes = [vp, vp, i32, i32, vp]
     lib.spc5_select.argtypes = [i64, i64, i64, vp, vp, vp, i32, i32, ctypes.POINTER(Selector), vp, vp, vp, vp]
-    for f in (lib.spc5_convert, lib.spc5_spmv, lib.spc5_spmv_acc, lib.spc5_export, lib.spc5_destroy, lib.spc5_set_variant,
+    for f in (lib.spc5_convert, lib.spc5_assemble, lib.spc5_spmv, lib.spc5_spmv_acc, lib.spc5_export, lib.spc5_destroy, lib.spc5_set_variant,
               lib.spc5_count_blocks, lib.spc5_csr_spmv, lib.spc5_copy, lib.spc5_fma_rate, lib.spc5_fma_rate_lanes,
               lib.spc5_spmv_noalloc, lib.spc5_cg, lib.spc5_spmm, lib.spc5_features,
               lib.spc5_time_formats, lib.spc5_mlp_train, lib.spc5_mlp_grad, lib.spc5_mlp_infer, lib.spc5_poly_fit,
@@ -267,6 +269,24 @@ def convert(rowptr: torch.Tensor, colidx: torch.Tensor, values: torch.Tensor, n:
     _check(load().spc5_convert(n, m, nnz, _ptr(rowptr), _ptr(colidx), _ptr(values), vt, r, c, ctypes.byref(opts),
                                _stream_ptr(stream), ctypes.byref(h)), "spc5_convert")
     return Matrix(h.value, n, m, nnz, r, c, vt)
+
+
+def assemble(n: int, m: int, r: int, c: int, block_rowptr: torch.Tensor, block_colidx: torch.Tensor,
+             block_masks: torch.Tensor, values: torch.Tensor, long_blocks: int = 0, seg_blocks: int = 0,
+             variant: int = 0, order_window: int = 0, stream=None) -> Matrix:
+    """beta(r,c) arrays built by the caller (device tensors: int32 block_rowptr and block_colidx,
+    uint8 block_masks, values float64 / float32 / bfloat16) -> handle (arrays copied)."""
+    if block_rowptr.dtype != torch.int32 or block_colidx.dtype != torch.int32 or block_masks.dtype != torch.uint8:
+        raise TypeError("block_rowptr / block_colidx must be int32 and block_masks uint8")
+    if values.dtype not in _VALUE_DTYPE:
+        raise TypeError("values must be float64, float32 or bfloat16")
+    vt = _VALUE_DTYPE[values.dtype]
+    opts = Opts(long_blocks, seg_blocks, variant, order_window)
+    h = ctypes.c_void_p()
+    _check(load().spc5_assemble(n, m, values.numel(), block_colidx.numel(), _ptr(block_rowptr), _ptr(block_colidx),
+                                _ptr(block_masks), _ptr(values), vt, r, c, ctypes.byref(opts), _stream_ptr(stream),
+                                ctypes.byref(h)), "spc5_assemble")
+    return Matrix(h.value, n, m, values.numel(), r, c, vt)
 
 
 def csr_spmv(rowptr: torch.Tensor, colidx: torch.Tensor, values: torch.Tensor, n: int, m: int, x: torch.Tensor,
