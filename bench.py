@@ -100,12 +100,15 @@ def profile_matrices():
             ("poisson7_96^3", lambda: inputs.stencil3d(96, 96, 96, points=7, normal_values=False))]
 
 
+# sources that decide the SpMV kernels and the layout they read
+SPMV_SOURCES = ("internal.cuh", "spmv_beta.cuh", "spmv_f64.cu", "spmv_f32.cu", "spmv_bf16.cu", "convert.cu")
+
+
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1801_01134_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    for f in SPMV_SOURCES:
+        h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 

@@ -1164,48 +1164,4 @@ spc5_status convert_impl(int64_t n, int64_t m, int64_t nnz, const int64_t* rowpt
   return SPC5_OK;
 }
 
-// N_blocks for the twelve shapes (r outer in {1,2,4,8}, c inner in {4,8,16}).
-spc5_status count_blocks_impl(int64_t n, int64_t nnz, const int64_t* rowptr, const int32_t* colidx,
-                              int64_t* nblocks_out, cudaStream_t s) {
-  const int rs[4] = {1, 2, 4, 8};
-  const int cs[3] = {4, 8, 16};
-  DeviceBuf counts;
-  int64_t I1 = n;  // r = 1 has the most intervals
-  cudaError_t e = counts.alloc(sizeof(int32_t) * (size_t)(I1 + 1), s);
-  if (e != cudaSuccess) return cuda_fail(e, "count_blocks: scratch");
-  DeviceBuf out;
-  e = out.alloc(sizeof(int32_t) * (size_t)(I1 + 1), s);
-  if (e != cudaSuccess) return cuda_fail(e, "count_blocks: scratch");
-  // r = 1: block starts marked over the entries (as in the conversion), then summed
-  DeviceBuf marks, marks_scan;
-  e = marks.alloc(sizeof(int32_t) * (size_t)(nnz + 1), s);
-  if (e == cudaSuccess) e = marks_scan.alloc(sizeof(int32_t) * (size_t)(nnz + 1), s);
-  if (e != cudaSuccess) return cuda_fail(e, "count_blocks: scratch");
-  const int64_t eth = (nnz + kEntriesPerThread - 1) / kEntriesPerThread;
-  for (int b = 0; b < 3; ++b) {
-    e = cudaMemsetAsync(marks.p, 0, sizeof(int32_t) * (size_t)(nnz + 1), s);
-    if (e != cudaSuccess) return cuda_fail(e, "count_blocks: scratch");
-    if (eth > 0)
-      k_r1_flags<<<(unsigned)((eth + 255) / 256), 256, 0, s>>>(n, nnz, cs[b], rowptr, colidx, (int32_t*)marks.p);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(e, "count_blocks: mark kernel");
-    int64_t tot = 0;
-    spc5_status st = scan_counts((const int32_t*)marks.p, nnz, (int32_t*)marks_scan.p, &tot, s);
-    if (st != SPC5_OK) return st;
-    nblocks_out[b] = tot;
-  }
-  for (int a = 1; a < 4; ++a)
-    for (int b = 0; b < 3; ++b) {
-      int64_t I = (n + rs[a] - 1) / rs[a];
-      count_r(rs[a], n, I, cs[b], rowptr, colidx, (int32_t*)counts.p, s);
-      e = cudaGetLastError();
-      if (e != cudaSuccess) return cuda_fail(e, "count_blocks: count kernel");
-      int64_t tot = 0;
-      spc5_status st = scan_counts((const int32_t*)counts.p, I, (int32_t*)out.p, &tot, s);
-      if (st != SPC5_OK) return st;
-      nblocks_out[a * 3 + b] = tot;
-    }
-  return SPC5_OK;
-}
-
 }  // namespace spc5

@@ -6,10 +6,10 @@
 // cheap to count (section "Performance prediction and optimal kernel
 // selection"), through one fitted polynomial per kernel (section "Performance
 // polynomial interpolation"); its conclusion asks for richer inputs. Here:
-//   * k_features: one pass over the CSR structure counts N_blocks for all
-//     twelve shapes (one merge of each interval's rows per r, three greedy
-//     covers c = 4, 8, 16 along the same merge) and the row-length sum, sum
-//     of squares and maximum;
+//   * features: N_blocks for all twelve shapes and the row-length sum, sum
+//     of squares and maximum, counted from the CSR structure by the kernels
+//     of counts.cu (runs between wide gaps for r = 1, one merge per interval
+//     and r otherwise);
 //   * spc5_time_formats: converts to each shape and times the SpMV (the
 //     exhaustive choice, and the training targets);
 //   * a least-squares polynomial per format (Householder QR on the
@@ -34,93 +34,6 @@ constexpr int kNF = SPC5_NFEATURES;  // 16
 constexpr int kNO = SPC5_NFORMATS;   // 12
 constexpr int kH = 64;
 constexpr int kNP = kH * kNF + kH + kH * kH + kH + kNO * kH + kNO;  // 6028 parameters
-
-// ------------------------------------------------------------ features
-// acc[0..11] = N_blocks per shape, acc[12] = sum of row lengths, acc[13] =
-// sum of squared row lengths, acc[14] = max row length
-__global__ void __launch_bounds__(128) k_features(int64_t n, const int64_t* __restrict__ rowptr,
-                                                  const int32_t* __restrict__ colidx,
-                                                  unsigned long long* __restrict__ acc) {
-  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // group of 8 rows
-  unsigned long long cnt[12];
-#pragma unroll
-  for (int q = 0; q < 12; ++q) cnt[q] = 0;
-  unsigned long long s1 = 0, s2 = 0, mx = 0;
-  const int64_t row0 = g * 8;
-  if (row0 < n) {
-    const int rows = (int)(n - row0 < 8 ? n - row0 : 8);
-    int64_t beg[8], end[8];
-    for (int i = 0; i < 8; ++i) {
-      if (i < rows) {
-        beg[i] = rowptr[row0 + i];
-        end[i] = rowptr[row0 + i + 1];
-        const unsigned long long len = (unsigned long long)(end[i] - beg[i]);
-        s1 += len;
-        s2 += len * len;
-        mx = len > mx ? len : mx;
-      } else {
-        beg[i] = end[i] = 0;
-      }
-    }
-    // r = 1, 2, 4, 8: merge the rows of each interval in column order; a
-    // column at or beyond the current block's end starts a new block
-    const int rs[4] = {1, 2, 4, 8};
-    for (int a = 0; a < 4; ++a) {
-      const int r = rs[a];
-      for (int i0 = 0; i0 < rows; i0 += r) {
-        int64_t h[8];
-        const int ri = rows - i0 < r ? rows - i0 : r;
-        for (int i = 0; i < ri; ++i) h[i] = beg[i0 + i];
-        int64_t e4 = LLONG_MIN, e8 = LLONG_MIN, e16 = LLONG_MIN;
-        for (;;) {
-          int best = -1;
-          int64_t bc = LLONG_MAX;
-          for (int i = 0; i < ri; ++i)
-            if (h[i] < end[i0 + i]) {
-              const int64_t cc = colidx[h[i]];
-              if (cc < bc) {
-                bc = cc;
-                best = i;
-              }
-            }
-          if (best < 0) break;
-          ++h[best];
-          if (bc >= e4) { ++cnt[a * 3 + 0]; e4 = bc + 4; }
-          if (bc >= e8) { ++cnt[a * 3 + 1]; e8 = bc + 8; }
-          if (bc >= e16) { ++cnt[a * 3 + 2]; e16 = bc + 16; }
-        }
-      }
-    }
-  }
-  // block sums (integers: the order does not matter) then one atomic each
-  __shared__ unsigned long long red[15][4];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  unsigned long long v[15];
-#pragma unroll
-  for (int q = 0; q < 12; ++q) v[q] = cnt[q];
-  v[12] = s1;
-  v[13] = s2;
-  v[14] = mx;
-#pragma unroll
-  for (int q = 0; q < 15; ++q) {
-    unsigned long long x = v[q];
-    for (int d = 16; d >= 1; d >>= 1) {
-      const unsigned long long o = __shfl_xor_sync(0xffffffffu, x, d);
-      x = q == 14 ? (o > x ? o : x) : x + o;
-    }
-    if (lane == 0) red[q][w] = x;
-  }
-  __syncthreads();
-  if (threadIdx.x < 15) {
-    const int q = threadIdx.x;
-    unsigned long long x = red[q][0];
-    for (int k = 1; k < 4; ++k) x = q == 14 ? (red[q][k] > x ? red[q][k] : x) : x + red[q][k];
-    if (q == 14)
-      atomicMax(&acc[q], x);
-    else
-      atomicAdd(&acc[q], x);
-  }
-}
 
 // ----------------------------------------------------------------- MLP
 // Parameter layout (float32, flat): W1[64][16], b1[64], W2[64][64], b2[64],
@@ -309,13 +222,8 @@ spc5_status features_impl(int64_t n, int64_t nnz, const int64_t* rowptr, const i
                           cudaStream_t s) {
   DBuf acc;
   cudaError_t e = cudaMalloc(&acc.p, sizeof(unsigned long long) * 16);
-  if (e == cudaSuccess) e = cudaMemsetAsync(acc.p, 0, sizeof(unsigned long long) * 16, s);
-  if (e != cudaSuccess) return cuda_fail(e, "features: scratch");
-  const int64_t groups = (n + 7) / 8;
-  if (groups > 0)
-    k_features<<<(unsigned)((groups + 127) / 128), 128, 0, s>>>(n, rowptr, colidx, (unsigned long long*)acc.p);
-  unsigned long long h[16];
-  e = cudaGetLastError();
+  if (e == cudaSuccess) e = launch_block_counts(n, nnz, rowptr, colidx, (unsigned long long*)acc.p, s);
+  unsigned long long h[15];
   if (e == cudaSuccess) e = cudaMemcpyAsync(h, acc.p, sizeof(h), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(e, "features");
