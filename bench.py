@@ -69,6 +69,7 @@ def parse():
     p.add_argument("--cg-graph", type=int, default=1)
     p.add_argument("--cg-variant", type=int, default=18, help="kernel variant of the inner (float32) CG handle")
     p.add_argument("--cg-shape", default="2x4", help="block shape of the CG profiling handles")
+    p.add_argument("--cg-inner-tol", type=float, default=0.0, help="inner tolerance of the mixed CG (0 = default)")
     return p.parse_args()
 
 
@@ -416,19 +417,21 @@ def run_cg_section(dev, reps: int = 3):
                                 variant=0 if name == "f64" else CG_INNER_VARIANT)
     out = {"workload": "7-point Poisson 96^3 (n=884,736, nnz=6,137,856), b uniform[-1,1] seed 0, tol 1e-10",
            "format": f"beta(2,4); float64 handle variant 5, inner handles variant {CG_INNER_VARIANT}"}
-    for label, inner in (("fp64_cg", None), ("mixed_f32", hs["f32"]), ("mixed_bf16", hs["bf16"])):
+    for label, inner, rel in (("fp64_cg", None, False), ("mixed_f32", hs["f32"], False),
+                              ("mixed_bf16", hs["bf16"], False), ("reliable_f32", hs["f32"], True),
+                              ("reliable_bf16", hs["bf16"], True)):
         ts, info = [], None
         for _ in range(reps):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
-            x, info = spc5.cg(hs["f64"], b, A_inner=inner, tol=1e-10, use_graph=True)
+            x, info = spc5.cg(hs["f64"], b, A_inner=inner, tol=1e-10, use_graph=True, reliable=rel)
             e1.record()
             e1.synchronize()
             ts.append(e0.elapsed_time(e1))
         out[label] = {"ms": round(min(ts), 3), "iterations": info["iterations"], "outer": info["outer"],
                       "rel_residual": info["rel_residual"], "converged": info["converged"]}
-    out["speedup_mixed_f32"] = round(out["fp64_cg"]["ms"] / out["mixed_f32"]["ms"], 3)
-    out["speedup_mixed_bf16"] = round(out["fp64_cg"]["ms"] / out["mixed_bf16"]["ms"], 3)
+    for k in ("mixed_f32", "mixed_bf16", "reliable_f32", "reliable_bf16"):
+        out[f"speedup_{k}"] = round(out["fp64_cg"]["ms"] / out[k]["ms"], 3)
     for h in hs.values():
         h.destroy()
     return out
@@ -542,11 +545,12 @@ def main():
             # --cg-variant sets the inner (float32) handle; the float64 handle keeps the default
             hs[name] = spc5.convert(d.rowptr, d.colidx, d.values, A.n, A.m, r, c,
                                     variant=0 if name == "f64" else args.cg_variant)
-        for label, inner in (("fp64_cg", None), ("mixed_f32", hs["f32"])):
+        for label, inner, rel in (("fp64_cg", None, False), ("mixed_f32", hs["f32"], False),
+                                  ("reliable_f32", hs["f32"], True)):
             for rep in range(2):
                 t0 = time.perf_counter()
                 x, info = spc5.cg(hs["f64"], b, A_inner=inner, tol=1e-10, check_every=args.cg_every,
-                                  use_graph=bool(args.cg_graph))
+                                  use_graph=bool(args.cg_graph), inner_tol=args.cg_inner_tol, reliable=rel)
                 dt = time.perf_counter() - t0
                 print(json.dumps({"solver": label, "rep": rep, "ms": round(dt * 1e3, 3), **info}), flush=True)
         return 0

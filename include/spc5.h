@@ -285,7 +285,11 @@ typedef struct {
                               check_every/4 and 8 x check_every apart); 1 reads
                               after every iteration (exact stopping point)       [8] */
   int32_t use_graph;       /* replay the iteration from a captured CUDA graph     [0: off] */
-  int32_t reserved[5];
+  int32_t reliable;        /* with A_inner: 1 = one float32 CG recurrence with
+                              reliable updates (the float64 residual replaces
+                              the recurred one whenever its norm fell 10x; no
+                              restarts) instead of refinement   [0: refinement] */
+  int32_t reserved[4];
 } spc5_cg_opts;
 
 typedef struct {
@@ -305,7 +309,11 @@ typedef struct {
  *            handle of the same matrix: mixed-precision iterative refinement
  *            - the residual r = b - A x, the update x += d and all norms in
  *            float64 with A; each correction d solved by CG in float32 with
- *            A_inner on r / ||r|| to a relative reduction inner_tol.
+ *            A_inner on r / ||r|| to a relative reduction inner_tol. With
+ *            opt->reliable, one float32 CG recurrence on A_inner instead,
+ *            its residual replaced by the float64 b - A x (and its iterate
+ *            folded into x) whenever the recurred norm fell by 10x
+ *            (info->outer counts these updates).
  *   b_d, x_d float64 device vectors of n entries; x is overwritten (the
  *            iteration starts from x = 0).
  *   info     receives iteration counts and the true relative residual.

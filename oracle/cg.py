@@ -7,7 +7,10 @@ here is textbook:
   * CG of Hestenes & Stiefel (1952) in float64, starting from x = 0;
   * iterative refinement (Wilkinson; Moler 1967): the residual r = b - A x,
     the update x += d and all norms in float64, the correction d solved
-    approximately by CG in float32 on the float32-rounded matrix.
+    approximately by CG in float32 on the float32-rounded matrix;
+  * CG in float32 with reliable updates (Sleijpen & van der Vorst 1996): the
+    float64 residual replaces the recurred one from time to time instead of
+    restarting the iteration.
 """
 from __future__ import annotations
 
@@ -105,6 +108,59 @@ def ir_cg(A, b: np.ndarray, tol: float = 1e-10, inner_tol: float = 1e-5, inner_m
         inner += k
         hist.append(math.sqrt(float(r @ r)) / bn)
     return x, outer, inner, hist
+
+
+def reliable_cg(A, b: np.ndarray, tol: float = 1e-10, delta: float = 0.1, maxit: int = 100000,
+                vals_low: np.ndarray | None = None):
+    """Mixed-precision CG with reliable updates (Sleijpen & van der Vorst, 1996):
+    one CG recurrence in float32 on the float32 matrix, never restarted;
+    whenever the recurred residual norm has fallen below delta times its value
+    at the last update (or below tol ||b|| / 2), the float32 iterate is added
+    to the float64 solution (and reset), the residual b - A x is recomputed in
+    float64 and replaces the recurred one, and the search direction is kept
+    (beta uses the replaced residual's norm).
+
+    Returns (x, reliable updates, float32 iterations, history of the true
+    ||r|| / ||b|| at the updates)."""
+    b = np.asarray(b, dtype=np.float64)
+    vals32 = (np.asarray(A.values, dtype=np.float64) if vals_low is None else vals_low).astype(np.float32)
+    bn = math.sqrt(float(b @ b))
+    x = np.zeros_like(b)
+    if bn == 0.0:
+        return x, 0, 0, [0.0]
+    r = b.astype(np.float32)
+    x32 = np.zeros_like(r)
+    p = r.copy()
+    rho = np.float32(r @ r)
+    rn_upd = math.sqrt(float(rho))
+    hist = [1.0]
+    k = updates = 0
+    while k < maxit:
+        q = _spmv32(A, vals32, p)
+        pq = np.float32(p @ q)
+        if pq == 0:
+            break
+        alpha = np.float32(rho / pq)
+        x32 = (x32 + alpha * p).astype(np.float32)
+        r = (r - alpha * q).astype(np.float32)
+        rho_new = np.float32(r @ r)
+        k += 1
+        if math.sqrt(float(rho_new)) <= max(delta * rn_upd, 0.5 * tol * bn):
+            x += x32.astype(np.float64)
+            x32[:] = 0
+            r64 = b - csr_spmv(A, x)
+            updates += 1
+            rn = math.sqrt(float(r64 @ r64))
+            hist.append(rn / bn)
+            if rn <= tol * bn:
+                break
+            r = r64.astype(np.float32)
+            rho_new = np.float32(r @ r)
+            rn_upd = rn
+        beta = np.float32(rho_new / rho)
+        p = (r + beta * p).astype(np.float32)
+        rho = rho_new
+    return x, updates, k, hist
 
 
 def poisson3d_eig_bounds(nx: int, ny: int, nz: int) -> tuple[float, float]:

@@ -6,6 +6,10 @@
 // one matrix many times (Introduction). CG is Hestenes & Stiefel's; the
 // refinement loop is the classical one (Wilkinson; Moler 1967):
 //     r = b - A x (float64);  solve A d ~= r / ||r|| in float32;  x += ||r|| d.
+// A third mode keeps one float32 CG recurrence and replaces its residual by the
+// float64 one from time to time (reliable updates, Sleijpen & van der Vorst
+// 1996), which needs about the float64 iteration count instead of paying for
+// restarts.
 // On GB300 float64 arithmetic is issue-bound (one float64 FMA warp-instruction
 // per ~16 SM cycles), so moving the bulk of the work to float32 pays twice:
 // half the bytes per SpMV and no float64 pipe in the inner loop.
@@ -39,6 +43,10 @@ constexpr int kThreads = 256;
 constexpr int kSpmvBlocksPerSm = 4;
 constexpr int kVecBlocksPerSm = 2;
 enum { S_RHO = 0, S_PQ, S_ALPHA, S_BETA, S_RHONEW, S_NORM, S_COUNT = 8 };
+// k_dot_final mode: the recurred residual was replaced (reliable update);
+// beta = rho_new / rho_previous = s * beta / rho, then rho = s
+constexpr int S_REPLACED = 100;
+constexpr double kReliableDelta = 0.1;  // update when the recurred norm fell by this factor
 
 template <class A>
 __device__ __forceinline__ A block_sum(A v) {
@@ -87,6 +95,9 @@ __global__ void __launch_bounds__(kThreads) k_dot_final(const A* __restrict__ pa
       scal[S_RHONEW] = s;
       scal[S_BETA] = scal[S_RHO] != 0.0 ? s / scal[S_RHO] : 0.0;
       scal[S_RHO] = s;
+    } else if (what == S_REPLACED) {
+      scal[S_BETA] = scal[S_RHO] != 0.0 ? s * scal[S_BETA] / scal[S_RHO] : 0.0;
+      scal[S_RHO] = s;
     } else {
       scal[what] = s;
     }
@@ -127,6 +138,21 @@ __global__ void __launch_bounds__(kThreads) k_inner_apply(double* __restrict__ x
   const double nr = sqrt(scal[S_NORM]);
   for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads)
     x64[i] = fma(nr, (double)x32[i], x64[i]);
+}
+
+// reliable update: x64 += x32, x32 = 0
+__global__ void __launch_bounds__(kThreads) k_fold_x(double* __restrict__ x64, float* __restrict__ x32, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads) {
+    x64[i] += (double)x32[i];
+    x32[i] = 0.0f;
+  }
+}
+
+// r32 = (float) r64
+__global__ void __launch_bounds__(kThreads) k_narrow(const double* __restrict__ r64, float* __restrict__ r32,
+                                                     int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads)
+    r32[i] = (float)r64[i];
 }
 
 template <class T>
@@ -372,12 +398,14 @@ cudaError_t cg_iteration(const spc5_matrix* M, T* x, T* r, T* p, T* q, T* w, int
 
 // Runs CG iterations until sqrt(rho) <= stop or max_it; iteration body
 // replayed from a CUDA graph when use_graph. Returns iterations done.
+// `keep`: when not NULL the instantiated graph is taken from / left in *keep
+// for later calls with the same vectors (the caller destroys it).
 template <class T, class A>
 spc5_status cg_loop(const spc5_matrix* M, T* x, T* r, T* p, T* q, T* w, int64_t n, double* scal, A* part, int nb,
                     unsigned* ticket, double stop, int max_it, int check_every, bool use_graph, double* host_scal,
-                    cudaStream_t s, int* iters) {
-  cudaGraphExec_t exec = nullptr;
-  if (use_graph) {
+                    cudaStream_t s, int* iters, cudaGraphExec_t* keep = nullptr) {
+  cudaGraphExec_t exec = keep ? *keep : nullptr;
+  if (use_graph && !exec) {
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(e, "cg: begin capture");
@@ -425,7 +453,10 @@ spc5_status cg_loop(const spc5_matrix* M, T* x, T* r, T* p, T* q, T* w, int64_t 
     prev_norm = nr;
     prev_k = k;
   }
-  if (exec) cudaGraphExecDestroy(exec);
+  if (keep)
+    *keep = exec;
+  else if (exec)
+    cudaGraphExecDestroy(exec);
   *iters = k;
   return st;
 }
@@ -524,6 +555,65 @@ spc5_status cg_impl(const spc5_matrix* A, const spc5_matrix* L, const double* b,
     st = cg_loop<double, double>(A, x, r, p, q, t, n, scal, part, nb, ticket, stop, max_it, every, use_graph, hs, s,
                                  &it);
     info->iterations = it;
+  } else if (o->reliable) {
+    // float32 CG with reliable updates: one recurrence, never restarted; when
+    // its residual norm has fallen by kReliableDelta since the last update,
+    // x += x32 and r = b - A x in float64 replace the recurred quantities
+    // (the search direction is kept, beta rescaled to the new residual)
+    Buf r32_b, p32_b, q32_b, x32_b, w32_b, part32_b;
+    e = r32_b.alloc(sizeof(float) * (size_t)n);
+    if (e == cudaSuccess) e = p32_b.alloc(sizeof(float) * (size_t)n);
+    if (e == cudaSuccess) e = q32_b.alloc(sizeof(float) * (size_t)n);
+    if (e == cudaSuccess) e = x32_b.alloc(sizeof(float) * (size_t)n);
+    if (e == cudaSuccess) e = w32_b.alloc(sizeof(float) * (size_t)n);
+    if (e == cudaSuccess) e = part32_b.alloc(sizeof(float) * (size_t)nparts);
+    if (e != cudaSuccess) return cuda_fail(e, "cg: workspace");
+    float* r32 = (float*)r32_b.p;
+    float* p32 = (float*)p32_b.p;
+    float* q32 = (float*)q32_b.p;
+    float* x32 = (float*)x32_b.p;
+    float* w32 = (float*)w32_b.p;
+    float* part32 = (float*)part32_b.p;
+    // x = 0 (done), r = b; r32 = b, p32 = q32 = x32 = 0, beta = 0, rho = r32.r32
+    k_copy_vec<double><<<nb, kThreads, 0, s>>>(r, b, n);
+    k_narrow<<<nb, kThreads, 0, s>>>(b, r32, n);
+    k_zero_vec<float><<<nb, kThreads, 0, s>>>(p32, n);
+    k_zero_vec<float><<<nb, kThreads, 0, s>>>(q32, n);
+    k_zero_vec<float><<<nb, kThreads, 0, s>>>(x32, n);
+    k_dot_part<float, float><<<nb, kThreads, 0, s>>>(r32, r32, n, part32);
+    k_dot_final<float><<<1, kThreads, 0, s>>>(part32, nb, scal, S_RHO);
+    double rn_upd = bnorm;
+    struct GraphKeep {
+      cudaGraphExec_t g = nullptr;
+      ~GraphKeep() {
+        if (g) cudaGraphExecDestroy(g);
+      }
+    } keep;  // one captured iteration for all stretches between updates
+    for (;;) {
+      const double target = kReliableDelta * rn_upd > 0.5 * stop ? kReliableDelta * rn_upd : 0.5 * stop;
+      int it = 0;
+      st = cg_loop<float, float>(L, x32, r32, p32, q32, w32, n, scal, part32, nb, ticket, target,
+                                 max_it - info->inner_total, every, use_graph, hs, s, &it, &keep.g);
+      if (st != SPC5_OK) return st;
+      info->inner_total += it;
+      // reliable update in float64
+      k_fold_x<<<nb, kThreads, 0, s>>>(x, x32, n);
+      e = spmv_any(A, x, t, s);
+      if (e != cudaSuccess) return cuda_fail(e, "cg: residual spmv");
+      k_residual<<<nb, kThreads, 0, s>>>(r, b, t, n, part);
+      k_dot_final<double><<<1, kThreads, 0, s>>>(part, nb, scal, S_NORM);
+      e = cudaMemcpyAsync(hs, scal, sizeof(hs), cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) return cuda_fail(e, "cg: reliable update");
+      info->outer += 1;
+      const double rn = sqrt(hs[S_NORM]);
+      if (!(rn > stop) || info->inner_total >= max_it || it == 0) break;
+      rn_upd = rn;
+      k_narrow<<<nb, kThreads, 0, s>>>(r, r32, n);
+      k_dot_part<float, float><<<nb, kThreads, 0, s>>>(r32, r32, n, part32);
+      k_dot_final<float><<<1, kThreads, 0, s>>>(part32, nb, scal, S_REPLACED);
+    }
+    info->iterations = info->inner_total;
   } else {
     Buf r32_b, p32_b, q32_b, x32_b, w32_b, part32_b;
     e = r32_b.alloc(sizeof(float) * (size_t)n);

@@ -40,7 +40,7 @@ class Opts(ctypes.Structure):
 class CgOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iters", ctypes.c_int32), ("max_outer", ctypes.c_int32),
                 ("inner_tol", ctypes.c_double), ("inner_max_iters", ctypes.c_int32), ("check_every", ctypes.c_int32),
-                ("use_graph", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+                ("use_graph", ctypes.c_int32), ("reliable", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
 
 
 class CgInfo(ctypes.Structure):
@@ -320,11 +320,13 @@ def copy(src: torch.Tensor, dst: torch.Tensor, stream=None):
 
 def cg(A: Matrix, b: torch.Tensor, A_inner: Matrix | None = None, x: torch.Tensor | None = None, tol: float = 1e-10,
        max_iters: int = 0, max_outer: int = 0, inner_tol: float = 0.0, inner_max_iters: int = 0, check_every: int = 0,
-       use_graph: bool = False, stream=None):
-    """Solve A x = b (float64 CG, or mixed-precision refinement with A_inner). Returns (x, info dict)."""
+       use_graph: bool = False, reliable: bool = False, stream=None):
+    """Solve A x = b (float64 CG, or mixed precision with A_inner: refinement, or one float32
+    recurrence with reliable updates when `reliable`). Returns (x, info dict)."""
     if x is None:
         x = torch.empty_like(b)
-    opts = CgOpts(tol, max_iters, max_outer, inner_tol, inner_max_iters, check_every, 1 if use_graph else 0)
+    opts = CgOpts(tol, max_iters, max_outer, inner_tol, inner_max_iters, check_every, 1 if use_graph else 0,
+                  1 if reliable else 0)
     info = CgInfo()
     _check(load().spc5_cg(A._h, A_inner._h if A_inner is not None else None, _ptr(b), _ptr(x), ctypes.byref(opts),
                           ctypes.byref(info), _stream_ptr(stream)), "spc5_cg")

@@ -70,6 +70,25 @@ def test_mixed_refinement_reaches_float64_residual(cuda_device, low):
     assert abs(info["outer"] - outer_ref) <= 1
 
 
+@pytest.mark.parametrize("low", [torch.float32, torch.bfloat16])
+def test_reliable_updates_reach_float64_residual(cuda_device, low):
+    A = poisson(24)
+    b = inputs.vec_uniform(A.n, seed=0)
+    M64, Ml = handles(A, low=low)
+    bd = torch.from_numpy(b).cuda()
+    x, info = spc5.cg(M64, bd, A_inner=Ml, tol=1e-10, use_graph=True, reliable=True)
+    assert info["converged"] and true_residual(A, x.cpu().numpy(), b) <= 1e-10
+    # one unrestarted recurrence: about the oracle's count, and no more than float64 CG's by much
+    _, upd_ref, k_ref, _ = ocg.reliable_cg(A, b, tol=1e-10, delta=0.1)
+    _, k64, _ = ocg.cg(A, b, tol=1e-10)
+    assert abs(info["iterations"] - k_ref) <= 0.2 * k_ref + 8
+    assert info["iterations"] <= 1.25 * k64 + 8
+    assert info["outer"] >= 2
+    # graph replay and plain launches give the same bits
+    x2, info2 = spc5.cg(M64, bd, A_inner=Ml, tol=1e-10, use_graph=False, reliable=True)
+    assert info2 == info and torch.equal(x, x2)
+
+
 def test_cg_full_size_poisson96(cuda_device):
     # the precision-form CG workload: 7-point Poisson on a 96^3 grid, b uniform[-1,1] seed 0
     A = poisson(96)
@@ -85,6 +104,9 @@ def test_cg_full_size_poisson96(cuda_device):
     assert true_residual(A, x.cpu().numpy(), b) <= 1.05e-10
     xm, im = spc5.cg(M64, bd, A_inner=M32, tol=1e-10, use_graph=True)
     assert im["converged"] and true_residual(A, xm.cpu().numpy(), b) <= 1e-10
+    xr, ir = spc5.cg(M64, bd, A_inner=M32, tol=1e-10, use_graph=True, reliable=True)
+    assert ir["converged"] and true_residual(A, xr.cpu().numpy(), b) <= 1e-10
+    assert ir["iterations"] <= 1.15 * info["iterations"] + 8
 
 
 def test_cg_with_long_interval_segments(cuda_device):
@@ -104,6 +126,9 @@ def test_cg_with_long_interval_segments(cuda_device):
     assert true_residual(A, x.cpu().numpy(), b) <= 1.05e-10
     xm, im = spc5.cg(M64, bd, A_inner=M32, tol=1e-10, use_graph=True)
     assert im["converged"] and true_residual(A, xm.cpu().numpy(), b) <= 1e-10
+    xr, ir = spc5.cg(M64, bd, A_inner=M32, tol=1e-10, use_graph=True, reliable=True)
+    assert ir["converged"] and true_residual(A, xr.cpu().numpy(), b) <= 1e-10
+    assert ir["iterations"] <= 1.15 * info["iterations"] + 8
 
 
 def test_cg_rejects_bad_handles(cuda_device):

@@ -70,3 +70,26 @@ def test_ir_cg_reaches_float64_accuracy():
     assert outer <= 5
     x64, k64, _ = ocg.cg(A, b, tol=1e-10)
     assert np.linalg.norm(x - x64) <= 1e-8 * np.linalg.norm(x64)
+
+
+def test_reliable_cg_reaches_float64_accuracy_with_cg_iteration_count():
+    # the float32 recurrence is never restarted, so it needs about as many
+    # iterations as float64 CG (refinement with restarts needs more), and the
+    # returned x solves the system to the float64 tolerance (checked against
+    # a direct solve)
+    A = inputs.stencil3d(12, 12, 12, points=7, normal_values=False)
+    b = inputs.vec_uniform(A.n, seed=0)
+    _, k64, _ = ocg.cg(A, b, tol=1e-10)
+    x, updates, k, hist = ocg.reliable_cg(A, b, tol=1e-10, delta=0.1)
+    assert hist[-1] <= 1e-10 and updates >= 2
+    assert k <= 1.15 * k64 + 5
+    _, _, inner_ir, _ = ocg.ir_cg(A, b, tol=1e-10, inner_tol=1e-6)
+    assert k <= inner_ir
+    xd = np.linalg.solve(A.to_dense(), b)
+    assert np.linalg.norm(x - xd) <= 1e-8 * np.linalg.norm(xd)
+
+
+def test_reliable_cg_zero_rhs():
+    A = inputs.stencil3d(4, 4, 4, points=7, normal_values=False)
+    x, updates, k, hist = ocg.reliable_cg(A, np.zeros(A.n))
+    assert updates == 0 and k == 0 and not x.any()
