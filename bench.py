@@ -258,7 +258,7 @@ def run_reference(args):
 
 # ---------------------------------------------------------------------- SpMM
 
-def run_spmm_section(mats, dev, ks=(1, 4, 8, 16, 32), tiles=(4, 8, 16, 32), reps: int = 5):
+def run_spmm_section(mats, dev, ks=(1, 4, 8, 16, 32), tiles=(4, -8, -16, -32, 8, 16, 32), reps: int = 5):
     """float32 Y = A X for k right-hand sides on the stencil and R-MAT matrices,
     best (shape, k-tile) per k from a small tuning sweep; GFLOP/s = 2 nnz k / t."""
     import torch
@@ -294,7 +294,7 @@ def run_spmm_section(mats, dev, ks=(1, 4, 8, 16, 32), tiles=(4, 8, 16, 32), reps
             best = None
             for rc, M in Ms.items():
                 for kt in (tiles if k > 1 else (1,)):
-                    if kt > 1 and kt > 2 * k:
+                    if abs(kt) > 1 and abs(kt) > 2 * k:
                         continue
                     t = timed(lambda: M.spmm(X, Y, ktile=kt))
                     if best is None or t < best[0]:

@@ -234,9 +234,11 @@ spc5_status spc5_copy(const void* src_d, void* dst_d, int64_t bytes, spc5_stream
  *   X_d   m-by-k, row-major, leading dimension ldx >= k (row j at X_d + j*ldx).
  *   Y_d   n-by-k, row-major, leading dimension ldy >= k; overwritten.
  *   Element type of X and Y: float64 for SPC5_F64 handles, float32 otherwise.
- *   k     1..1024; ktile = column tile: 1 or 4 (one lane per row holding that
- *         many columns), 8, 16 or 32 (that many lanes per row, one column
- *         each); 0 = choose from k. The grid covers ceil(k / ktile) tiles.
+ *   k     1..1024; ktile = column tile: 1, 4, -8, -16 or -32 (one lane per
+ *         row holding 1 to 32 columns; X rows read as 16-byte vectors when
+ *         X_d is 16-byte aligned and ldx a multiple of 16 bytes), 8, 16 or 32
+ *         (that many lanes per row, one column each); 0 = choose from k. The
+ *         grid covers ceil(k / |ktile|) tiles.
  * A handle with long intervals keeps n_segments * r * k partial sums; the first
  * call with a larger k grows that buffer (cudaMalloc, device synchronisation).
  */

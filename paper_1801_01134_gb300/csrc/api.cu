@@ -194,8 +194,9 @@ spc5_status spc5_spmm(spc5_handle h, int k, const void* X_d, int64_t ldx, void* 
   if (!h) return fail(SPC5_EINVAL, "spmm: NULL handle");
   if (k < 1 || k > 1024) return fail(SPC5_EINVAL, "spmm: k must be in [1, 1024]");
   if (ldx < k || ldy < k) return fail(SPC5_EINVAL, "spmm: leading dimensions must be >= k");
-  if (!(ktile == 0 || ktile == 1 || ktile == 4 || ktile == 8 || ktile == 16 || ktile == 32))
-    return fail(SPC5_EINVAL, "spmm: ktile must be 0, 1, 4, 8, 16 or 32");
+  if (!(ktile == 0 || ktile == 1 || ktile == 4 || ktile == -8 || ktile == -16 || ktile == -32 || ktile == 8 ||
+        ktile == 16 || ktile == 32))
+    return fail(SPC5_EINVAL, "spmm: ktile must be 0, 1, 4, -8, -16, -32, 8, 16 or 32");
   if ((h->m > 0 && !X_d) || (h->n > 0 && !Y_d)) return fail(SPC5_EINVAL, "spmm: NULL matrix");
   return spmm_impl(h, k, X_d, ldx, Y_d, ldy, ktile, (cudaStream_t)stream);
 }

@@ -89,6 +89,7 @@ spc5_status assemble_impl(int64_t n, int64_t m, int64_t nnz, int64_t nb, int r, 
                           const int32_t* brp, const int32_t* bcol, const uint8_t* bmask, const void* vals,
                           const spc5_opts* opt, cudaStream_t s, spc5_matrix** out);
 spc5_status build_order(spc5_matrix* h, cudaStream_t s);
+// block counts of the twelve shapes without conversion (counts.cu)
 cudaError_t launch_block_counts(int64_t n, int64_t nnz, const int64_t* rowptr, const int32_t* colidx,
                                 unsigned long long* acc, cudaStream_t s);
 spc5_status count_blocks_impl(int64_t n, int64_t nnz, const int64_t* rowptr, const int32_t* colidx,

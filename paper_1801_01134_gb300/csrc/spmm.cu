@@ -6,8 +6,9 @@
 // Y n-by-k, both row-major with leading dimensions ldx, ldy >= k.
 //
 // Mappings for the short intervals, chosen by the column tile ktile:
-//   ktile 1 or 4   one lane per row keeps ktile accumulators and, per nonzero,
-//                  reads one matrix value and a ktile-wide slice of an X row;
+//   ktile 1, 4, -8, -16, -32   one lane per row keeps 1 to 32 accumulators
+//                  and, per nonzero, reads one matrix value and that wide a
+//                  slice of an X row (16-byte loads when X rows are aligned);
 //   ktile 8/16/32  ktile lanes per row, one column each: the X values of a
 //                  nonzero are one coalesced load (better for large k).
 // The grid's y dimension covers the column tiles. Long intervals go through
@@ -76,6 +77,30 @@ __device__ __forceinline__ void fma_row(typename T::A (&acc)[KT], typename T::A 
     if (t < kk) acc[t] = fma(v, (typename T::A)__ldg(xr + t), acc[t]);
 }
 
+// the same with the KT values of the X row read as 16-byte vectors (the
+// caller checked the alignment and that the tile is full)
+template <class T, int KT>
+__device__ __forceinline__ void fma_row_vec(typename T::A (&acc)[KT], typename T::A v,
+                                            const typename T::X* __restrict__ xr) {
+  if constexpr (sizeof(typename T::X) == 4) {
+#pragma unroll
+    for (int q = 0; q < KT / 4; ++q) {
+      const float4 t = __ldg(reinterpret_cast<const float4*>(xr) + q);
+      acc[4 * q + 0] = fma(v, (typename T::A)t.x, acc[4 * q + 0]);
+      acc[4 * q + 1] = fma(v, (typename T::A)t.y, acc[4 * q + 1]);
+      acc[4 * q + 2] = fma(v, (typename T::A)t.z, acc[4 * q + 2]);
+      acc[4 * q + 3] = fma(v, (typename T::A)t.w, acc[4 * q + 3]);
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < KT / 2; ++q) {
+      const double2 t = __ldg(reinterpret_cast<const double2*>(xr) + q);
+      acc[2 * q + 0] = fma(v, (typename T::A)t.x, acc[2 * q + 0]);
+      acc[2 * q + 1] = fma(v, (typename T::A)t.y, acc[2 * q + 1]);
+    }
+  }
+}
+
 // short intervals: one lane per row, KT columns of X per lane
 template <class T, int KT>
 __global__ void __launch_bounds__(256) k_spmm_rows(int64_t n, int64_t I, int r, int c, int mb, int32_t long_blocks,
@@ -84,7 +109,7 @@ __global__ void __launch_bounds__(256) k_spmm_rows(int64_t n, int64_t I, int r, 
                                                    const typename T::V* __restrict__ val,
                                                    const int64_t* __restrict__ valptr,
                                                    const typename T::X* __restrict__ X, int64_t ldx,
-                                                   typename T::X* __restrict__ Y, int64_t ldy, int k) {
+                                                   typename T::X* __restrict__ Y, int64_t ldy, int k, bool vec) {
   using A = typename T::A;
   const int lane = threadIdx.x & 31;
   const int S = kWarp / r;
@@ -93,6 +118,7 @@ __global__ void __launch_bounds__(256) k_spmm_rows(int64_t n, int64_t I, int r, 
   const int i = lane % r;
   const int j0 = blockIdx.y * KT;
   const int kk = k - j0 < KT ? k - j0 : KT;
+  const bool full_vec = vec && kk == KT;  // 16-byte X loads for this tile
   if (it >= I || lane >= S * r) return;
   int32_t b = __ldg(brp + it);
   const int32_t bend = __ldg(brp + it + 1);
@@ -113,6 +139,12 @@ __global__ void __launch_bounds__(256) k_spmm_rows(int64_t n, int64_t I, int r, 
     while (bits) {
       const int kb = __ffs(bits) - 1;
       bits &= bits - 1;
+      if constexpr (KT >= 4) {
+        if (full_vec) {
+          fma_row_vec<T, KT>(acc, T::val(vrow, vo++), X + (col0 + kb) * ldx + j0);
+          continue;
+        }
+      }
       fma_row<T, KT>(acc, T::val(vrow, vo++), X + (col0 + kb) * ldx + j0, kk);
     }
   }
@@ -256,9 +288,12 @@ cudaError_t spmm_launch(const spc5_matrix* h, int k, const void* Xv, int64_t ldx
   if (h->I > 0) {
     const int64_t warps = (h->I + S - 1) / S;
     dim3 grid((unsigned)((warps * kWarp + 255) / 256), tiles);
+    // 16-byte X loads when every tile start is 16-byte aligned
+    constexpr int N = 16 / (int)sizeof(X);
+    const bool vec = KT >= 4 && KT % N == 0 && ldx % N == 0 && (reinterpret_cast<uintptr_t>(Xm) & 15u) == 0;
     k_spmm_rows<T, KT><<<grid, 256, 0, s>>>(h->n, h->I, h->r, h->c, h->mb, h->long_blocks, h->long_values,
                                             h->block_rowptr, h->block_colidx, h->block_masks, val, h->valptr, Xm, ldx,
-                                            Ym, ldy, k);
+                                            Ym, ldy, k, vec);
   }
   if (h->nseg > 0) {
     dim3 grid((unsigned)((h->nseg * kWarp + 255) / 256), tiles);
@@ -299,14 +334,17 @@ cudaError_t spmm_launch_cols(const spc5_matrix* h, int k, const void* Xv, int64_
   return cudaGetLastError();
 }
 
-// ktile 1 or 4: one lane per row holding that many columns; 8, 16, 32: that
-// many lanes per row, one column each
+// ktile 1 or 4, and -8 / -16 / -32: one lane per row holding 1, 4, 8, 16 or
+// 32 columns; 8, 16, 32: that many lanes per row, one column each
 template <class T>
 cudaError_t spmm_tile(int kt, const spc5_matrix* h, int k, const void* X, int64_t ldx, void* Y, int64_t ldy,
                       void* part, cudaStream_t s) {
   switch (kt) {
     case 1: return spmm_launch<T, 1>(h, k, X, ldx, Y, ldy, part, s);
     case 4: return spmm_launch<T, 4>(h, k, X, ldx, Y, ldy, part, s);
+    case -8: return spmm_launch<T, 8>(h, k, X, ldx, Y, ldy, part, s);
+    case -16: return spmm_launch<T, 16>(h, k, X, ldx, Y, ldy, part, s);
+    case -32: return spmm_launch<T, 32>(h, k, X, ldx, Y, ldy, part, s);
     case 8: return spmm_launch_cols<T, 8>(h, k, X, ldx, Y, ldy, part, s);
     case 16: return spmm_launch_cols<T, 16>(h, k, X, ldx, Y, ldy, part, s);
     default: return spmm_launch_cols<T, 32>(h, k, X, ldx, Y, ldy, part, s);
@@ -325,7 +363,7 @@ int spmm_auto_tile(int k) {
 
 spc5_status spmm_impl(spc5_matrix* h, int k, const void* X, int64_t ldx, void* Y, int64_t ldy, int ktile,
                       cudaStream_t s) {
-  const int kt = ktile > 0 ? ktile : spmm_auto_tile(k);
+  const int kt = ktile != 0 ? ktile : spmm_auto_tile(k);
   // segment partials: n_segments * r * k accumulators, kept by the handle and
   // grown on demand (the growth synchronises the device)
   const size_t need = (size_t)h->nseg * (size_t)h->r * (size_t)k * (h->vt == SPC5_F64 ? 8 : 4);

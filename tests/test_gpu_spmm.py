@@ -25,7 +25,7 @@ def get(name):
 
 @pytest.mark.parametrize("name", list(MATS))
 @pytest.mark.parametrize("r,c", [(1, 8), (2, 4), (4, 16), (8, 8)])
-@pytest.mark.parametrize("k,ktile", [(1, 0), (3, 4), (8, 0), (13, 8), (32, 0), (32, 32), (5, 1)])
+@pytest.mark.parametrize("k,ktile", [(1, 0), (3, 4), (8, 0), (13, 8), (32, 0), (32, 32), (5, 1), (13, -8), (20, -16)])
 def test_spmm_f64(cuda_device, name, r, c, k, ktile):
     A = get(name)
     X = inputs.vec_uniform(A.m * k, seed=k).reshape(A.m, k)
@@ -62,6 +62,35 @@ def test_spmm_f32_and_column_equals_spmv(cuda_device, name, k):
     for j in (0, k - 1):
         yj = M.spmv(Xd[:, j].contiguous()).double().cpu().numpy()
         assert np.all(np.abs(Y[:, j] - yj) <= 2 * (L[:, 0] + 1) * u * S[:, j] + 1e-45)
+    M.destroy()
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("ktile", [4, -8, -16, -32])
+@pytest.mark.parametrize("pad", [0, 1])
+def test_spmm_row_tiles_vector_and_scalar_loads(cuda_device, dtype, ktile, pad):
+    # pad 0: X rows 16-byte aligned (vector loads of X); pad 1: scalar loads; k not a
+    # multiple of the tile, so the last tile is partial either way
+    A = get("st27_ragged")
+    k = 2 * abs(ktile) + 3
+    vals = A.values if dtype == torch.float64 else oracle.round_f32(A.values)
+    Ar = inputs.CSR(A.n, A.m, A.rowptr, A.colidx, vals)
+    X = inputs.vec_uniform(A.m * k, seed=7).reshape(A.m, k)
+    if dtype == torch.float32:
+        X = oracle.round_f32(X)
+    Yref, S = oracle.csr_spmm_dot2(Ar, X)
+    d = spc5.upload_csr(Ar, dtype, "cuda")
+    M = spc5.convert(d.rowptr, d.colidx, d.values, A.n, A.m, 2, 8)
+    ld = k + pad if pad else ((k + 3) // 4) * 4
+    Xd = torch.zeros(A.m, ld, dtype=dtype, device="cuda")
+    Xd[:, :k] = torch.from_numpy(X).to(dtype)
+    Y = M.spmm(Xd[:, :k], ktile=ktile).double().cpu().numpy()
+    L = np.diff(A.rowptr).astype(np.float64)[:, None]
+    if dtype == torch.float64:
+        assert np.all(np.abs(Y - Yref) <= 1e-13 * S)
+    else:
+        u = 2.0**-24
+        assert np.all(np.abs(Y - Yref) <= (L + 1) * u / (1 - (L + 1) * u) * S + 1e-45)
     M.destroy()
 
 
