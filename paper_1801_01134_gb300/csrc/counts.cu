@@ -11,10 +11,14 @@
 //     for c = 4, 8 and 16 at once.
 //   * r > 1: one thread per interval walks the merged columns of its r rows
 //     (heads kept in registers, one load per step) and counts the greedy
-//     blocks for c = 4, 8 and 16 in the same walk.
+//     blocks for c = 4, 8 and 16 in the same walk; intervals with more than
+//     kLongEntries entries (power-law hubs) are cut into chunks along their
+//     longest row at columns that start a block in every cover (no merged
+//     column in the 16 before them), one thread per chunk.
 // All counts are integers summed with atomics, so the order of the sums does
 // not matter.
 #include <climits>
+#include <vector>
 
 #include "internal.cuh"
 
@@ -80,46 +84,143 @@ __global__ void __launch_bounds__(256) k_count_r1(int64_t n, int64_t nnz, const 
   for (int q = 0; q < 3; ++q) warp_add(&acc[q], cnt[q]);
 }
 
+// Greedy block counts (c = 4, 8, 16) of the merged columns of rows
+// row0 .. row0 + R - 1 that lie in [lo, hi); lo must start a block for every c
+// (the first column of the interval, or one with no merged column in the 16
+// before it).
+template <int R>
+__device__ __forceinline__ void count_merged(int64_t n, int64_t row0, const int64_t* __restrict__ rowptr,
+                                             const int32_t* __restrict__ colidx, int32_t lo, int32_t hi,
+                                             unsigned long long (&cnt)[3]) {
+  int64_t h[R], e[R];
+  int32_t cur[R];
+#pragma unroll
+  for (int i = 0; i < R; ++i) {
+    if (row0 + i < n) {
+      h[i] = rowptr[row0 + i];
+      e[i] = rowptr[row0 + i + 1];
+      if (lo > INT_MIN) {  // first entry >= lo
+        int64_t a = h[i], b = e[i];
+        while (a < b) {
+          const int64_t mid = (a + b) >> 1;
+          if (colidx[mid] < lo) a = mid + 1; else b = mid;
+        }
+        h[i] = a;
+      }
+    } else {
+      h[i] = e[i] = 0;
+    }
+    cur[i] = h[i] < e[i] && colidx[h[i]] < hi ? colidx[h[i]] : INT_MAX;
+  }
+  int64_t end[3] = {LLONG_MIN, LLONG_MIN, LLONG_MIN};
+  for (;;) {
+    int32_t s = INT_MAX;
+#pragma unroll
+    for (int i = 0; i < R; ++i) s = cur[i] < s ? cur[i] : s;
+    if (s == INT_MAX) break;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      if ((int64_t)s >= end[q]) {
+        ++cnt[q];
+        end[q] = (int64_t)s + (4 << q);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+      if (cur[i] == s) {
+        ++h[i];
+        cur[i] = h[i] < e[i] && colidx[h[i]] < hi ? colidx[h[i]] : INT_MAX;
+      }
+    }
+  }
+}
+
+constexpr int64_t kLongEntries = 1024;  // intervals with more entries are counted in chunks
+constexpr int kChunk = 256;             // entries of the longest row per chunk
+
+struct LongInterval {
+  int64_t it;       // interval
+  int64_t row;      // its longest row
+  int64_t first;    // that row's first entry
+  int64_t len;      // and its length
+};
+
 template <int R>
 __global__ void __launch_bounds__(256) k_count_rk(int64_t n, int64_t I, const int64_t* __restrict__ rowptr,
                                                   const int32_t* __restrict__ colidx,
-                                                  unsigned long long* __restrict__ acc) {
+                                                  unsigned long long* __restrict__ acc, LongInterval* __restrict__ longs,
+                                                  unsigned long long* __restrict__ nlong, int64_t cap) {
   const int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   unsigned long long cnt[3] = {0ull, 0ull, 0ull};
   if (it < I) {
     const int64_t row0 = it * R;
-    int64_t h[R], e[R];
-    int32_t cur[R];
-#pragma unroll
-    for (int i = 0; i < R; ++i) {
-      if (row0 + i < n) {
-        h[i] = rowptr[row0 + i];
-        e[i] = rowptr[row0 + i + 1];
-      } else {
-        h[i] = e[i] = 0;
+    const int64_t rend = row0 + R < n ? row0 + R : n;
+    if (rowptr[rend] - rowptr[row0] > kLongEntries) {
+      // counted by k_count_long in chunks along its longest row
+      LongInterval li{it, row0, rowptr[row0], 0};
+      for (int64_t row = row0; row < rend; ++row) {
+        const int64_t len = rowptr[row + 1] - rowptr[row];
+        if (len > li.len) li = LongInterval{it, row, rowptr[row], len};
       }
-      cur[i] = h[i] < e[i] ? colidx[h[i]] : INT_MAX;
+      const unsigned long long slot = atomicAdd(nlong, 1ull);
+      if ((int64_t)slot < cap) longs[slot] = li;
+    } else {
+      count_merged<R>(n, row0, rowptr, colidx, INT_MIN, INT_MAX, cnt);
     }
-    int64_t end[3] = {LLONG_MIN, LLONG_MIN, LLONG_MIN};
-    for (;;) {
-      int32_t s = INT_MAX;
+  }
 #pragma unroll
-      for (int i = 0; i < R; ++i) s = cur[i] < s ? cur[i] : s;
-      if (s == INT_MAX) break;
+  for (int q = 0; q < 3; ++q) warp_add(&acc[q], cnt[q]);
+}
+
+// A long interval in chunks: chunk j looks for its start among the entries
+// j*kChunk .. (j+1)*kChunk - 1 of the longest row, taking the first column
+// with no merged column of the interval in the 16 before it (such a column
+// starts a block in every cover with c <= 16, so the covers on either side
+// are independent); it counts the blocks from there to the next chunk's start
+// (the first such column from entry (j+1)*kChunk on). A chunk without such a
+// column counts nothing: the chunk before it runs on through its range.
+// task = (index into longs, chunk)
+template <int R>
+__device__ __forceinline__ bool clean_start(int64_t n, int64_t row0, const int64_t* __restrict__ rowptr,
+                                            const int32_t* __restrict__ colidx, int32_t b) {
 #pragma unroll
-      for (int q = 0; q < 3; ++q) {
-        if ((int64_t)s >= end[q]) {
-          ++cnt[q];
-          end[q] = (int64_t)s + (4 << q);
-        }
-      }
-#pragma unroll
-      for (int i = 0; i < R; ++i) {
-        if (cur[i] == s) {
-          ++h[i];
-          cur[i] = h[i] < e[i] ? colidx[h[i]] : INT_MAX;
-        }
-      }
+  for (int i = 0; i < R; ++i) {
+    if (row0 + i >= n) break;
+    int64_t a = rowptr[row0 + i], e = rowptr[row0 + i + 1];
+    while (a < e) {  // first entry >= b
+      const int64_t mid = (a + e) >> 1;
+      if (colidx[mid] < b) a = mid + 1; else e = mid;
+    }
+    if (a > rowptr[row0 + i] && colidx[a - 1] > b - 16) return false;
+  }
+  return true;
+}
+
+template <int R>
+__device__ __forceinline__ int32_t next_start(int64_t n, const LongInterval& li, const int64_t* __restrict__ rowptr,
+                                              const int32_t* __restrict__ colidx, int64_t from, int64_t to) {
+  for (int64_t p = from; p < to && p < li.len; ++p) {
+    const int32_t b = colidx[li.first + p];
+    if (clean_start<R>(n, li.it * R, rowptr, colidx, b)) return b;
+  }
+  return INT_MAX;
+}
+
+template <int R>
+__global__ void __launch_bounds__(256) k_count_long(int64_t n, const int64_t* __restrict__ rowptr,
+                                                    const int32_t* __restrict__ colidx,
+                                                    const LongInterval* __restrict__ longs, const int2* __restrict__ tasks,
+                                                    int64_t ntasks, unsigned long long* __restrict__ acc) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned long long cnt[3] = {0ull, 0ull, 0ull};
+  if (t < ntasks) {
+    const int2 tk = tasks[t];
+    const LongInterval li = longs[tk.x];
+    const int64_t j = tk.y;
+    const int32_t lo = j == 0 ? INT_MIN : next_start<R>(n, li, rowptr, colidx, j * kChunk, (j + 1) * kChunk);
+    if (lo != INT_MAX) {
+      const int32_t hi = next_start<R>(n, li, rowptr, colidx, (j + 1) * kChunk, li.len);
+      count_merged<R>(n, li.it * R, rowptr, colidx, lo, hi, cnt);
     }
   }
 #pragma unroll
@@ -157,11 +258,58 @@ cudaError_t launch_block_counts(int64_t n, int64_t nnz, const int64_t* rowptr, c
   if (e != cudaSuccess) return e;
   const int64_t th = (nnz + kPerThread - 1) / kPerThread;
   if (th > 0) k_count_r1<<<(unsigned)((th + 255) / 256), 256, 0, s>>>(n, nnz, rowptr, colidx, acc);
-  const int64_t I2 = (n + 1) / 2, I4 = (n + 3) / 4, I8 = (n + 7) / 8;
-  if (I2 > 0) k_count_rk<2><<<(unsigned)((I2 + 255) / 256), 256, 0, s>>>(n, I2, rowptr, colidx, acc + 3);
-  if (I4 > 0) k_count_rk<4><<<(unsigned)((I4 + 255) / 256), 256, 0, s>>>(n, I4, rowptr, colidx, acc + 6);
-  if (I8 > 0) k_count_rk<8><<<(unsigned)((I8 + 255) / 256), 256, 0, s>>>(n, I8, rowptr, colidx, acc + 9);
   if (n > 0) k_row_stats<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, rowptr, acc + 12);
+  // r = 2, 4, 8: short intervals directly, long ones listed and then counted in chunks
+  const int64_t cap = nnz / kLongEntries + 1;
+  LongInterval* longs = nullptr;
+  unsigned long long* nlong = nullptr;
+  e = cudaMallocAsync((void**)&longs, sizeof(LongInterval) * (size_t)cap, s);
+  if (e == cudaSuccess) e = cudaMallocAsync((void**)&nlong, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  for (int a = 1; a < 4 && e == cudaSuccess; ++a) {
+    const int r = 1 << a;
+    const int64_t I = (n + r - 1) / r;
+    if (I == 0) continue;
+    e = cudaMemsetAsync(nlong, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) break;
+    const unsigned g = (unsigned)((I + 255) / 256);
+    unsigned long long* dst = acc + 3 * a;
+    switch (r) {
+      case 2: k_count_rk<2><<<g, 256, 0, s>>>(n, I, rowptr, colidx, dst, longs, nlong, cap); break;
+      case 4: k_count_rk<4><<<g, 256, 0, s>>>(n, I, rowptr, colidx, dst, longs, nlong, cap); break;
+      default: k_count_rk<8><<<g, 256, 0, s>>>(n, I, rowptr, colidx, dst, longs, nlong, cap); break;
+    }
+    unsigned long long nl = 0;
+    e = cudaMemcpyAsync(&nl, nlong, sizeof(nl), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess || nl == 0) continue;
+    std::vector<LongInterval> hl((size_t)nl);
+    e = cudaMemcpyAsync(hl.data(), longs, sizeof(LongInterval) * (size_t)nl, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) break;
+    std::vector<int2> tasks;
+    for (size_t q = 0; q < hl.size(); ++q)
+      for (int64_t j = 0; j * kChunk < hl[q].len; ++j) tasks.push_back(make_int2((int)q, (int)j));
+    int2* td = nullptr;
+    e = cudaMallocAsync((void**)&td, sizeof(int2) * tasks.size(), s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(td, tasks.data(), sizeof(int2) * tasks.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) {
+      const int64_t nt = (int64_t)tasks.size();
+      const unsigned gt = (unsigned)((nt + 255) / 256);
+      switch (r) {
+        case 2: k_count_long<2><<<gt, 256, 0, s>>>(n, rowptr, colidx, longs, td, nt, dst); break;
+        case 4: k_count_long<4><<<gt, 256, 0, s>>>(n, rowptr, colidx, longs, td, nt, dst); break;
+        default: k_count_long<8><<<gt, 256, 0, s>>>(n, rowptr, colidx, longs, td, nt, dst); break;
+      }
+      e = cudaGetLastError();
+      // the host task list must live until the copy ran
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    }
+    if (td) cudaFreeAsync(td, s);
+  }
+  cudaFreeAsync(longs, s);
+  cudaFreeAsync(nlong, s);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 

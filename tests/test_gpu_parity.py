@@ -294,6 +294,42 @@ def test_count_blocks_matches_oracle(cuda_device):
         assert list(got) == want
 
 
+def _long_rows_csr():
+    # rows far longer than the chunked counting threshold: sparse random,
+    # one dense run, and clusters with gaps around c
+    rng = np.random.default_rng(5)
+    m = 200_000
+    rows = []
+    for i in range(64):
+        if i == 5:
+            cols = rng.choice(m, 30_000, replace=False)
+        elif i == 6:
+            cols = np.arange(1000, 21_000)
+        elif i == 7:
+            starts = np.cumsum(rng.integers(5, 21, 6000)) + 3
+            cols = np.unique(np.concatenate([starts, starts + 1, starts + 2]))
+            cols = cols[cols < m]
+        elif i in (4, 13):  # neighbours of the long rows inside their intervals
+            cols = rng.choice(m, 9000, replace=False)
+        else:
+            cols = rng.choice(m, rng.integers(0, 40), replace=False)
+        rows.append(np.sort(cols).astype(np.int32))
+    rowptr = np.zeros(65, np.int64)
+    rowptr[1:] = np.cumsum([len(r) for r in rows])
+    colidx = np.concatenate(rows)
+    return inputs.CSR(64, m, rowptr, colidx, np.ones(colidx.size))
+
+
+def test_count_blocks_long_rows_match_oracle(cuda_device):
+    A = _long_rows_csr()
+    d = dev_csr(A)
+    got = spc5.count_blocks(d.rowptr, d.colidx, A.n, A.m)
+    want = [oracle.beta_count(A, r, c)[1] for r, c in spc5.SHAPES]
+    assert list(got) == want
+    f = spc5.features(d)
+    assert np.allclose(f[:12], [A.nnz / w for w in want], rtol=0, atol=0)
+
+
 def test_copy_kernel(cuda_device):
     a = torch.randint(0, 2**31, (1 << 20,), dtype=torch.int32, device="cuda")
     b = torch.zeros_like(a)
