@@ -632,14 +632,49 @@ void free_matrix(spc5_matrix* h) {
   cudaFree(h->order);
   cudaFree(h->spmm_scratch);
   cudaFree(h->block_rowptr);
-  cudaFree(h->block_colidx);
-  cudaFree(h->block_masks);
-  cudaFree(h->values);
-  cudaFree(h->valptr);
-  cudaFree(h->segs);
   cudaFree(h->seg_first);
-  cudaFree(h->partials);
+  if (h->arena) {
+    cudaFree(h->arena);
+  } else {
+    cudaFree(h->block_colidx);
+    cudaFree(h->block_masks);
+    cudaFree(h->values);
+    cudaFree(h->valptr);
+    cudaFree(h->segs);
+    cudaFree(h->partials);
+  }
   delete h;
+}
+
+// One allocation for the arrays whose sizes are known once the blocks are
+// counted: each region starts on a 256-byte boundary and is followed by at
+// least 16 bytes of padding (zeroed; the window and vector loads may read
+// into it).
+cudaError_t alloc_arena(spc5_matrix* h, int64_t nb, int64_t nnz, int64_t ns, cudaStream_t s) {
+  const size_t vsz = value_size(h->vt), asz = h->vt == SPC5_F64 ? 8 : 4;
+  const size_t bytes[6] = {sizeof(int32_t) * (size_t)nb,        (size_t)nb * (size_t)h->mb,
+                           vsz * (size_t)nnz,                   sizeof(int64_t) * (size_t)(h->I + 1),
+                           sizeof(Segment) * (size_t)ns,        asz * (size_t)ns * (size_t)h->r};
+  size_t off[6], total = 0;
+  for (int q = 0; q < 6; ++q) {
+    off[q] = total;
+    total += ((bytes[q] + 16 + 255) / 256) * 256;
+  }
+  uint8_t* base = nullptr;
+  cudaError_t e = cudaMalloc((void**)&base, total);
+  if (e != cudaSuccess) return e;
+  h->arena = base;
+  h->block_colidx = reinterpret_cast<int32_t*>(base + off[0]);
+  h->block_masks = base + off[1];
+  h->values = base + off[2];
+  h->valptr = reinterpret_cast<int64_t*>(base + off[3]);
+  h->segs = reinterpret_cast<Segment*>(base + off[4]);
+  h->partials = base + off[5];
+  for (int q = 0; q < 6 && e == cudaSuccess; ++q) {
+    const size_t end = q < 5 ? off[q + 1] : total;
+    e = cudaMemsetAsync(base + off[q] + bytes[q], 0, end - off[q] - bytes[q], s);  // the padding
+  }
+  return e;
 }
 
 // allocation padded to a multiple of 16 bytes plus 16 (bulk copies may round up)
@@ -1097,12 +1132,7 @@ spc5_status convert_impl(int64_t n, int64_t m, int64_t nnz, const int64_t* rowpt
   h->nseg = ns;
 
   // 4. arrays + fill
-  e = alloc_padded((void**)&h->block_colidx, sizeof(int32_t) * (size_t)nb, s);
-  if (e == cudaSuccess) e = alloc_padded((void**)&h->block_masks, (size_t)nb * (size_t)h->mb, s);
-  if (e == cudaSuccess) e = alloc_padded(&h->values, value_size(vt) * (size_t)nnz, s);
-  if (e == cudaSuccess) e = alloc_padded((void**)&h->valptr, sizeof(int64_t) * (size_t)(I + 1), s);
-  if (e == cudaSuccess) e = alloc_padded((void**)&h->segs, sizeof(Segment) * (size_t)ns, s);
-  if (e == cudaSuccess) e = alloc_padded(&h->partials, (vt == SPC5_F64 ? 8 : 4) * (size_t)ns * (size_t)r, s);
+  e = alloc_arena(h, nb, nnz, ns, s);
   if (e != cudaSuccess) return bail(e == cudaErrorMemoryAllocation ? fail(SPC5_ENOMEM, "convert: out of device memory")
                                                                     : cuda_fail(e, "convert: allocation"));
   const int32_t* sp = ns > 0 ? (const int32_t*)segptr.p : nullptr;

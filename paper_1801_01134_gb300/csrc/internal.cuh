@@ -62,6 +62,9 @@ struct spc5_matrix {
   // SpMM segment partials, grown on demand
   void* spmm_scratch = nullptr;
   size_t spmm_scratch_bytes = 0;
+  // when not NULL, one allocation holding block_colidx, block_masks, values,
+  // valptr, segs and partials (freed as a whole)
+  void* arena = nullptr;
   // work order of the lane-per-row kernel (short intervals only)
   int64_t norder = 0;
   int32_t* order = nullptr;            // [norder] interval indices
