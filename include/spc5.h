@@ -167,6 +167,19 @@ spc5_status spc5_spmv_acc(spc5_handle h, const void* x_d, void* y_d, spc5_stream
 spc5_status spc5_set_variant(spc5_handle h, int variant, spc5_stream_t stream);
 
 /*
+ * spc5_autotune - time the short-interval kernel variants on this handle and
+ * this GPU (median of `reps` SpMVs each, x_d / y_d as in spc5_spmv, y_d
+ * overwritten) and keep the fastest; the GPU form of the paper's choice of
+ * the best kernel for a matrix (section "Performance prediction and optimal
+ * kernel selection"). Candidates: variants 5, 10, 13, 15, plus 16 and 18 for
+ * float32 / bfloat16 values (the ones that win on some matrix). Writes the
+ * chosen variant and its median milliseconds (either pointer may be NULL).
+ * Synchronises `stream`. On error the handle keeps its previous variant.
+ */
+spc5_status spc5_autotune(spc5_handle h, const void* x_d, void* y_d, int reps, int* variant_out, float* ms_out,
+                          spc5_stream_t stream);
+
+/*
  * spc5_spmv_noalloc - y = A x like spc5_spmv, for callers that cannot have a
  * library allocate device memory (their memory is owned by another
  * component's pool, or every allocation is budgeted up front). The paper has

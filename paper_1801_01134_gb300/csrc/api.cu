@@ -265,6 +265,57 @@ spc5_status spc5_time_formats(int64_t n, int64_t m, int64_t nnz, const int64_t* 
   return st;
 }
 
+spc5_status spc5_autotune(spc5_handle h, const void* x_d, void* y_d, int reps, int* variant_out, float* ms_out,
+                          spc5_stream_t stream) {
+  if (!h) return fail(SPC5_EINVAL, "autotune: NULL handle");
+  if (reps < 1) return fail(SPC5_EINVAL, "autotune: reps < 1");
+  if ((h->m > 0 && !x_d) || (h->n > 0 && !y_d)) return fail(SPC5_EINVAL, "autotune: NULL vector");
+  // the decodes that win somewhere: flattened (natural, sorted), mask windows
+  // (sorted); for float32 / bfloat16 also the unrolled bit positions
+  static const int kF64[] = {5, 10, 13, 15};
+  static const int kLow[] = {5, 10, 13, 15, 16, 18};
+  const int* cand = h->vt == SPC5_F64 ? kF64 : kLow;
+  const int ncand = h->vt == SPC5_F64 ? 4 : 6;
+  const cudaStream_t s = (cudaStream_t)stream;
+  const int keep = h->variant;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e != cudaSuccess) return cuda_fail(e, "autotune: events");
+  spc5_status st = SPC5_OK;
+  int best = keep;
+  float best_ms = -1.0f;
+  for (int q = 0; q < ncand && st == SPC5_OK; ++q) {
+    st = spc5_set_variant(h, cand[q], stream);
+    if (st == SPC5_OK) st = spc5_spmv(h, x_d, y_d, stream);  // untimed
+    std::vector<float> t((size_t)reps);
+    for (int k = 0; k < reps && st == SPC5_OK; ++k) {
+      e = cudaEventRecord(e0, s);
+      if (e == cudaSuccess) st = spc5_spmv(h, x_d, y_d, stream);
+      if (e == cudaSuccess && st == SPC5_OK) e = cudaEventRecord(e1, s);
+      if (e == cudaSuccess && st == SPC5_OK) e = cudaEventSynchronize(e1);
+      if (e == cudaSuccess && st == SPC5_OK) e = cudaEventElapsedTime(&t[(size_t)k], e0, e1);
+      if (e != cudaSuccess) st = cuda_fail(e, "autotune: timing");
+    }
+    if (st == SPC5_OK) {
+      std::sort(t.begin(), t.end());
+      const float med = t[(size_t)reps / 2];
+      if (best_ms < 0.0f || med < best_ms) {
+        best_ms = med;
+        best = cand[q];
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  const spc5_status st2 = spc5_set_variant(h, st == SPC5_OK ? best : keep, stream);
+  if (st != SPC5_OK) return st;
+  if (st2 != SPC5_OK) return st2;
+  if (variant_out) *variant_out = best;
+  if (ms_out) *ms_out = best_ms;
+  return SPC5_OK;
+}
+
 int spc5_mlp_nparams(void) { return mlp_param_count(); }
 
 spc5_status spc5_mlp_train(float* params_d, const float* X_d, const float* Y_d, const float* M_d, int N, int epochs,

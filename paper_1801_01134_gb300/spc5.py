@@ -89,6 +89,7 @@ def load(build_if_missing: bool = False):
     lib.spc5_spmv_acc.argtypes = [vp, vp, vp, vp]
     lib.spc5_export.argtypes = [vp, ctypes.POINTER(Arrays)]
     lib.spc5_set_variant.argtypes = [vp, i32, vp]
+    lib.spc5_autotune.argtypes = [vp, vp, vp, i32, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_float), vp]
     lib.spc5_destroy.argtypes = [vp]
     lib.spc5_last_error.argtypes = []
     lib.spc5_last_error.restype = ctypes.c_char_p
@@ -115,7 +116,7 @@ def load(build_if_missing: bool = False):
     lib.spc5_mlp_infer.argtypes = [vp, vp, i32, vp, vp]
     lib.spc5_poly_fit.argtypes = [vp, vp, i32, i32, vp]
     lib.spc5_select.argtypes = [i64, i64, i64, vp, vp, vp, i32, i32, ctypes.POINTER(Selector), vp, vp, vp, vp]
-    for f in (lib.spc5_convert, lib.spc5_assemble, lib.spc5_spmv, lib.spc5_spmv_acc, lib.spc5_export, lib.spc5_destroy, lib.spc5_set_variant,
+    for f in (lib.spc5_convert, lib.spc5_assemble, lib.spc5_autotune, lib.spc5_spmv, lib.spc5_spmv_acc, lib.spc5_export, lib.spc5_destroy, lib.spc5_set_variant,
               lib.spc5_count_blocks, lib.spc5_csr_spmv, lib.spc5_copy, lib.spc5_fma_rate, lib.spc5_fma_rate_lanes,
               lib.spc5_spmv_noalloc, lib.spc5_cg, lib.spc5_spmm, lib.spc5_features,
               lib.spc5_time_formats, lib.spc5_mlp_train, lib.spc5_mlp_grad, lib.spc5_mlp_infer, lib.spc5_poly_fit,
@@ -208,6 +209,14 @@ class Matrix:
                                 Y.data_ptr() if Y.numel() else None, Y.stride(0), ktile, _stream_ptr(stream)),
                "spc5_spmm")
         return Y
+
+    def autotune(self, x: torch.Tensor, y: torch.Tensor, reps: int = 5, stream=None) -> tuple[int, float]:
+        """Time the kernel variants on this matrix and keep the fastest; returns (variant, median ms)."""
+        v = ctypes.c_int32()
+        ms = ctypes.c_float()
+        _check(load().spc5_autotune(self._h, _ptr(x), _ptr(y), reps, ctypes.byref(v), ctypes.byref(ms),
+                                    _stream_ptr(stream)), "spc5_autotune")
+        return v.value, ms.value
 
     def set_variant(self, variant: int, stream=None):
         """Switch the short-interval kernel variant (see spc5_opts.variant)."""

@@ -144,6 +144,22 @@ def test_variants_sum_in_the_same_order(cuda_device, name, r, c):
         M.destroy()
 
 
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_autotune_keeps_a_candidate_and_the_result(cuda_device, dtype):
+    A = get("rmat11")
+    vals = A.values if dtype == torch.float64 else oracle.round_f32(A.values)
+    d = dev_csr(inputs.CSR(A.n, A.m, A.rowptr, A.colidx, vals), dtype)
+    M = spc5.convert(d.rowptr, d.colidx, d.values, A.n, A.m, 1, 8)
+    xd = torch.from_numpy(inputs.vec_uniform(A.m, seed=0)).to(torch.float64 if dtype == torch.float64 else torch.float32).cuda()
+    ref = M.spmv(xd).clone()
+    y = torch.empty_like(ref)
+    v, ms = M.autotune(xd, y, reps=3)
+    cands = (5, 10, 13, 15) if dtype == torch.float64 else (5, 10, 13, 15, 16, 18)
+    assert v in cands and ms > 0
+    assert torch.equal(M.spmv(xd), ref)  # every variant adds in the same order
+    M.destroy()
+
+
 @pytest.mark.parametrize("r,c", spc5.SHAPES)
 def test_long_interval_segments(cuda_device, r, c):
     # force every interval with more than one block onto the segment path
