@@ -60,7 +60,7 @@ typedef struct {
   /* An interval with more than long_blocks blocks is processed by whole warps
    * in segments of seg_blocks blocks instead of one lane per row. 0 selects
    * the defaults: long_blocks = max(64, 4 x mean blocks per interval),
-   * seg_blocks = 256. */
+   * seg_blocks = 384. */
   int32_t long_blocks;
   int32_t seg_blocks;
   /* SpMV kernel variant for short intervals (one lane per row):
@@ -68,7 +68,7 @@ typedef struct {
    *   3       natural order, 4 nonzeros per trip;
    *   1       natural order, one nonzero per trip (plain form);
    *   9 / 10  intervals taken in a work order sorted by row length inside
-   *           windows of 4096 rows (2 / 4 nonzeros per trip); the order is
+   *           windows of order_window rows (2 / 4 nonzeros per trip); the order is
    *           built at conversion.
    *   12 / 14 natural order, block masks read as 8-byte windows of 8/mb
    *           blocks (no memory round trip per block; for low fill),
@@ -82,9 +82,8 @@ typedef struct {
    * the flattened one otherwise.
    * All variants compute the same sums in the same order per row. */
   int32_t variant;
-  /* Rows per sorting window of the work order of variants 9, 10, 13, 15:
-   * 0 selects 4096; a negative value sorts all intervals together (heaviest
-   * warps first, for heavy-tailed row lengths). */
+  /* Rows per sorting window of the work order of the sorted variants:
+   * 0 selects 1024; a negative value sorts all intervals together. */
   int32_t order_window;
   int32_t reserved[4];
 } spc5_opts;

@@ -736,7 +736,7 @@ void launch_order_key(int c, const spc5_matrix* h, int32_t* key, cudaStream_t s)
 // warp's multiply-adds are fully packed. Small windows keep the rows that
 // neighbouring warps read close together in memory (measured: one global
 // sort, or handing whole thread blocks out heaviest first, is slower on
-// power-law graphs than 4096-row windows). The storage is untouched; only the
+// power-law graphs than 1024-row windows). The storage is untouched; only the
 // assignment of intervals to lanes changes.
 spc5_status build_order(spc5_matrix* h, cudaStream_t s) {
   if (h->order || h->I == 0) return SPC5_OK;

@@ -15,10 +15,10 @@ namespace spc5 {
 // max(kLongBlocks, 4 x mean blocks per interval) blocks is split into
 // segments of kSegBlocks blocks, each handled by a warp.
 constexpr int kLongBlocks = 64;
-constexpr int kSegBlocks = 256;
+constexpr int kSegBlocks = 384;  // measured best of 256 / 384 / 512 on R-MAT scale 22
 constexpr int kWarp = 32;
 
-constexpr int kOrderWindow = 4096;  // rows per sorting window of the work order
+constexpr int kOrderWindow = 1024;  // rows per sorting window of the work order (best of 1024 / 2048 / 4096)
 
 // short-interval kernel variants (spc5_opts.variant)
 inline bool valid_variant(int v) {
