@@ -647,7 +647,7 @@ cudaError_t launch_beta(const spc5_matrix* h, const void* xv, void* yv, bool acc
   constexpr int S = kWarp / R;
   const int threads = 256;
   const int v = h->variant;
-  const bool ordered = (v == 9 || v == 10 || v == 13 || v == 15) && h->norder > 0;
+  const bool ordered = ordered_variant(v) && h->norder > 0;
   if (h->I > 0) {
     const int64_t warps = ordered ? (h->norder + S - 1) / S : (h->I + S - 1) / S;
     const unsigned grid = (unsigned)((warps * kWarp + threads - 1) / threads);
