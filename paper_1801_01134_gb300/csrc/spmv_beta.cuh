@@ -473,18 +473,16 @@ __device__ __forceinline__ typename T::A row_sum(int i, int32_t b, int32_t bend,
 // (the sorted work order built at conversion; long intervals are not in it).
 // DEC picks the row decode (see row_sum).
 template <int R, int C, class T, bool ACCUM, int U, bool ORDER, int DEC>
-__global__ void __launch_bounds__(256) k_spmv_rows_u(int64_t n, int64_t I, int32_t long_blocks, int64_t long_values,
-                                                     const int32_t* __restrict__ brp, const int32_t* __restrict__ bcol,
-                                                     const uint8_t* __restrict__ bmask,
-                                                     const typename T::V* __restrict__ val,
-                                                     const int64_t* __restrict__ valptr,
-                                                     const typename T::X* __restrict__ x,
-                                                     typename T::X* __restrict__ y,
-                                                     const int32_t* __restrict__ order, int64_t norder) {
+__device__ __forceinline__ void rows_u_body(int64_t bid, int64_t n, int64_t I, int32_t long_blocks,
+                                            int64_t long_values, const int32_t* __restrict__ brp,
+                                            const int32_t* __restrict__ bcol, const uint8_t* __restrict__ bmask,
+                                            const typename T::V* __restrict__ val,
+                                            const int64_t* __restrict__ valptr, const typename T::X* __restrict__ x,
+                                            typename T::X* __restrict__ y, const int32_t* __restrict__ order,
+                                            int64_t norder) {
   constexpr int S = kWarp / R;
-  using A = typename T::A;
   const int lane = threadIdx.x & 31;
-  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t warp = (bid * blockDim.x + threadIdx.x) >> 5;
   int64_t it = warp * S + lane / R;
   if (ORDER) {
     if (it >= norder) return;
@@ -506,6 +504,19 @@ __global__ void __launch_bounds__(256) k_spmv_rows_u(int64_t n, int64_t I, int32
   }
 }
 
+template <int R, int C, class T, bool ACCUM, int U, bool ORDER, int DEC>
+__global__ void __launch_bounds__(256) k_spmv_rows_u(int64_t n, int64_t I, int32_t long_blocks, int64_t long_values,
+                                                     const int32_t* __restrict__ brp, const int32_t* __restrict__ bcol,
+                                                     const uint8_t* __restrict__ bmask,
+                                                     const typename T::V* __restrict__ val,
+                                                     const int64_t* __restrict__ valptr,
+                                                     const typename T::X* __restrict__ x,
+                                                     typename T::X* __restrict__ y,
+                                                     const int32_t* __restrict__ order, int64_t norder) {
+  rows_u_body<R, C, T, ACCUM, U, ORDER, DEC>(blockIdx.x, n, I, long_blocks, long_values, brp, bcol, bmask, val, valptr,
+                                             x, y, order, norder);
+}
+
 // -------------------------------------------------------- long intervals
 // A warp per segment (at most seg_blocks blocks of one long interval). The
 // segment's blocks are cut into S = 32/r contiguous runs, one per group of r
@@ -518,15 +529,15 @@ __global__ void __launch_bounds__(256) k_spmv_rows_u(int64_t n, int64_t I, int32
 // interval, is about 1.35x slower on power-law rows; the warp's lanes then
 // stream 32 separate stretches of memory.)
 template <int R, int C, class T, int U, int DEC>
-__global__ void __launch_bounds__(256) k_spmv_segments(int64_t nseg, const Segment* __restrict__ segs,
-                                                       const int32_t* __restrict__ bcol, const uint8_t* __restrict__ bmask,
-                                                       const typename T::V* __restrict__ val,
-                                                       const typename T::X* __restrict__ x,
-                                                       typename T::A* __restrict__ partials) {
+__device__ __forceinline__ void segments_body(int64_t bid, int64_t nseg, const Segment* __restrict__ segs,
+                                              const int32_t* __restrict__ bcol, const uint8_t* __restrict__ bmask,
+                                              const typename T::V* __restrict__ val,
+                                              const typename T::X* __restrict__ x,
+                                              typename T::A* __restrict__ partials) {
   constexpr int MB = (R * C + 7) / 8;
   constexpr int S = kWarp / R;  // runs per segment
   const int lane = threadIdx.x & 31;
-  const int64_t seg = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t seg = (bid * blockDim.x + threadIdx.x) >> 5;
   if (seg >= nseg) return;  // whole warp leaves together
   const int slot = lane / R, i = lane % R;
   const Segment sg = segs[seg];
@@ -558,6 +569,39 @@ __global__ void __launch_bounds__(256) k_spmv_segments(int64_t nseg, const Segme
 #pragma unroll
   for (int d = kWarp / 2; d >= R; d >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, d);
   if (lane < R) partials[seg * R + lane] = acc;
+}
+
+template <int R, int C, class T, int U, int DEC>
+__global__ void __launch_bounds__(256) k_spmv_segments(int64_t nseg, const Segment* __restrict__ segs,
+                                                       const int32_t* __restrict__ bcol, const uint8_t* __restrict__ bmask,
+                                                       const typename T::V* __restrict__ val,
+                                                       const typename T::X* __restrict__ x,
+                                                       typename T::A* __restrict__ partials) {
+  segments_body<R, C, T, U, DEC>(blockIdx.x, nseg, segs, bcol, bmask, val, x, partials);
+}
+
+// Both kinds of work in one launch: thread blocks [0, seg_ctas) take the
+// segments of the long intervals, the rest the short intervals. One grid lets
+// the short-interval blocks fill the SMs that the segment blocks leave idle
+// (and the reverse) instead of each launch draining before the next starts;
+// the sums are those of the two separate kernels, bit for bit.
+template <int R, int C, class T, bool ACCUM, int U, bool ORDER, int DEC>
+__global__ void __launch_bounds__(256) k_spmv_rows_segs(int64_t seg_ctas, int64_t n, int64_t I, int32_t long_blocks,
+                                                        int64_t long_values, const int32_t* __restrict__ brp,
+                                                        const int32_t* __restrict__ bcol,
+                                                        const uint8_t* __restrict__ bmask,
+                                                        const typename T::V* __restrict__ val,
+                                                        const int64_t* __restrict__ valptr,
+                                                        const typename T::X* __restrict__ x,
+                                                        typename T::X* __restrict__ y,
+                                                        const int32_t* __restrict__ order, int64_t norder,
+                                                        int64_t nseg, const Segment* __restrict__ segs,
+                                                        typename T::A* __restrict__ partials) {
+  if ((int64_t)blockIdx.x < seg_ctas)
+    segments_body<R, C, T, 4, 1>(blockIdx.x, nseg, segs, bcol, bmask, val, x, partials);
+  else
+    rows_u_body<R, C, T, ACCUM, U, ORDER, DEC>((int64_t)blockIdx.x - seg_ctas, n, I, long_blocks, long_values, brp,
+                                               bcol, bmask, val, valptr, x, y, order, norder);
 }
 
 // Finishes the long intervals (list of first segments built at conversion;
@@ -648,6 +692,10 @@ cudaError_t launch_beta(const spc5_matrix* h, const void* xv, void* yv, bool acc
   const int threads = 256;
   const int v = h->variant;
   const bool ordered = ordered_variant(v) && h->norder > 0;
+  A* part = static_cast<A*>(partials);
+  // segments and short intervals in one launch (not for the plain variant 1)
+  const bool fused = h->I > 0 && h->nseg > 0 && v != 1;
+  const int64_t seg_ctas = (h->nseg * kWarp + threads - 1) / threads;
   if (h->I > 0) {
     const int64_t warps = ordered ? (h->norder + S - 1) / S : (h->I + S - 1) / S;
     const unsigned grid = (unsigned)((warps * kWarp + threads - 1) / threads);
@@ -657,8 +705,15 @@ cudaError_t launch_beta(const spc5_matrix* h, const void* xv, void* yv, bool acc
       kern<<<grid, threads, 0, s>>>(h->n, h->I, h->long_blocks, h->long_values, h->block_rowptr, h->block_colidx,
                                     h->block_masks, val, h->valptr, x, y, order, norder);
     };
-#define SPC5_GO(U, ORD, DEC) \
-  (acc ? go(k_spmv_rows_u<R, C, T, true, U, ORD, DEC>) : go(k_spmv_rows_u<R, C, T, false, U, ORD, DEC>))
+    auto go_both = [&](auto kern) {
+      kern<<<(unsigned)(seg_ctas + grid), threads, 0, s>>>(seg_ctas, h->n, h->I, h->long_blocks, h->long_values,
+                                                           h->block_rowptr, h->block_colidx, h->block_masks, val,
+                                                           h->valptr, x, y, order, norder, h->nseg, h->segs, part);
+    };
+#define SPC5_GO(U, ORD, DEC)                                                                                   \
+  (fused ? (acc ? go_both(k_spmv_rows_segs<R, C, T, true, U, ORD, DEC>)                                         \
+                : go_both(k_spmv_rows_segs<R, C, T, false, U, ORD, DEC>))                                       \
+         : (acc ? go(k_spmv_rows_u<R, C, T, true, U, ORD, DEC>) : go(k_spmv_rows_u<R, C, T, false, U, ORD, DEC>)))
     if (v == 1) {
       if (acc)
         k_spmv_rows<R, C, T, true><<<grid, threads, 0, s>>>(h->n, h->I, h->long_blocks, h->long_values, h->block_rowptr,
@@ -684,10 +739,9 @@ cudaError_t launch_beta(const spc5_matrix* h, const void* xv, void* yv, bool acc
 #undef SPC5_GO
   }
   if (h->nseg > 0) {
-    A* part = static_cast<A*>(partials);
-    const unsigned grid = (unsigned)((h->nseg * kWarp + threads - 1) / threads);
-    k_spmv_segments<R, C, T, 4, 1><<<grid, threads, 0, s>>>(h->nseg, h->segs, h->block_colidx, h->block_masks, val, x,
-                                                            part);
+    if (!fused)
+      k_spmv_segments<R, C, T, 4, 1><<<(unsigned)seg_ctas, threads, 0, s>>>(h->nseg, h->segs, h->block_colidx,
+                                                                            h->block_masks, val, x, part);
     const unsigned g2 = (unsigned)((h->nlong + 255) / 256);
     if (acc)
       k_spmv_fixup<R, T, true><<<g2, 256, 0, s>>>(h->n, h->nlong, h->seg_first, h->segs, part, y);
