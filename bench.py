@@ -40,6 +40,7 @@ FP64_PEAK_GFLOPS = 1250.0  # nominal GB300 float64 rate (2 FMA lanes/clk/SM x 15
 # short-interval kernel variants the tuner tries per shape: float64 keeps to the
 # flattened decodes (16's unrolled positions cost float64 pipe slots when empty)
 VARIANTS = {"f64": (5, 10, 13, 15), "f32": (5, 10, 13, 15, 16, 18)}
+GROUP_VARIANTS = (22,)  # beta(1,c) only: two lanes per row
 CG_INNER_VARIANT = 18  # decode of the float32 / bfloat16 inner CG handle (unrolled positions, two blocks a trip)
 
 
@@ -606,7 +607,7 @@ def main():
             for (r, c) in shapes:
                 M = spc5.convert(d.rowptr, d.colidx, d.values, A.n, A.m, r, c)
                 tv = {}
-                for v in VARIANTS["f64" if dtype == torch.float64 else "f32"]:
+                for v in VARIANTS["f64" if dtype == torch.float64 else "f32"] + (GROUP_VARIANTS if r == 1 else ()):
                     M.set_variant(v)
                     tv[v] = time_call(lambda: M.spmv(xd, yd), 5)
                 v = min(tv, key=tv.get)

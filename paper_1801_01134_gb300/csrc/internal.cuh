@@ -22,8 +22,10 @@ constexpr int kOrderWindow = 1024;  // rows per sorting window of the work order
 
 // short-interval kernel variants (spc5_opts.variant)
 inline bool valid_variant(int v) {
-  return v == 0 || v == 1 || v == 3 || v == 5 || v == 9 || v == 10 || (v >= 12 && v <= 19);
+  return v == 0 || v == 1 || v == 3 || v == 5 || v == 9 || v == 10 || (v >= 12 && v <= 19) || v == 22;
 }
+// variants that need r = 1 (two lanes per row)
+inline bool r1_variant(int v) { return v == 22; }
 // variants that take intervals in the sorted work order
 inline bool ordered_variant(int v) { return v == 9 || v == 10 || v == 13 || v == 15 || v == 17 || v == 19; }
 

@@ -517,6 +517,115 @@ __global__ void __launch_bounds__(256) k_spmv_rows_u(int64_t n, int64_t I, int32
                                              x, y, order, norder);
 }
 
+// ---------------------------------------- two lanes per row (beta(1,c))
+// Variant 22, r = 1: the two lanes of a pair share a short row and lane g
+// takes the row's stored values of rank g, g + 2, ... (rank = position among
+// the row's values). Its values are then every other one, so the pair reads
+// them as one contiguous stretch and each lane makes half the row's
+// multiply-adds (within one of its partner's), as in a two-lane CSR kernel,
+// while the column indices are still read once per block. The bits of a mask
+// with even (odd) rank inside the block are those where the inclusive prefix
+// parity of the mask is 1 (0). (Measured on GB300: float64 FEM beta(1,8)
+// 534 -> 640 GFLOP/s against the one-lane flattened decode, uniform
+// 286 -> 309; four lanes per row, with a two-plane prefix count, was slower
+// on every test matrix, and 1 or 4 values per trip slower than 2.)
+template <int G, int NB>
+__device__ __forceinline__ uint32_t rank_class_bits(uint32_t m, int cls) {
+  static_assert(G == 2, "two lanes per row");
+  // inclusive prefix parity of the NB-bit mask
+  uint32_t p = m;
+#pragma unroll
+  for (int s = 1; s < NB; s <<= 1) p ^= p << s;
+  // a set bit of rank j has inclusive count j + 1
+  return m & (cls == 0 ? p : ~p);
+}
+
+template <int C, class T, bool ACCUM, int G, int U>
+__device__ __forceinline__ void rows_g_body(int64_t bid, int64_t n, int64_t I, int32_t long_blocks,
+                                            int64_t long_values, const int32_t* __restrict__ brp,
+                                            const int32_t* __restrict__ bcol, const uint8_t* __restrict__ bmask,
+                                            const typename T::V* __restrict__ val,
+                                            const int64_t* __restrict__ valptr, const typename T::X* __restrict__ x,
+                                            typename T::X* __restrict__ y) {
+  constexpr int MB = (C + 7) / 8;
+  constexpr int S = kWarp / G;  // rows per warp
+  using A = typename T::A;
+  const int lane = threadIdx.x & 31;
+  const int g = lane & (G - 1);
+  const int64_t warp = (bid * blockDim.x + threadIdx.x) >> 5;
+  if (warp * S >= I) return;  // whole warp
+  const int64_t it = warp * S + lane / G;
+  int32_t b = 0, bend = 0;
+  int64_t vp = 0;
+  bool have = it < I;
+  if (have) {
+    b = __ldg(brp + it);
+    bend = __ldg(brp + it + 1);
+    const int64_t v0 = __ldg(valptr + it);
+    if (bend - b > long_blocks || __ldg(valptr + it + 1) - v0 > long_values) have = false;  // the segment path's
+    vp = v0 + g;
+  }
+  if (!have) bend = b;  // no work, but the group still meets at the shuffle below
+  uint32_t sel = 0, nm = b < bend ? load_mask<MB>(bmask, b).w[0] : 0u;
+  int32_t col0 = 0, ncol = b < bend ? __ldg(bcol + b) : 0;
+  int before = 0;  // values of the row in the blocks already entered
+  A acc = 0;
+  for (;;) {
+    int64_t vi[U];
+    int32_t xi[U];
+    bool h[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      while (sel == 0 && b < bend) {
+        const uint32_t m = nm;
+        col0 = ncol;
+        if (b + 1 < bend) {
+          nm = load_mask<MB>(bmask, b + 1).w[0];
+          ncol = __ldg(bcol + b + 1);
+        }
+        sel = rank_class_bits<G, C>(m, (g - before) & (G - 1));
+        before += __popc(m);
+        ++b;
+      }
+      h[u] = sel != 0;
+      const int k = __ffs(sel) - 1;
+      sel &= sel - 1;
+      vi[u] = vp;
+      vp += h[u] ? G : 0;
+      xi[u] = col0 + k;
+    }
+    if (!h[0]) break;
+    A v[U], xx[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      v[u] = h[u] ? T::val(val, vi[u]) : A(0);
+      xx[u] = h[u] ? T::xv(x, xi[u]) : A(0);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (h[u]) acc = fmadd<T>(v[u], xx[u], acc);
+  }
+#pragma unroll
+  for (int d = G / 2; d >= 1; d >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, d, G);
+  if (have && g == 0 && it < n) {
+    if (ACCUM)
+      y[it] = y[it] + acc;
+    else
+      y[it] = acc;
+  }
+}
+
+template <int C, class T, bool ACCUM, int G, int U>
+__global__ void __launch_bounds__(256) k_spmv_rows_g(int64_t n, int64_t I, int32_t long_blocks, int64_t long_values,
+                                                     const int32_t* __restrict__ brp, const int32_t* __restrict__ bcol,
+                                                     const uint8_t* __restrict__ bmask,
+                                                     const typename T::V* __restrict__ val,
+                                                     const int64_t* __restrict__ valptr,
+                                                     const typename T::X* __restrict__ x,
+                                                     typename T::X* __restrict__ y) {
+  rows_g_body<C, T, ACCUM, G, U>(blockIdx.x, n, I, long_blocks, long_values, brp, bcol, bmask, val, valptr, x, y);
+}
+
 // -------------------------------------------------------- long intervals
 // A warp per segment (at most seg_blocks blocks of one long interval). The
 // segment's blocks are cut into S = 32/r contiguous runs, one per group of r
@@ -585,7 +694,7 @@ __global__ void __launch_bounds__(256) k_spmv_segments(int64_t nseg, const Segme
 // the short-interval blocks fill the SMs that the segment blocks leave idle
 // (and the reverse) instead of each launch draining before the next starts;
 // the sums are those of the two separate kernels, bit for bit.
-template <int R, int C, class T, bool ACCUM, int U, bool ORDER, int DEC>
+template <int R, int C, class T, bool ACCUM, int U, bool ORDER, int DEC, int G = 1>
 __global__ void __launch_bounds__(256) k_spmv_rows_segs(int64_t seg_ctas, int64_t n, int64_t I, int32_t long_blocks,
                                                         int64_t long_values, const int32_t* __restrict__ brp,
                                                         const int32_t* __restrict__ bcol,
@@ -599,9 +708,12 @@ __global__ void __launch_bounds__(256) k_spmv_rows_segs(int64_t seg_ctas, int64_
                                                         typename T::A* __restrict__ partials) {
   if ((int64_t)blockIdx.x < seg_ctas)
     segments_body<R, C, T, 4, 1>(blockIdx.x, nseg, segs, bcol, bmask, val, x, partials);
-  else
+  else if constexpr (G == 1)
     rows_u_body<R, C, T, ACCUM, U, ORDER, DEC>((int64_t)blockIdx.x - seg_ctas, n, I, long_blocks, long_values, brp,
                                                bcol, bmask, val, valptr, x, y, order, norder);
+  else
+    rows_g_body<C, T, ACCUM, G, U>((int64_t)blockIdx.x - seg_ctas, n, I, long_blocks, long_values, brp, bcol, bmask,
+                                   val, valptr, x, y);
 }
 
 // Finishes the long intervals (list of first segments built at conversion;
@@ -677,7 +789,8 @@ __global__ void __launch_bounds__(256) k_spmv_fixup(int64_t n, int64_t nlong, co
 // 3 natural U=4; 9/10 sorted order U=2/U=4; 12/14 natural order, mask
 // windows, U=4/U=2; 13/15 sorted order, mask windows, U=4/U=2; 16/17
 // natural / sorted order, bit positions unrolled (row_sum_e); 18/19 the same
-// two blocks per trip (row_sum_e2). (Measured:
+// two blocks per trip (row_sum_e2); 22 (r = 1) two lanes per row taking
+// alternate stored values (rows_g_body). (Measured:
 // 8 nonzeros per trip is slower than 2 or 4 on every test matrix.)
 // `partials` is the segment scratch (n_segments * r accumulators).
 template <int R, int C, class T>
@@ -696,7 +809,30 @@ cudaError_t launch_beta(const spc5_matrix* h, const void* xv, void* yv, bool acc
   // segments and short intervals in one launch (not for the plain variant 1)
   const bool fused = h->I > 0 && h->nseg > 0 && v != 1;
   const int64_t seg_ctas = (h->nseg * kWarp + threads - 1) / threads;
-  if (h->I > 0) {
+  bool rows_done = false;  // the short intervals already launched (G lanes per row)
+  if constexpr (R == 1) {
+    if (v == 22 && h->I > 0) {
+      constexpr int U = 2;
+      const int64_t warps = (h->I + kWarp / 2 - 1) / (kWarp / 2);
+      const unsigned grid = (unsigned)((warps * kWarp + threads - 1) / threads);
+      auto go = [&](auto kern) {
+        kern<<<grid, threads, 0, s>>>(h->n, h->I, h->long_blocks, h->long_values, h->block_rowptr, h->block_colidx,
+                                      h->block_masks, val, h->valptr, x, y);
+      };
+      auto go_both = [&](auto kern) {
+        kern<<<(unsigned)(seg_ctas + grid), threads, 0, s>>>(seg_ctas, h->n, h->I, h->long_blocks, h->long_values,
+                                                             h->block_rowptr, h->block_colidx, h->block_masks, val,
+                                                             h->valptr, x, y, nullptr, 0, h->nseg, h->segs, part);
+      };
+      if (fused)
+        acc ? go_both(k_spmv_rows_segs<1, C, T, true, U, false, 0, 2>)
+            : go_both(k_spmv_rows_segs<1, C, T, false, U, false, 0, 2>);
+      else
+        acc ? go(k_spmv_rows_g<C, T, true, 2, U>) : go(k_spmv_rows_g<C, T, false, 2, U>);
+      rows_done = true;
+    }
+  }
+  if (h->I > 0 && !rows_done) {
     const int64_t warps = ordered ? (h->norder + S - 1) / S : (h->I + S - 1) / S;
     const unsigned grid = (unsigned)((warps * kWarp + threads - 1) / threads);
     const int32_t* order = ordered ? h->order : nullptr;

@@ -116,6 +116,71 @@ def test_spmv_variants(cuda_device, variant, name, r, c):
     M.destroy()
 
 
+GROUP_VARIANTS = [22]  # beta(1,c): two lanes per row, alternate stored values
+
+
+@pytest.mark.parametrize("variant", GROUP_VARIANTS)
+@pytest.mark.parametrize("name", list(MATS))
+@pytest.mark.parametrize("c", [4, 8, 16])
+def test_spmv_group_variants(cuda_device, variant, name, c):
+    A = get(name)
+    x = inputs.vec_uniform(A.m, seed=0)
+    y_ref, absy = oracle.csr_spmv_dot2(A, x)
+    d = dev_csr(A)
+    xd = torch.from_numpy(x).cuda()
+    # default thresholds, and most rows on the segment path
+    for lb, sb in [(0, 0), (1, 3)]:
+        M = spc5.convert(d.rowptr, d.colidx, d.values, A.n, A.m, 1, c, variant=variant, long_blocks=lb, seg_blocks=sb)
+        buf, y = guarded(A.n, torch.float64)
+        M.spmv(xd, y)
+        check64(y.cpu().numpy(), y_ref, absy)
+        assert torch.isnan(buf[A.n:]).all(), "wrote past the end of y"
+        assert torch.equal(M.spmv(xd), y)  # a fixed order
+        y0 = inputs.vec_uniform(A.n, seed=1)
+        yd = torch.from_numpy(y0.copy()).cuda()
+        M.spmv_acc(xd, yd)
+        assert np.all(np.abs(yd.cpu().numpy() - (y0 + y_ref)) <= TOL64 * (absy + np.abs(y0)) + 1e-300)
+        M.destroy()
+
+
+def test_group_variants_low_precision_and_limits(cuda_device):
+    # dyadic Laplacian: exact partial sums, so any order gives the oracle's bits
+    A = get("lap128")
+    x = inputs.vec_dyadic(A.m, seed=0, bits=20)
+    y_ref = oracle.csr_spmv(A, x)
+    for vdt, xdt in [(torch.float64, torch.float64), (torch.float32, torch.float32), (torch.bfloat16, torch.float32)]:
+        d = dev_csr(A, vdt)
+        for v in GROUP_VARIANTS:
+            M = spc5.convert(d.rowptr, d.colidx, d.values, A.n, A.m, 1, 8, variant=v)
+            y = M.spmv(torch.from_numpy(x).to(xdt).cuda()).double().cpu().numpy()
+            assert np.array_equal(y, y_ref), (vdt, v)
+            M.destroy()
+    # float32 storage on a ragged matrix: the worst-case float32 summation bound
+    B = get("rmat11")
+    rv = oracle.round_f32(B.values)
+    xr = oracle.round_f32(inputs.vec_uniform(B.m, seed=0))
+    y_ref, absy = oracle.csr_spmv_dot2(inputs.CSR(B.n, B.m, B.rowptr, B.colidx, rv), xr)
+    vals = torch.from_numpy(rv).float().cuda()
+    L = np.diff(B.rowptr).astype(np.float64)
+    u = 2.0**-24
+    for v in GROUP_VARIANTS:
+        M = spc5.convert(torch.from_numpy(B.rowptr).cuda(), torch.from_numpy(B.colidx).cuda(), vals, B.n, B.m, 1, 4,
+                         variant=v)
+        y = M.spmv(torch.from_numpy(xr).float().cuda()).double().cpu().numpy()
+        assert np.all(np.abs(y - y_ref) <= (L + 1) * u / (1 - (L + 1) * u) * absy + 1e-45)
+        M.destroy()
+    # r > 1: refused at conversion and when switching
+    d = dev_csr(B)
+    with pytest.raises(spc5.Spc5Error) as ei:
+        spc5.convert(d.rowptr, d.colidx, d.values, B.n, B.m, 2, 4, variant=22)
+    assert ei.value.status == spc5.EUNSUPPORTED
+    M = spc5.convert(d.rowptr, d.colidx, d.values, B.n, B.m, 4, 8)
+    with pytest.raises(spc5.Spc5Error) as ei:
+        M.set_variant(22)
+    assert ei.value.status == spc5.EUNSUPPORTED
+    M.destroy()
+
+
 @pytest.mark.parametrize("name", ["st27_ragged", "rmat11", "fem", "uniform"])
 @pytest.mark.parametrize("r,c", spc5.SHAPES)
 def test_variants_sum_in_the_same_order(cuda_device, name, r, c):
@@ -154,9 +219,17 @@ def test_autotune_keeps_a_candidate_and_the_result(cuda_device, dtype):
     ref = M.spmv(xd).clone()
     y = torch.empty_like(ref)
     v, ms = M.autotune(xd, y, reps=3)
-    cands = (5, 10, 13, 15) if dtype == torch.float64 else (5, 10, 13, 15, 16, 18)
+    cands = ((5, 10, 13, 15) if dtype == torch.float64 else (5, 10, 13, 15, 16, 18)) + (22,)
     assert v in cands and ms > 0
-    assert torch.equal(M.spmv(xd), ref)  # every variant adds in the same order
+    got = M.spmv(xd)
+    if v < 20:
+        assert torch.equal(got, ref)  # variants 0-19 add in the same order
+    else:  # two lanes per row add in their own fixed order
+        Ar = inputs.CSR(A.n, A.m, A.rowptr, A.colidx, vals)
+        y_ref, absy = oracle.csr_spmv_dot2(Ar, xd.double().cpu().numpy())
+        L = np.diff(A.rowptr).astype(np.float64)
+        tol = TOL64 if dtype == torch.float64 else (L + 1) * 2.0**-23
+        assert np.all(np.abs(got.double().cpu().numpy() - y_ref) <= tol * absy + 1e-45)
     M.destroy()
 
 
