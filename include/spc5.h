@@ -365,8 +365,10 @@ spc5_status spc5_features(int64_t n, int64_t m, int64_t nnz, const int64_t* rowp
 /*
  * spc5_time_formats - the timing recorder: converts the CSR to each of the
  * twelve shapes and times `reps` SpMVs of each (after one untimed product),
- * writing the median milliseconds to ms_out[12] (host). x_d / y_d: work
- * vectors of the vector type (m and n entries). Synchronises `stream`.
+ * writing the median milliseconds to ms_out[12] (host); for r = 1 the
+ * shape's time is the faster of its default kernel and variant 22 (two
+ * lanes per row). x_d / y_d: work vectors of the vector type (m and n
+ * entries). Synchronises `stream`.
  */
 spc5_status spc5_time_formats(int64_t n, int64_t m, int64_t nnz, const int64_t* rowptr_d, const int32_t* colidx_d,
                               const void* values_d, spc5_dtype vt, const void* x_d, void* y_d, int reps,
