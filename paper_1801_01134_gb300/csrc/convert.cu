@@ -727,6 +727,66 @@ void launch_order_key(int c, const spc5_matrix* h, int32_t* key, cudaStream_t s)
   }
 }
 
+// Sorting of the work order on the device, one thread block per window of at
+// most kSortWindow intervals: each short interval becomes the 64-bit word
+// (INT32_MAX - key) << 32 | position, so that an ascending bitonic sort in
+// shared memory orders by key descending and keeps the interval order among
+// equal keys (the stable sort of the host path); long intervals (key -1) and
+// the padding sort last and are dropped.
+constexpr int kSortWindow = 4096;
+
+__global__ void k_order_count(int64_t I, int64_t wiv, const int32_t* __restrict__ key, int32_t* __restrict__ cnt) {
+  const int64_t w0 = (int64_t)blockIdx.x * wiv;
+  const int64_t w1 = w0 + wiv < I ? w0 + wiv : I;
+  int c = 0;
+  for (int64_t it = w0 + threadIdx.x; it < w1; it += blockDim.x) c += key[it] >= 0 ? 1 : 0;
+  c = __reduce_add_sync(0xffffffffu, (unsigned)c);
+  __shared__ int part[32];
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int t = 0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += part[q];
+    cnt[blockIdx.x] = t;
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_order_sort(int64_t I, int64_t wiv, int P, const int32_t* __restrict__ key,
+                                                     const int32_t* __restrict__ off, int32_t* __restrict__ order) {
+  extern __shared__ unsigned long long sk[];  // P words, P = power of two >= wiv
+  const int64_t w0 = (int64_t)blockIdx.x * wiv;
+  const int64_t w1 = w0 + wiv < I ? w0 + wiv : I;
+  const int nw = (int)(w1 - w0);
+  for (int q = threadIdx.x; q < P; q += blockDim.x) {
+    unsigned long long v = ~0ull;
+    if (q < nw) {
+      const int32_t k = key[w0 + q];
+      if (k >= 0) v = ((unsigned long long)(uint32_t)(INT32_MAX - k) << 32) | (unsigned)q;
+    }
+    sk[q] = v;
+  }
+  __syncthreads();
+  for (int size = 2; size <= P; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int q = threadIdx.x; q < P; q += blockDim.x) {
+        const int p = q ^ stride;
+        if (p > q) {
+          const bool up = (q & size) == 0;
+          const unsigned long long a = sk[q], b = sk[p];
+          if ((a > b) == up) {
+            sk[q] = b;
+            sk[p] = a;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  const int32_t base = off[blockIdx.x];
+  const int32_t valid = off[blockIdx.x + 1] - base;
+  for (int q = threadIdx.x; q < valid; q += blockDim.x) order[base + q] = (int32_t)(w0 + (int64_t)(uint32_t)sk[q]);
+}
+
 }  // namespace
 
 // Work order of the lane-per-row kernel (variants 9, 10, 13, 15): the short
@@ -750,6 +810,42 @@ spc5_status build_order(spc5_matrix* h, cudaStream_t s) {
     case 4: launch_order_key<4>(h->c, h, (int32_t*)keyd.p, s); break;
     default: launch_order_key<8>(h->c, h, (int32_t*)keyd.p, s); break;
   }
+  const int64_t wiv_d = h->order_window > 0 ? (h->order_window + h->r - 1) / h->r : I;
+  if (wiv_d <= kSortWindow) {
+    // windows small enough for one thread block each: sort on the device
+    const int64_t nwin = (I + wiv_d - 1) / wiv_d;
+    int P = 1;
+    while (P < wiv_d) P <<= 1;
+    DeviceBuf cnt, off;
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cnt.alloc(sizeof(int32_t) * (size_t)nwin, s);
+    if (e == cudaSuccess) e = off.alloc(sizeof(int32_t) * (size_t)(nwin + 1), s);
+    if (e != cudaSuccess) return cuda_fail(e, "work order: scratch");
+    k_order_count<<<(unsigned)nwin, 256, 0, s>>>(I, wiv_d, (const int32_t*)keyd.p, (int32_t*)cnt.p);
+    int64_t total = 0;
+    spc5_status st = scan_counts((const int32_t*)cnt.p, nwin, (int32_t*)off.p, &total, s);
+    if (st != SPC5_OK) return st;
+    int32_t* d = nullptr;
+    if (total > 0) {
+      e = alloc_padded((void**)&d, sizeof(int32_t) * (size_t)total, s);
+      if (e != cudaSuccess) return cuda_fail(e, "work order: allocation");
+      const size_t smem = sizeof(unsigned long long) * (size_t)P;
+      if (smem > 48 * 1024) e = cudaFuncSetAttribute(k_order_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e == cudaSuccess) {
+        k_order_sort<<<(unsigned)nwin, 1024, smem, s>>>(I, wiv_d, P, (const int32_t*)keyd.p, (const int32_t*)off.p, d);
+        e = cudaGetLastError();
+      }
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) {
+        cudaFree(d);
+        return cuda_fail(e, "work order: sort");
+      }
+    }
+    h->order = d;
+    h->norder = total;
+    return SPC5_OK;
+  }
+  // larger windows (or all intervals together): stable sort on the host
   std::vector<int32_t> key((size_t)I);
   e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaMemcpyAsync(key.data(), keyd.p, sizeof(int32_t) * (size_t)I, cudaMemcpyDeviceToHost, s);

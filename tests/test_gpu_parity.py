@@ -209,6 +209,25 @@ def test_variants_sum_in_the_same_order(cuda_device, name, r, c):
         M.destroy()
 
 
+@pytest.mark.parametrize("r,c", [(1, 4), (2, 8), (8, 16)])
+def test_sorted_order_device_and_host_sorts(cuda_device, r, c):
+    # windows of up to 4096 intervals are sorted on the device, larger ones
+    # (or all intervals together) on the host; every order must cover each
+    # short interval once, so y is bit for bit that of the natural order
+    A = inputs.rmat(14, seed=7)  # 16,384 rows, power-law lengths
+    x = torch.from_numpy(inputs.vec_uniform(A.m, seed=0)).cuda()
+    d = dev_csr(A)
+    M = spc5.convert(d.rowptr, d.colidx, d.values, A.n, A.m, r, c, variant=5)
+    ref = M.spmv(x).clone()
+    M.destroy()
+    I = (A.n + r - 1) // r
+    for ow in (1, 33, 1024, 4096 * r, 4096 * r + r, -1):
+        for v in (10, 13):
+            M = spc5.convert(d.rowptr, d.colidx, d.values, A.n, A.m, r, c, variant=v, order_window=ow)
+            assert torch.equal(M.spmv(x), ref), (ow, v, I)
+            M.destroy()
+
+
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
 def test_autotune_keeps_a_candidate_and_the_result(cuda_device, dtype):
     A = get("rmat11")
