@@ -8,7 +8,7 @@ inputs. This module records SpMV timings of every block shape over generated
 matrices with the library's own timing recorder (spc5_time_formats), trains
 the library's MLP on the GPU (spc5_mlp_train) to score the shapes from the 16
 features (spc5_features), fits the polynomial predictor (spc5_poly_fit) as the
-fallback and judge, and reports the regret t(chosen) / t(best) - 1 of both on
+fallback and yardstick, and reports the regret t(chosen) / t(best) - 1 of both on
 held-out matrices. Timing, feature counting, MLP training and inference and
 the polynomial fit run in libspc5; this module drives them and computes the
 input standardisation and the regret statistics.
