@@ -70,7 +70,8 @@ def mlp_inputs(F: np.ndarray, mean=None, scale=None):
     if mean is None:
         mean = L.mean(axis=0)
         scale = L.std(axis=0)
-        scale[scale == 0] = 1.0
+        # a constant feature (its spread only rounding noise) keeps a unit scale
+        scale[scale <= 1e-9 * np.maximum(np.abs(mean), 1.0)] = 1.0
     return ((L - mean) / scale).astype(np.float32), mean.astype(np.float32), scale.astype(np.float32)
 
 

@@ -36,3 +36,42 @@ def test_poly_fit_rejects_bad_arguments():
     with pytest.raises(spc5.Spc5Error) as ei:
         spc5.poly_fit(avg, perf, 7)  # more coefficients than the library fits
     assert ei.value.status == spc5.EINVAL
+
+
+def test_selector_regret_and_targets():
+    from paper_1801_01134_gb300 import selector
+
+    rng = np.random.default_rng(3)
+    T = rng.uniform(0.1, 2.0, (50, 12))
+    best = T.argmin(axis=1)
+    assert np.all(selector.regret(T, best) == 0.0)
+    other = (best + 1) % 12
+    r = selector.regret(T, other)
+    assert np.allclose(r, T[np.arange(50), other] / T[np.arange(50), best] - 1.0) and np.all(r > 0)
+    # training targets: log times centred per matrix (same ordering, rows sum to zero)
+    Y = selector.centred_log(T)
+    assert np.allclose(Y.sum(axis=1), 0.0) and np.array_equal(Y.argmin(axis=1), best)
+
+
+def test_selector_input_transform_is_the_library_one():
+    from paper_1801_01134_gb300 import selector
+
+    rng = np.random.default_rng(4)
+    F = rng.uniform(0.0, 50.0, (200, 16))
+    F[:, 5] = 3.0  # a constant feature keeps a unit scale
+    X, mean, scale = selector.mlp_inputs(F)
+    assert np.allclose(X.mean(axis=0)[[0, 1, 2]], 0.0, atol=1e-5) and scale[5] == 1.0
+    X2, _, _ = selector.mlp_inputs(F, mean, scale)  # the stored transform reapplied
+    assert np.array_equal(X, X2)
+    assert np.allclose(X2, (np.log1p(F) - mean.astype(np.float64)) / scale.astype(np.float64), atol=1e-5)
+
+
+def test_selector_poly_choices_match_the_oracle_rule():
+    from paper_1801_01134_gb300 import selector
+
+    rng = np.random.default_rng(6)
+    coef = rng.standard_normal((12, 3))
+    F = rng.uniform(1.0, 16.0, (40, 16))
+    got = selector.poly_choices(coef, F)
+    want = [osel.poly_select(list(coef), f) for f in F]
+    assert list(got) == want
