@@ -61,8 +61,8 @@ def test_selector_input_transform_is_the_library_one():
     F[:, 5] = 3.0  # a constant feature keeps a unit scale
     X, mean, scale = selector.mlp_inputs(F)
     assert np.allclose(X.mean(axis=0)[[0, 1, 2]], 0.0, atol=1e-5) and scale[5] == 1.0
-    X2, _, _ = selector.mlp_inputs(F, mean, scale)  # the stored transform reapplied
-    assert np.array_equal(X, X2)
+    X2, _, _ = selector.mlp_inputs(F, mean, scale)  # the stored (float32) transform reapplied
+    assert np.allclose(X, X2, atol=1e-5)
     assert np.allclose(X2, (np.log1p(F) - mean.astype(np.float64)) / scale.astype(np.float64), atol=1e-5)
 
 
