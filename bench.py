@@ -247,7 +247,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": round(val, 3), "unit": "GFLOP/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "suite4: " + ", ".join(n for n, _ in mats), "format": "CSR (CPU oracle)",
+        "config": {"workload": "suite4 float64: " + ", ".join(n for n, _ in mats), "format": "CSR (CPU oracle)",
                    "parallelism": "host OpenMP"},
         "cpu_baseline": {"value": round(val, 3), "unit": "GFLOP/s", "cores": threads, "kind": "oracle",
                          "sample": f"full workload, {args.steps} steps of 4 CSR SpMVs, float64, {threads} threads"},
