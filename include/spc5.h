@@ -241,6 +241,22 @@ spc5_status spc5_csr_spmv(int64_t n, int64_t m, int64_t nnz, const int64_t* rowp
                           spc5_stream_t stream);
 
 /*
+ * spc5_partition - the static partition of the row intervals among `nparts`
+ * workers (section "Parallelization"): walking the intervals in order, the
+ * next interval joins part t while that does not move the part's block prefix
+ * farther from its target (t+1) * N_b / nparts, so every boundary lands on the
+ * block prefix nearest to its target and empty intervals are absorbed; the
+ * last part ends at the last interval. The distances are compared exactly (in
+ * integers scaled by nparts). Host function, no device work.
+ *   block_rowptr  HOST int32[nintervals+1], a block prefix (rising from 0),
+ *                 e.g. a host copy of spc5_arrays.block_rowptr_d.
+ *   bounds_out    HOST int64[nparts+1]: part t owns intervals
+ *                 [bounds_out[t], bounds_out[t+1]).
+ * SPC5_EINVAL for NULL pointers, nintervals < 0 or nparts < 1.
+ */
+spc5_status spc5_partition(const int32_t* block_rowptr, int64_t nintervals, int nparts, int64_t* bounds_out);
+
+/*
  * spc5_copy - dst = src for `bytes` bytes (a multiple of 16, both pointers
  * 16-byte aligned): the streaming-copy kernel that measures the achievable
  * HBM bandwidth next to the SpMV kernels.

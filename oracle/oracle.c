@@ -275,15 +275,19 @@ void or_beta_spmv_alg1(int64_t n, int r, int c, const int32_t* block_rowptr, con
  * target (t+1)*Nb/T, i.e. while |target - prefix[row+1]| <= |target -
  * prefix[row]|, so each boundary lands on the prefix nearest to its target
  * (empty intervals are absorbed). The comparison in the paper's text reads
- * reversed; this is the reading that balances the blocks. bounds receives
+ * reversed; this is the reading that balances the blocks. The distances are
+ * compared exactly, scaled by T: |(t+1)*Nb - T*prefix|. bounds receives
  * nthreads+1 interval indices. */
+static int64_t or_absdiff(int64_t a, int64_t b) { return a > b ? a - b : b - a; }
+
 void or_partition(int64_t nintervals, const int32_t* block_rowptr, int nthreads, int64_t* bounds) {
-  double per = (double)block_rowptr[nintervals] / (double)nthreads;
+  const int64_t nb = block_rowptr[nintervals];
   int64_t row = 0;
   bounds[0] = 0;
   for (int t = 0; t < nthreads; ++t) {
-    double target = (t + 1) * per;
-    while (row < nintervals && fabs(target - (double)block_rowptr[row + 1]) <= fabs(target - (double)block_rowptr[row]))
+    const int64_t target = (int64_t)(t + 1) * nb; /* scaled by nthreads */
+    while (row < nintervals && or_absdiff(target, (int64_t)nthreads * block_rowptr[row + 1]) <=
+                                   or_absdiff(target, (int64_t)nthreads * block_rowptr[row]))
       ++row;
     if (t == nthreads - 1) row = nintervals;
     bounds[t + 1] = row;

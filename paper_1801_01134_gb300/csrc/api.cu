@@ -185,6 +185,30 @@ spc5_status spc5_csr_spmv(int64_t n, int64_t m, int64_t nnz, const int64_t* rowp
   return SPC5_OK;
 }
 
+spc5_status spc5_partition(const int32_t* block_rowptr, int64_t nintervals, int nparts, int64_t* bounds_out) {
+  if (!block_rowptr || !bounds_out) return fail(SPC5_EINVAL, "partition: NULL array");
+  if (nintervals < 0 || nparts < 1) return fail(SPC5_EINVAL, "partition: nintervals < 0 or nparts < 1");
+  // distance of a block prefix p to part t's target, scaled by nparts:
+  // |(t + 1) * N_b - nparts * p| (exact in 64 bits: both terms are below 2^62)
+  const int64_t total = block_rowptr[nintervals];
+  auto dist = [&](int64_t scaled_target, int64_t i) {
+    const int64_t d = scaled_target - (int64_t)nparts * block_rowptr[i];
+    return d < 0 ? -d : d;
+  };
+  int64_t at = 0;
+  bounds_out[0] = 0;
+  for (int t = 0; t < nparts; ++t) {
+    const int64_t tgt = (int64_t)(t + 1) * total;
+    if (t + 1 == nparts) {
+      at = nintervals;
+    } else {
+      while (at < nintervals && dist(tgt, at + 1) <= dist(tgt, at)) ++at;
+    }
+    bounds_out[t + 1] = at;
+  }
+  return SPC5_OK;
+}
+
 spc5_status spc5_copy(const void* src_d, void* dst_d, int64_t bytes, spc5_stream_t stream) {
   if (bytes < 0 || (bytes % 16) != 0) return fail(SPC5_EINVAL, "copy: bytes must be a non-negative multiple of 16");
   if (bytes > 0 && (!src_d || !dst_d)) return fail(SPC5_EINVAL, "copy: NULL pointer");

@@ -115,13 +115,14 @@ def load(build_if_missing: bool = False):
     lib.spc5_mlp_grad.argtypes = [vp, vp, vp, vp, i32, vp, vp, vp]
     lib.spc5_mlp_infer.argtypes = [vp, vp, i32, vp, vp]
     lib.spc5_poly_fit.argtypes = [vp, vp, i32, i32, vp]
+    lib.spc5_partition.argtypes = [vp, i64, i32, vp]
     lib.spc5_select.argtypes = [i64, i64, i64, vp, vp, vp, i32, i32, ctypes.POINTER(Selector), vp, vp, vp, vp]
     for f in (lib.spc5_convert, lib.spc5_assemble, lib.spc5_autotune, lib.spc5_spmv, lib.spc5_spmv_acc, lib.spc5_export, lib.spc5_destroy, lib.spc5_set_variant,
               lib.spc5_count_blocks, lib.spc5_csr_spmv, lib.spc5_copy, lib.spc5_fma_rate, lib.spc5_fma_rate_lanes,
               lib.spc5_spmv_noalloc, lib.spc5_cg, lib.spc5_spmm, lib.spc5_features,
               lib.spc5_time_formats, lib.spc5_mlp_train, lib.spc5_mlp_grad, lib.spc5_mlp_infer, lib.spc5_poly_fit,
               lib.spc5_select, lib.spc5_batch_create, lib.spc5_batch_spmv, lib.spc5_batch_spmv_direct,
-              lib.spc5_batch_destroy):
+              lib.spc5_batch_destroy, lib.spc5_partition):
         f.restype = st
     _lib = lib
     return lib
@@ -389,6 +390,14 @@ def mlp_infer(params: torch.Tensor, X: torch.Tensor, stream=None) -> torch.Tenso
     out = torch.empty(X.shape[0], NFORMATS, dtype=torch.float32, device=params.device)
     _check(load().spc5_mlp_infer(_ptr(params), _ptr(X), X.shape[0], _ptr(out), _stream_ptr(stream)), "spc5_mlp_infer")
     return out
+
+
+def partition(block_rowptr: np.ndarray, nparts: int) -> np.ndarray:
+    """Interval bounds (int64[nparts + 1]) of the paper's block-balanced static partition."""
+    brp = np.ascontiguousarray(block_rowptr, dtype=np.int32)
+    bounds = np.zeros(nparts + 1 if nparts >= 1 else 1, dtype=np.int64)
+    _check(load().spc5_partition(brp.ctypes.data, brp.shape[0] - 1, nparts, bounds.ctypes.data), "spc5_partition")
+    return bounds
 
 
 def poly_fit(avg: np.ndarray, perf: np.ndarray, degree: int) -> np.ndarray:

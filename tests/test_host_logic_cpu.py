@@ -75,3 +75,44 @@ def test_selector_poly_choices_match_the_oracle_rule():
     got = selector.poly_choices(coef, F)
     want = [osel.poly_select(list(coef), f) for f in F]
     assert list(got) == want
+
+
+def _partition_brute(brp, T):
+    """Each boundary by exhaustion: from the previous boundary, the last interval
+    index whose block prefix is nearest (exactly, in integers) to (t+1)*Nb/T."""
+    brp = [int(v) for v in brp]
+    I, nb = len(brp) - 1, brp[-1]
+    b = [0]
+    for t in range(T):
+        if t == T - 1:
+            b.append(I)
+            continue
+        d = [abs((t + 1) * nb - T * brp[i]) for i in range(b[-1], I + 1)]
+        m = min(d)
+        b.append(b[-1] + max(k for k, v in enumerate(d) if v == m))
+    return b
+
+
+def test_partition_matches_the_oracle_and_its_definition():
+    import oracle
+
+    rng = np.random.default_rng(21)
+    cases = [np.array([0]), np.array([0, 0, 0, 0]), np.array([0, 7]), np.array([0, 3, 3, 7, 9, 12])]
+    for _ in range(300):
+        I = int(rng.integers(0, 50))
+        per = rng.integers(0, 9, I) * (rng.random(I) < 0.6)
+        cases.append(np.concatenate([[0], np.cumsum(per)]).astype(np.int32))
+    from paper_1801_01134_gb300 import inputs
+
+    B = oracle.beta_convert(inputs.rmat(11, seed=3), 2, 8)  # power-law block counts
+    cases.append(B.block_rowptr)
+    for brp in cases:
+        for T in (1, 2, 3, 7, 16, 100):
+            got = spc5.partition(brp, T)
+            assert list(got) == list(oracle.partition(brp, T)) == _partition_brute(brp, T), (T,)
+
+
+def test_partition_rejects_bad_arguments():
+    with pytest.raises(spc5.Spc5Error) as ei:
+        spc5.partition(np.array([0, 1, 2]), 0)
+    assert ei.value.status == spc5.EINVAL

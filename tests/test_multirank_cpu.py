@@ -36,7 +36,10 @@ def _worker(rank, world, port, out_dir):
     A = inputs.rmat(12, seed=4)
     r, c = 2, 8
     B = oracle.beta_convert(A, r, c)
-    bounds = oracle.partition(B.block_rowptr, world)
+    from paper_1801_01134_gb300 import spc5
+
+    bounds = spc5.partition(B.block_rowptr, world)  # the library's partition (host call)
+    assert np.array_equal(bounds, oracle.partition(B.block_rowptr, world))
     # this rank's rows and its shard of x
     i0, i1 = int(bounds[rank]), int(bounds[rank + 1])
     row0, row1 = min(i0 * r, A.n), min(i1 * r, A.n)

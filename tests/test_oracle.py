@@ -350,6 +350,34 @@ def test_partition_rule_balances_blocks():
         assert np.all(np.abs(np.cumsum(loads)[:-1] - B.nblocks / T * np.arange(1, T)) <= per_iv.max() + 1)
 
 
+def _partition_brute(brp, T):
+    """Each boundary by exhaustion: from the previous boundary, the last interval
+    index whose block prefix is nearest (exactly, in integers) to (t+1)*Nb/T."""
+    brp = [int(v) for v in brp]
+    I, nb = len(brp) - 1, brp[-1]
+    b = [0]
+    for t in range(T):
+        if t == T - 1:
+            b.append(I)
+            continue
+        d = [abs((t + 1) * nb - T * brp[i]) for i in range(b[-1], I + 1)]
+        m = min(d)
+        b.append(b[-1] + max(k for k, v in enumerate(d) if v == m))
+    return b
+
+
+def test_partition_equals_its_definition_by_exhaustion():
+    rng = np.random.default_rng(9)
+    cases = [np.array([0]), np.array([0, 0, 0]), np.array([0, 5]), np.array([0, 3, 3, 7, 9, 12])]
+    for _ in range(300):
+        I = int(rng.integers(0, 40))
+        per = rng.integers(0, 6, I) * (rng.random(I) < 0.7)  # many empty intervals
+        cases.append(np.concatenate([[0], np.cumsum(per)]))
+    for brp in cases:
+        for T in (1, 2, 3, 5, 8, 64):
+            assert list(oracle.partition(brp, T)) == _partition_brute(brp, T), (list(brp), T)
+
+
 def test_round_bf16_against_torch():
     torch = pytest.importorskip("torch")
     v = inputs.vec_normal(20000, seed=4) * 10.0 ** inputs.vec_uniform(20000, seed=5, lo=-3, hi=3)
