@@ -190,6 +190,15 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+SLOWDOWN_REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown")
+
+
+def throttled(clocks: dict) -> bool:
+    """True when the clock samples of a timed region saw a hardware or thermal
+    slowdown (sw_power_cap alone is kept and noted)."""
+    return any(r in SLOWDOWN_REASONS for r in clocks.get("reasons", []))
+
+
 def dist_init(args):
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -655,19 +664,31 @@ def main():
     flops_step = sum(2.0 * p["A"].nnz for p in prep64)
 
     # ---- timed region (float64, selected formats)
-    barrier(ws)
-    torch.cuda.synchronize()
-    with ClockSampler(local) as cs:
-        wall0 = time.perf_counter()
-        times = run_steps(prep64, args.steps, args.warmup)
+    def timed_region():
+        barrier(ws)
         torch.cuda.synchronize()
-        wall1 = time.perf_counter()
-    torch.cuda.synchronize()
-    barrier(ws)
+        with ClockSampler(local) as cs:
+            w0 = time.perf_counter()
+            t = run_steps(prep64, args.steps, args.warmup)
+            torch.cuda.synchronize()
+            w1 = time.perf_counter()
+        torch.cuda.synchronize()
+        barrier(ws)
+        return t, cs.summary(), w0, w1
+
+    times, clocks, wall0, wall1 = timed_region()
+    # a run that saw a hardware or thermal slowdown is measured once more (every
+    # rank together: the decision is the max over ranks)
+    if max_over_ranks(1.0 if throttled(clocks) else 0.0, ws, dev) > 0:
+        first = clocks
+        times, clocks, wall0, wall1 = timed_region()
+        clocks["remeasured_after"] = first["reasons"]
     step_ms = [sum(times[p["name"]][k] for p in prep64) for k in range(args.steps)]
     total_ms = max_over_ranks(sum(step_ms), ws, dev)
     value = flops_step * args.steps * ws / (total_ms * 1e-3) / 1e9
-    launches_per_step = sum(1 + (2 if p["nseg"] > 0 else 0) + 1 for p in prep64)  # SpMV kernels + L2 flush copy
+    # kernels of one product (one grid, plus the fix-up when there are long
+    # intervals) and the L2-flush copy before it
+    launches_per_step = sum((2 if p["nseg"] > 0 else 1) + 1 for p in prep64)
 
     # bytes model (algorithmic): values + colidx + masks + block_rowptr + valptr + x + y
     def beta_bytes(p, vsize, xsize):
@@ -829,7 +850,7 @@ def main():
                 "pipeline": "pinned host x in and y out every step on two copy streams, overlapping the products "
                             "(spc5_spmv on the compute stream), L2 not flushed"},
         "gpu_launches": launches_per_step * args.steps,
-        "clocks": cs.summary(), "wall_s_timed": round(wall1 - wall0, 3),
+        "clocks": clocks, "wall_s_timed": round(wall1 - wall0, 3),
         "csr": {"value": round(csr_value, 2), "unit": "GFLOP/s", "per_matrix": csr_per,
                 "speedup_beta_over_csr": round(value / csr_value, 3)},
         "per_matrix": per_matrix, "f32": f32, "cg": cg_res, "spmm_f32": spmm_res, "batch_f32": batch_res, "selector": sel_res,

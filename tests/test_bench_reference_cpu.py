@@ -49,3 +49,22 @@ def test_reference_arm_two_gloo_ranks():
     lines = _json_lines(r.stdout)
     assert len(lines) == 1  # rank 0 only
     _check(lines[0], 2)
+
+
+def test_clock_samples_and_the_slowdown_rule():
+    sys.path.insert(0, ROOT)
+    import bench
+
+    cs = bench.ClockSampler(0)
+    # clocks.sm, clocks.max.sm, power, active-mask, hw, hw_thermal, sw_thermal, sw_power_cap
+    cs.lines = ["2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active",
+                "2040, 2070, 1390.0, 0x4, Not Active, Not Active, Not Active, Active",
+                "2055, 2070, 1200.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+                "garbage line"]
+    s = cs.summary()
+    assert s["sm_mhz"] == 2055 and s["sm_max_mhz"] == 2070 and s["samples"] == 3
+    assert s["reasons"] == ["sw_power_cap"] and not bench.throttled(s)  # power cap: kept and noted
+    cs.lines.append("1600, 2070, 1400.0, 0x8, Not Active, Active, Not Active, Not Active")
+    s = cs.summary()
+    assert "hw_thermal_slowdown" in s["reasons"] and bench.throttled(s)  # measured again
+    assert not bench.throttled(bench.ClockSampler(0).summary())  # no samples at all
