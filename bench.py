@@ -268,6 +268,38 @@ def run_reference(args):
 
 # ---------------------------------------------------------------------- SpMM
 
+def precision_errors(prep32, y64_ref):
+    """Error of the float32 and bfloat16 storage forms against the float64 product of
+    the same matrix and x (the float64 result the tests hold to the oracle within
+    1e-13 (|A||x|)_i), per matrix: max_i |y_i - y64_i| / max_i |y64_i| and the
+    relative 2-norm. bfloat16 is converted in the shape float32 selected; x is the
+    float32 rounding of the float64 x in both forms."""
+    import torch
+
+    from paper_1801_01134_gb300 import spc5
+
+    def measures(y, y64):
+        d = (y.double() - y64).abs()
+        return {"max_rel_to_max": float(d.max() / y64.abs().max().clamp_min(1e-300)),
+                "rel_l2": float(torch.linalg.vector_norm(d) / torch.linalg.vector_norm(y64).clamp_min(1e-300))}
+
+    out = {}
+    try:
+        for p in prep32:
+            y64 = y64_ref[p["name"]]
+            res = {"shape": f"{p['r']}x{p['c']}", "f32": measures(p["M"].spmv(p["x"]), y64)}
+            A = p["A"]
+            d16 = spc5.upload_csr(A, torch.bfloat16, p["x"].device)
+            M16 = spc5.convert(d16.rowptr, d16.colidx, d16.values, A.n, A.m, p["r"], p["c"])
+            res["bf16"] = measures(M16.spmv(p["x"]), y64)
+            M16.destroy()
+            del d16
+            out[p["name"]] = res
+    except Exception as e:  # reporting only: never costs the measured line
+        out["unavailable"] = f"{type(e).__name__}: {e}"
+    return out
+
+
 def run_spmm_section(mats, dev, ks=(1, 4, 8, 16, 32), tiles=(4, -8, -16, -32, 8, 16, 32), reps: int = 5):
     """float32 Y = A X for k right-hand sides on the stencil and R-MAT matrices,
     best (shape, k-tile) per k from a small tuning sweep; GFLOP/s = 2 nnz k / t."""
@@ -796,6 +828,8 @@ def main():
     sel_res = run_selector_section(prep64, dev)
 
     # ---- float32 storage form
+    # float64 products kept to report the error of the low-precision forms
+    y64_ref = {p["name"]: p["M"].spmv(p["x"]).clone() for p in prep64}
     for p in prep64:
         p["M"].destroy()
         del p["d"]
@@ -811,6 +845,7 @@ def main():
                           for p in prep32]}
     csr32_times = run_steps(prep32, args.steps, 1, fn_name="csr")
     f32["csr_value"] = round(flops_step * args.steps / (sum(sum(v) for v in csr32_times.values()) * 1e-3) / 1e9, 1)
+    f32["error_vs_float64"] = precision_errors(prep32, y64_ref)
     for p in prep32:
         p["M"].destroy()
 
