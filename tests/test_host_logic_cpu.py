@@ -116,3 +116,29 @@ def test_partition_rejects_bad_arguments():
     with pytest.raises(spc5.Spc5Error) as ei:
         spc5.partition(np.array([0, 1, 2]), 0)
     assert ei.value.status == spc5.EINVAL
+
+
+def test_binding_checks_vectors_before_calling_the_library():
+    import torch
+
+    # a handle value that is never passed on: every call below fails in the binding first
+    M = spc5.Matrix(0x10, n=10, m=7, nnz=0, r=1, c=4, vt=spc5.SPC5_F64)
+    try:
+        with pytest.raises(TypeError):
+            M.spmv_acc(torch.zeros(7, dtype=torch.float32), torch.zeros(10, dtype=torch.float64))
+        with pytest.raises(ValueError):
+            M.spmv_acc(torch.zeros(6, dtype=torch.float64), torch.zeros(10, dtype=torch.float64))
+        with pytest.raises(ValueError):
+            M.spmv_noalloc(torch.zeros(7, dtype=torch.float64), torch.zeros(11, dtype=torch.float64))
+        M32 = spc5.Matrix(0x10, n=4, m=4, nnz=0, r=2, c=8, vt=spc5.SPC5_BF16)
+        try:
+            assert M32.vector_dtype == torch.float32  # bfloat16 storage takes float32 vectors
+            with pytest.raises(TypeError):
+                M32.spmv_acc(torch.zeros(4, dtype=torch.bfloat16), torch.zeros(4, dtype=torch.float32))
+        finally:
+            M32._h = None
+    finally:
+        M._h = None  # never handed to spc5_destroy
+    M._h = None
+    with pytest.raises(ValueError):  # a destroyed matrix
+        M.spmv_acc(torch.zeros(7, dtype=torch.float64), torch.zeros(10, dtype=torch.float64))
