@@ -11,7 +11,8 @@ Each function cites the part of the paper it follows:
     and as a compensated Dot2 product (Ogita, Rump & Oishi 2005);
   * CSR -> beta(r,c) conversion and beta(r,c) -> CSR expansion (section
     "Block-based storage without zero padding", Eq. 1);
-  * Algorithm 1 run on the beta(r,c) arrays;
+  * the product y += A x read straight from the beta(r,c) arrays (block
+    masks decoded into (row, column, value) triples, Eq. 1);
   * the occupancy model, Eq. 1-4;
   * the static partition of section "Parallelization";
   * dense GEMV for tiny matrices.
@@ -69,10 +70,11 @@ def _load():
         lib.or_beta_convert.restype = i32
         lib.or_beta_expand.argtypes = [i64, i32, i32, vp, vp, vp, vp, vp, vp, vp]
         lib.or_beta_expand.restype = i32
-        lib.or_beta_spmv_alg1.argtypes = [i64, i32, i32, vp, vp, vp, vp, vp, vp]
+        lib.or_beta_spmv.argtypes = [i64, i32, i32, vp, vp, vp, vp, vp, vp]
+        lib.or_beta_spmv.restype = i32
         lib.or_partition.argtypes = [i64, vp, i32, vp]
         lib.or_omp_threads.restype = i32
-        for f in (lib.or_csr_spmv, lib.or_csr_spmv_omp, lib.or_csr_spmv_dot2, lib.or_beta_spmv_alg1, lib.or_partition):
+        for f in (lib.or_csr_spmv, lib.or_csr_spmv_omp, lib.or_csr_spmv_dot2, lib.or_partition):
             f.restype = None
         _lib = lib
     return _lib
@@ -238,15 +240,18 @@ def beta_expand(B: Beta) -> _CSR:
     return _CSR(B.n, B.m, rowptr, colidx[:nnz].copy(), values[:nnz].copy())
 
 
-def beta_spmv_alg1(B: Beta, x: np.ndarray, y0: np.ndarray | None = None) -> np.ndarray:
-    """Algorithm 1 on the beta(r,c) arrays: y = y0 + A x (y0 = 0 if omitted)."""
+def beta_spmv(B: Beta, x: np.ndarray, y0: np.ndarray | None = None) -> np.ndarray:
+    """y = y0 + A x read from the beta(r,c) arrays (y0 = 0 if omitted): every set
+    mask bit is one stored value, in storage order (Eq. 1)."""
     y = np.zeros(B.n) if y0 is None else np.array(y0, dtype=np.float64, copy=True)
     x = np.ascontiguousarray(x, dtype=np.float64)
     brp = np.ascontiguousarray(B.block_rowptr, dtype=np.int32)
     bcol = np.ascontiguousarray(B.block_colidx if B.nblocks else np.zeros(1, np.int32), dtype=np.int32)
     bmask = np.ascontiguousarray(B.block_masks if B.nblocks else np.zeros(1, np.uint8), dtype=np.uint8)
     bval = np.ascontiguousarray(B.values if B.nnz else np.zeros(1), dtype=np.float64)
-    _load().or_beta_spmv_alg1(B.n, B.r, B.c, _p(brp), _p(bcol), _p(bmask), _p(bval), _p(x), _p(y))
+    st = _load().or_beta_spmv(B.n, B.r, B.c, _p(brp), _p(bcol), _p(bmask), _p(bval), _p(x), _p(y))
+    if st != OK:
+        raise ValueError(f"or_beta_spmv failed: {st}")
     return y
 
 

@@ -242,29 +242,54 @@ int or_beta_expand(int64_t n, int r, int c, const int32_t* block_rowptr, const i
   return OR_OK;
 }
 
-/* Algorithm 1 (section "SpMV kernels for beta(r,c) storages"), scalar form,
- * on the beta(r,c) arrays: per interval, per block, per block row, per set bit
- * k, sum[row] += x[colidx + k] * values[idxVal++]; then y[row] += sum[row].
- * The paper's kernel accumulates into y. */
-void or_beta_spmv_alg1(int64_t n, int r, int c, const int32_t* block_rowptr, const int32_t* block_colidx,
-                       const uint8_t* block_masks, const double* bvalues, const double* x, double* y) {
-  int mb = mask_bytes(r, c);
-  int64_t idxVal = 0;
-  double sum[64];
-  for (int64_t idxRow = 0; idxRow < n; idxRow += r) {
-    for (int i = 0; i < r; ++i) sum[i] = 0.0;
-    for (int64_t idxBlock = block_rowptr[idxRow / r]; idxBlock < block_rowptr[idxRow / r + 1]; ++idxBlock) {
-      int64_t idxCol = block_colidx[idxBlock];
-      for (int idxRowBlock = 0; idxRowBlock < r; ++idxRowBlock)
-        for (int k = 0; k < c; ++k)
-          if (get_bit(block_masks + idxBlock * mb, idxRowBlock * c + k)) {
-            sum[idxRowBlock] += x[idxCol + k] * bvalues[idxVal];
-            idxVal += 1;
-          }
-    }
-    for (int idxRowBlock = 0; idxRowBlock < r && idxRow + idxRowBlock < n; ++idxRowBlock)
-      y[idxRow + idxRowBlock] += sum[idxRowBlock];
+/* y += A x on the beta(r,c) arrays, from the storage definition (section
+ * "Block-based storage without zero padding", Eq. 1): the stored values are
+ * the blocks' nonzeros, block after block, and inside a block in the order of
+ * the set mask bits (row-major, bit i*c + k = row i, column k). Step 1 turns
+ * the arrays back into one (row, column, value) triple per stored value;
+ * step 2 forms t[row] = sum of value * x[column] over the row's triples in
+ * storage order, then adds t to y (the paper's kernels accumulate into y).
+ * A row's triples come out left to right (an interval's blocks are disjoint
+ * and stored in column order), so t[row] takes the same additions as the
+ * plain CSR loop. Returns OR_ERANGE if a set bit lies past row n-1. */
+int or_beta_spmv(int64_t n, int r, int c, const int32_t* block_rowptr, const int32_t* block_colidx,
+                 const uint8_t* block_masks, const double* bvalues, const double* x, double* y) {
+  const int mb = mask_bytes(r, c);
+  const int64_t nint = (n + r - 1) / r;
+  const int64_t nblocks = nint > 0 ? block_rowptr[nint] : 0;
+  int64_t ntrip = 0;
+  for (int64_t q = 0; q < nblocks * mb; ++q)
+    for (int bit = 0; bit < 8; ++bit) ntrip += (block_masks[q] >> bit) & 1;
+  int64_t* trow = (int64_t*)malloc(sizeof(int64_t) * (size_t)(ntrip > 0 ? ntrip : 1));
+  int64_t* tcol = (int64_t*)malloc(sizeof(int64_t) * (size_t)(ntrip > 0 ? ntrip : 1));
+  double* t = (double*)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+  if (!trow || !tcol || !t) {
+    free(trow);
+    free(tcol);
+    free(t);
+    return OR_EINVAL;
   }
+  /* step 1: triples; the value of triple j is bvalues[j] */
+  int64_t j = 0;
+  int st = OR_OK;
+  for (int64_t interval = 0; interval < nint; ++interval)
+    for (int64_t blk = block_rowptr[interval]; blk < block_rowptr[interval + 1]; ++blk)
+      for (int bit = 0; bit < r * c; ++bit)
+        if (get_bit(block_masks + blk * mb, bit)) {
+          trow[j] = interval * r + bit / c;
+          tcol[j] = (int64_t)block_colidx[blk] + bit % c;
+          if (trow[j] >= n) st = OR_ERANGE;
+          ++j;
+        }
+  /* step 2: row sums in storage order, then y += t */
+  if (st == OR_OK) {
+    for (int64_t q = 0; q < ntrip; ++q) t[trow[q]] += bvalues[q] * x[tcol[q]];
+    for (int64_t i = 0; i < n; ++i) y[i] += t[i];
+  }
+  free(trow);
+  free(tcol);
+  free(t);
+  return st;
 }
 
 /* ----------------------------------------------------------- partition */

@@ -55,7 +55,7 @@ def _worker(rank, world, port, out_dir):
                       B.block_colidx[B.block_rowptr[i0]:B.block_rowptr[i1]],
                       B.block_masks[B.block_rowptr[i0] * 2:B.block_rowptr[i1] * 2],
                       B.values[A.rowptr[row0]:A.rowptr[row1]])
-    y_mine = oracle.beta_spmv_alg1(sub, x)
+    y_mine = oracle.beta_spmv(sub, x)
     sizes = [torch.zeros(1, dtype=torch.int64) for _ in range(world)]
     dist.all_gather(sizes, torch.tensor([y_mine.size], dtype=torch.int64))
     mx = int(max(s.item() for s in sizes))

@@ -192,12 +192,12 @@ def test_vexpand_worked_example():
     assert B.nblocks == 1 and B.block_colidx[0] == 0
     assert int(B.block_masks[0]) == mask
     assert np.array_equal(B.values, p)
-    # Algorithm 1 with x = unit vector e_k reads lane k of the expanded vector
+    # the product with x = unit vector e_k reads lane k of the expanded vector
     for k in range(8):
         x = np.zeros(8)
         x[k] = 1.0
         want = 0.0 if lanes[k] < 0 else p[lanes[k]]
-        assert oracle.beta_spmv_alg1(B, x)[0] == want
+        assert oracle.beta_spmv(B, x)[0] == want
 
 
 def check_beta_invariants(A, B):
@@ -239,17 +239,36 @@ def test_roundtrip_bit_exact_all_shapes(r, c):
 
 
 @pytest.mark.parametrize("r,c", oracle.SHAPES)
-def test_alg1_equals_plain_csr_bitwise(r, c):
-    # Algorithm 1 visits each row's entries in ascending column order, as the
-    # plain CSR loop does, so with y0 = 0 the float64 results are identical.
+def test_beta_spmv_equals_plain_csr_bitwise(r, c):
+    # the blocks of an interval are disjoint and stored left to right, so the
+    # product read from the beta arrays adds each row's entries in ascending
+    # column order, as the plain CSR loop does: identical float64 results.
     A = inputs.stencil3d(9, 7, 5, points=27, seed=4)
     x = inputs.vec_uniform(A.m, seed=0)
     B = oracle.beta_convert(A, r, c)
     check_beta_invariants(A, B)
-    assert np.array_equal(oracle.beta_spmv_alg1(B, x), oracle.csr_spmv(A, x))
-    # Algorithm 1 accumulates into y
+    assert np.array_equal(oracle.beta_spmv(B, x), oracle.csr_spmv(A, x))
+    # the paper's kernels accumulate into y
     y0 = inputs.vec_uniform(A.n, seed=9)
-    assert np.allclose(oracle.beta_spmv_alg1(B, x, y0), y0 + oracle.csr_spmv(A, x), rtol=0, atol=1e-13)
+    assert np.allclose(oracle.beta_spmv(B, x, y0), y0 + oracle.csr_spmv(A, x), rtol=0, atol=1e-13)
+
+
+@pytest.mark.parametrize("r,c", [(1, 4), (2, 8), (4, 4), (8, 16)])
+def test_beta_spmv_matches_dense_gemv_bruteforce(r, c):
+    # n not a multiple of r (a ragged last interval) and columns near m - 1 (blocks
+    # running past the last column): the product read from the beta arrays must
+    # equal the textbook dense sum on every row
+    rng = np.random.default_rng(40 + r * c)
+    for n, m in ((13, 11), (9, 30), (3, 5)):
+        D = np.where(rng.random((n, m)) < 0.35, rng.standard_normal((n, m)), 0.0)
+        x = rng.standard_normal(m)
+        B = oracle.beta_convert(csr_of_dense(D), r, c)
+        got = oracle.beta_spmv(B, x)
+        assert np.allclose(got, oracle.dense_gemv(D, x), rtol=1e-14, atol=1e-14)
+        # a nonzero moved to another place changes the product there
+        if B.nnz:
+            B2 = oracle.Beta(B.n, B.m, B.r, B.c, B.block_rowptr, B.block_colidx, B.block_masks, B.values * 2.0)
+            assert np.allclose(oracle.beta_spmv(B2, x), 2.0 * got, rtol=1e-14, atol=1e-14)
 
 
 def min_cover_bruteforce(colsets, c):

@@ -27,6 +27,41 @@ def test_features_known_matrices():
     assert f[12] == lens.mean() and f[14] == 5
 
 
+def test_row_length_std_hand_worked():
+    # row lengths 1, 1, 4 (and one more matrix with 0, 2, 4, 6): mean 2 and
+    # population standard deviation sqrt(((1-2)^2 + (1-2)^2 + (4-2)^2) / 3) = sqrt(2);
+    # for 0, 2, 4, 6: mean 3, sqrt((9 + 1 + 1 + 9) / 4) = sqrt(5)
+    D = np.zeros((3, 8))
+    D[0, 2] = 1.0
+    D[1, 7] = 1.0
+    D[2, :4] = 1.0
+    f = osel.features(inputs.CSR.from_dense(D))
+    assert f[12] == 2.0 and abs(f[13] - 2 ** 0.5) < 1e-15 and f[14] == 4.0
+    E = np.zeros((4, 6))
+    E[1, :2] = 1.0
+    E[2, 1:5] = 1.0
+    E[3, :] = 1.0
+    f = osel.features(inputs.CSR.from_dense(E))
+    assert f[12] == 3.0 and abs(f[13] - 5 ** 0.5) < 1e-15 and f[14] == 6.0
+
+
+def test_poly_select_takes_the_highest_estimate():
+    # the paper's predictor keeps the format whose polynomial promises the most
+    # GFLOP/s at the matrix's Avg(r,c). Hand-built table: format q estimates
+    # q + 1 at every Avg except format 7, whose estimate is 100 - Avg^2
+    coefs = [np.array([q + 1.0]) for q in range(osel.NFMT)]
+    coefs[7] = np.array([100.0, 0.0, -1.0])
+    feats = np.zeros(osel.NFEAT)
+    feats[:12] = 3.0  # estimate of format 7: 91, the highest
+    assert osel.poly_select(coefs, feats) == 7
+    feats[7] = 9.5  # 100 - 90.25 = 9.75 < 12: format 11 (estimate 12) is best
+    assert osel.poly_select(coefs, feats) == 11
+    # estimates that fall with Avg: the format with the smallest Avg wins
+    coefs = [np.array([50.0, -2.0]) for _ in range(osel.NFMT)]
+    feats[:12] = [5, 4, 9, 7, 2.5, 6, 8, 3, 11, 10, 12, 13]
+    assert osel.poly_select(coefs, feats) == 4
+
+
 def test_poly_fit_recovers_exact_polynomials():
     rng = np.random.default_rng(0)
     for deg in (1, 2, 3, 4):
