@@ -266,17 +266,83 @@ def run_reference(args):
     return 0
 
 
+# ------------------------------------------------------------ bytes, rooflines
+
+VSIZE = {"f64": (8, 8), "f32": (4, 4), "bf16": (2, 4)}  # bytes per stored value, per x / y entry
+NOMINAL_NOTE = "of nominal"
+
+
+def beta_bytes(p, vsize, xsize):
+    """Algorithmic bytes of one beta(r,c) SpMV: values + colidx + masks + block_rowptr
+    + valptr + x + y, x counted once."""
+    A, r, c = p["A"], p["r"], p["c"]
+    I = (A.n + r - 1) // r
+    mb = (r * c + 7) // 8
+    return vsize * A.nnz + (4 + mb) * p["nblocks"] + 4 * (I + 1) + 8 * (I + 1) + xsize * A.m + xsize * A.n
+
+
+def csr_bytes(p, vsize, xsize):
+    """Algorithmic bytes of one CSR SpMV (int64 row pointer here)."""
+    A = p["A"]
+    return vsize * A.nnz + 4 * A.nnz + 8 * (A.n + 1) + xsize * A.m + xsize * A.n
+
+
+def measured_hbm_peak():
+    """The measured copy ceiling (MEASURED_PEAKS.json), else the recipe's fallback."""
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]), \
+            "MEASURED_PEAKS.json hbm_gbs: copy ceiling (of measured)"
+    except Exception:
+        return 6800.0, "fallback 6.8 TB/s (of fallback)"
+
+
+def spmv_kernel_names(p):
+    """The kernels one product of a prepared matrix launches (names as ncu lists them)."""
+    if p["variant"] == 22:
+        rows = "k_spmv_rows_g"
+    elif p["variant"] == 1:
+        rows = "k_spmv_rows"
+    else:
+        rows = "k_spmv_rows_u"
+    if p["nseg"] > 0:
+        return ("k_spmv_rows_segs" if p["variant"] != 1 else f"{rows}+k_spmv_segments") + "+k_spmv_fixup"
+    return rows
+
+
+def roofline_entry(p, tlist, key, hbm_peak, hbm_src, hbm_nominal):
+    """HBM roofline of one matrix's product: algorithmic bytes / mean duration."""
+    t = statistics.mean(tlist)
+    b = beta_bytes(p, *VSIZE[key])
+    gbs = b / t / 1e6
+    return {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s", "frac": round(gbs / hbm_peak, 4),
+            "traffic": profile_traffic(traffic_key(p["r"], p["c"], p["variant"], key, p["name"])),
+            "algorithmic_bytes": int(b), "mean_ms": round(t, 4),
+            "kernel": f"{spmv_kernel_names(p)}<{p['r']},{p['c']},{key}> variant {p['variant']} on {p['name']}",
+            "peak_source": hbm_src, "nominal_peak": round(hbm_nominal, 1),
+            "frac_of_nominal": round(gbs / hbm_nominal, 4)}
+
+
+def matrix_entry(p, tlist, key, hbm_peak, roofline=None):
+    t = statistics.median(tlist)
+    A = p["A"]
+    gbs = beta_bytes(p, *VSIZE[key]) / t / 1e6
+    e = {"matrix": p["name"], "n": A.n, "nnz": A.nnz, "shape": f"{p['r']}x{p['c']}", "variant": p["variant"],
+         "avg_nnz_per_block": round(A.nnz / max(p["nblocks"], 1), 3), "segments": p["nseg"], "ms": round(t, 4),
+         "gflops": round(2.0 * A.nnz / t / 1e6, 1), "gbs": round(gbs, 1), "hbm_frac": round(gbs / hbm_peak, 4),
+         "sweep_gflops": p["sweep_gflops"]}
+    if roofline is not None:
+        e["roofline"] = roofline
+    return e
+
+
 # ---------------------------------------------------------------------- SpMM
 
-def precision_errors(prep32, y64_ref):
-    """Error of the float32 and bfloat16 storage forms against the float64 product of
-    the same matrix and x (the float64 result the tests hold to the oracle within
+def precision_errors(prep, y64_ref):
+    """Error of a float32 or bfloat16 storage form against the float64 product of the
+    same matrix and x (the float64 result the tests hold to the oracle within
     1e-13 (|A||x|)_i), per matrix: max_i |y_i - y64_i| / max_i |y64_i| and the
-    relative 2-norm. bfloat16 is converted in the shape float32 selected; x is the
-    float32 rounding of the float64 x in both forms."""
+    relative 2-norm; x is the float32 rounding of the float64 x."""
     import torch
-
-    from paper_1801_01134_gb300 import spc5
 
     def measures(y, y64):
         d = (y.double() - y64).abs()
@@ -285,16 +351,8 @@ def precision_errors(prep32, y64_ref):
 
     out = {}
     try:
-        for p in prep32:
-            y64 = y64_ref[p["name"]]
-            res = {"shape": f"{p['r']}x{p['c']}", "f32": measures(p["M"].spmv(p["x"]), y64)}
-            A = p["A"]
-            d16 = spc5.upload_csr(A, torch.bfloat16, p["x"].device)
-            M16 = spc5.convert(d16.rowptr, d16.colidx, d16.values, A.n, A.m, p["r"], p["c"])
-            res["bf16"] = measures(M16.spmv(p["x"]), y64)
-            M16.destroy()
-            del d16
-            out[p["name"]] = res
+        for p in prep:
+            out[p["name"]] = {"shape": f"{p['r']}x{p['c']}", **measures(p["M"].spmv(p["x"]), y64_ref[p["name"]])}
     except Exception as e:  # reporting only: never costs the measured line
         out["unavailable"] = f"{type(e).__name__}: {e}"
     return out
@@ -477,6 +535,52 @@ def run_cg_section(dev, reps: int = 3):
     for h in hs.values():
         h.destroy()
     return out
+
+
+# ---------------------------------------------------------------- CPU baseline
+
+def run_cpu_baseline(mats, prep64, budget_s: float = 20.0):
+    """The oracle as it stands on the host cores, timed as the paper times its kernels
+    (mean of 16 runs): the plain CSR loop over all cores (the reported value) and on one
+    core, and the oracle's product read from the beta(r,c) arrays (one core) in each
+    matrix's selected shape. Run counts shrink so that the whole sample stays near
+    budget_s seconds of CPU time."""
+    import oracle
+
+    flops = sum(2.0 * mt["A"].nnz for mt in mats)
+
+    def mean_runs(fn, runs):
+        ts = []
+        for _ in range(runs):
+            t0 = time.perf_counter()
+            fn()
+            ts.append(time.perf_counter() - t0)
+        return statistics.mean(ts), runs
+
+    def suite(f):
+        for mt in mats:
+            f(mt["A"], mt["x"])
+
+    t_all, n_all = mean_runs(lambda: suite(oracle.csr_spmv_omp), 16)
+    t1 = mean_runs(lambda: suite(oracle.csr_spmv), 1)[0]
+    t_one, n_one = mean_runs(lambda: suite(oracle.csr_spmv), max(1, min(16, int(budget_s * 0.5 / max(t1, 1e-9)))))
+    beta = {}
+    shapes = {p["name"]: (p["r"], p["c"]) for p in prep64}
+    for mt in mats:
+        A = mt["A"]
+        r, c = shapes[mt["name"]]
+        B = oracle.beta_convert(A, r, c)
+        tb1 = mean_runs(lambda: oracle.beta_spmv(B, mt["x"]), 1)[0]
+        tb, nb = mean_runs(lambda: oracle.beta_spmv(B, mt["x"]), max(1, min(16, int(budget_s * 0.1 / max(tb1, 1e-9)))))
+        beta[mt["name"]] = {"shape": f"{r}x{c}", "gflops": round(2.0 * A.nnz / tb / 1e9, 3), "runs": nb}
+        del B
+    cores = oracle.omp_threads()
+    return {"value": round(flops / t_all / 1e9, 3), "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
+            "sample": f"mean of {n_all} runs of the 4 float64 CSR SpMVs (plain loop, OpenMP over rows, "
+                      f"{cores} threads), full matrices",
+            "single_thread": {"value": round(flops / t_one / 1e9, 3), "unit": "GFLOP/s", "runs": n_one,
+                              "sample": "the same loop on one core"},
+            "beta_oracle_one_core": beta}
 
 
 # ------------------------------------------------------------------ profiling
@@ -691,7 +795,77 @@ def main():
         torch.cuda.synchronize()
         return {k: [a.elapsed_time(b) for a, b in v] for k, v in per.items()}
 
+    def csr_section(prep, K, key, beta_value):
+        """The plain CSR kernel (lanes per row tuned per matrix) under the same protocol."""
+        ct = run_steps(prep, K, 1, fn_name="csr")
+        cms = sum(sum(v) for v in ct.values())
+        cval = sum(2.0 * p["A"].nnz for p in prep) * K / (cms * 1e-3) / 1e9
+        per = {}
+        for p in prep:
+            tc = statistics.median(ct[p["name"]])
+            per[p["name"]] = {"group": p["csr_group"], "gflops": round(2.0 * p["A"].nnz / tc / 1e6, 1),
+                              "gbs": round(csr_bytes(p, *VSIZE[key]) / tc / 1e6, 1)}
+        return {"value": round(cval, 2), "unit": "GFLOP/s", "per_matrix": per,
+                "speedup_beta_over_csr": round(beta_value / cval, 3)}
+
+    def run_e2e(prep, K, stream, ws, dev, flops_step):
+        """Pinned host x -> device, SpMV through the public call, y -> pinned host, every step."""
+        hx = [torch.from_numpy(p["x"].cpu().numpy()).pin_memory() for p in prep]
+        hy = [torch.empty(p["A"].n, dtype=p["y"].dtype).pin_memory() for p in prep]
+        h2d = sum(t.numel() * t.element_size() for t in hx)
+        d2h = sum(t.numel() * t.element_size() for t in hy)
+        # three streams: host->device copies, the products, device->host copies;
+        # events order each matrix's x copy before its product, its product before
+        # its y copy, and keep the next step from overwriting a buffer still in use
+        s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
+        nmat = len(prep)
+        ev_x = [torch.cuda.Event() for _ in range(nmat)]    # x_j arrived
+        ev_mv = [torch.cuda.Event() for _ in range(nmat)]   # product j done (x_j free, y_j ready)
+        ev_y = [torch.cuda.Event() for _ in range(nmat)]    # y_j copied out (y_j free)
+        for j in range(nmat):  # all "free" at the start
+            ev_mv[j].record(stream)
+            ev_y[j].record(stream)
+
+        def e2e_step():
+            for j, (p, a, b) in enumerate(zip(prep, hx, hy)):
+                s_in.wait_event(ev_mv[j])
+                with torch.cuda.stream(s_in):
+                    p["x"].copy_(a, non_blocking=True)
+                ev_x[j].record(s_in)
+                stream.wait_event(ev_x[j])
+                stream.wait_event(ev_y[j])
+                p["M"].spmv(p["x"], p["y"], stream=stream)
+                ev_mv[j].record(stream)
+                s_out.wait_event(ev_mv[j])
+                with torch.cuda.stream(s_out):
+                    b.copy_(p["y"], non_blocking=True)
+                ev_y[j].record(s_out)
+
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for _ in range(2):
+            e2e_step()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(K):
+            e2e_step()
+        for j in range(nmat):  # the last copies out belong to the timed region
+            stream.wait_event(ev_y[j])
+        e1.record(stream)
+        e1.synchronize()
+        torch.cuda.synchronize()
+        e2e_ms = max_over_ranks(e0.elapsed_time(e1), ws, dev)
+        return {"value": round(flops_step * K * ws / (e2e_ms * 1e-3) / 1e9, 2), "unit": "GFLOP/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "pipeline": "pinned host x in and y out every step on two copy streams, overlapping the products "
+                            "(spc5_spmv on the compute stream); no L2 flush: x arrives through the copy (as it would "
+                            "in a user's pipeline), the matrix arrays are cold because the other three matrices "
+                            "(several GB) pass through L2 between two products of one matrix"}
+
     fp64_measured = spc5.fma_rate(torch.float64)  # live measured float64 FMA rate (GFLOP/s)
+    peaks = spc5.device_peaks()
+    hbm_nominal = peaks["hbm_gbs_nominal"]
+    hbm_peak, hbm_src = measured_hbm_peak()
     prep64 = prepare(torch.float64)
     flops_step = sum(2.0 * p["A"].nnz for p in prep64)
 
@@ -718,136 +892,63 @@ def main():
     step_ms = [sum(times[p["name"]][k] for p in prep64) for k in range(args.steps)]
     total_ms = max_over_ranks(sum(step_ms), ws, dev)
     value = flops_step * args.steps * ws / (total_ms * 1e-3) / 1e9
-    # kernels of one product (one grid, plus the fix-up when there are long
-    # intervals) and the L2-flush copy before it
-    launches_per_step = sum((2 if p["nseg"] > 0 else 1) + 1 for p in prep64)
+    # kernels of one product (as the library reports them) and the L2-flush copy before it
+    launches_per_step = sum(p["M"].launch_count() + 1 for p in prep64)
 
-    # bytes model (algorithmic): values + colidx + masks + block_rowptr + valptr + x + y
-    def beta_bytes(p, vsize, xsize):
-        A, r, c = p["A"], p["r"], p["c"]
-        I = (A.n + r - 1) // r
-        mb = (r * c + 7) // 8
-        return vsize * A.nnz + (4 + mb) * p["nblocks"] + 4 * (I + 1) + 8 * (I + 1) + xsize * A.m + xsize * A.n
+    def roof(p, tlist, key):
+        return roofline_entry(p, tlist, key, hbm_peak, hbm_src, hbm_nominal)
 
-    def csr_bytes(p, vsize, xsize):
-        A = p["A"]
-        return vsize * A.nnz + 4 * A.nnz + 8 * (A.n + 1) + xsize * A.m + xsize * A.n
-
-    per_matrix = []
-    for p in prep64:
-        t = statistics.median(times[p["name"]])
-        per_matrix.append({"matrix": p["name"], "n": p["A"].n, "nnz": p["A"].nnz, "shape": f"{p['r']}x{p['c']}",
-                           "variant": p["variant"],
-                           "avg_nnz_per_block": round(p["A"].nnz / max(p["nblocks"], 1), 3),
-                           "ms": round(t, 4), "gflops": round(2.0 * p["A"].nnz / t / 1e6, 1),
-                           "gbs": round(beta_bytes(p, 8, 8) / t / 1e6, 1), "segments": p["nseg"],
-                           "sweep_gflops": p["sweep_gflops"]})
+    per_matrix = [matrix_entry(p, times[p["name"]], "f64", hbm_peak) for p in prep64]
     dom = max(prep64, key=lambda p: statistics.median(times[p["name"]]))
+    roofline = roof(dom, times[dom["name"]], "f64")
+    # float64 on this GPU is also bounded by its float64 multiply-add rate
     dom_t = statistics.mean(times[dom["name"]])
-    dom_flops = 2.0 * dom["A"].nnz
-    dom_bytes = beta_bytes(dom, 8, 8)
-    hbm_peak = 6682.5
-    try:
-        hbm_peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
-    except Exception:
-        pass
-    # the kernels of one SpMV of the dominant matrix in its tuned form
-    kname = "k_spmv_rows_g" if dom["variant"] == 22 else "k_spmv_rows_u"
-    if dom["nseg"] > 0:
-        kname = "k_spmv_rows_segs+k_spmv_fixup"  # short and long intervals in one grid, then the fix-up
-    roofline = {
-        "bound": "alu", "achieved": round(dom_flops / dom_t / 1e6, 1), "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
-        "frac": round(dom_flops / dom_t / 1e6 / FP64_PEAK_GFLOPS, 4),
-        "traffic": profile_traffic(traffic_key(dom["r"], dom["c"], dom["variant"], "f64", dom["name"])),
-        "kernel": f"{kname}<{dom['r']},{dom['c']},f64> on {dom['name']}",
-        "peak_source": "nominal float64 rate (2 FMA lanes/clk/SM x 152 SMs x 2.07 GHz x 2 = 1.25 TFLOP/s)",
-        "peak_measured": round(fp64_measured, 1), "frac_of_measured": round(dom_flops / dom_t / 1e6 / fp64_measured, 4),
-        "hbm": {"achieved": round(dom_bytes / dom_t / 1e6, 1), "peak": hbm_peak, "unit": "GB/s",
-                "frac": round(dom_bytes / dom_t / 1e6 / hbm_peak, 4), "algorithmic_bytes": int(dom_bytes),
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"},
-    }
+    dom_gflops = 2.0 * dom["A"].nnz / dom_t / 1e6
+    roofline["alu_fp64"] = {
+        "achieved": round(dom_gflops, 1), "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+        "frac": round(dom_gflops / FP64_PEAK_GFLOPS, 4), "peak_measured": round(fp64_measured, 1),
+        "frac_of_measured": round(dom_gflops / fp64_measured, 4),
+        "why": "float64 multiply-adds run at 1/51 of the float32 rate on GB300: 2 flops per stored value need "
+               "nnz/32 float64 warp-instructions, comparable to the HBM time of the value stream",
+        "peak_source": "nominal float64 rate (2 FMA lanes/clk/SM x 152 SMs x 2.07 GHz x 2 = 1.25 TFLOP/s); "
+                       "peak_measured by the library's multiply-add probe in this run"}
 
     # ---- CSR comparator, same protocol
-    csr_times = run_steps(prep64, args.steps, 1, fn_name="csr")
-    csr_ms = sum(sum(v) for v in csr_times.values())
-    csr_value = flops_step * args.steps / (csr_ms * 1e-3) / 1e9
-    csr_per = {p["name"]: {"group": p["csr_group"],
-                           "gflops": round(2.0 * p["A"].nnz / statistics.median(csr_times[p["name"]]) / 1e6, 1),
-                           "gbs": round(csr_bytes(p, 8, 8) / statistics.median(csr_times[p["name"]]) / 1e6, 1)}
-               for p in prep64}
+    csr64 = csr_section(prep64, args.steps, "f64", value)
 
     # ---- end to end: pinned host x -> device, SpMV, y -> pinned host, every step
-    hx = [torch.from_numpy(p["x"].cpu().numpy()).pin_memory() for p in prep64]
-    hy = [torch.empty(p["A"].n, dtype=torch.float64).pin_memory() for p in prep64]
-    h2d = sum(p["A"].m * 8 for p in prep64)
-    d2h = sum(p["A"].n * 8 for p in prep64)
-    # three streams: host->device copies, the products, device->host copies;
-    # events order each matrix's x copy before its product, its product before
-    # its y copy, and keep the next step from overwriting a buffer still in use
-    s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
-    nmat = len(prep64)
-    ev_x = [torch.cuda.Event() for _ in range(nmat)]    # x_j arrived
-    ev_mv = [torch.cuda.Event() for _ in range(nmat)]   # product j done (x_j free, y_j ready)
-    ev_y = [torch.cuda.Event() for _ in range(nmat)]    # y_j copied out (y_j free)
-    for j in range(nmat):  # all "free" at the start
-        ev_mv[j].record(stream)
-        ev_y[j].record(stream)
-
-    def e2e_step():
-        for j, (p, a, b) in enumerate(zip(prep64, hx, hy)):
-            s_in.wait_event(ev_mv[j])
-            with torch.cuda.stream(s_in):
-                p["x"].copy_(a, non_blocking=True)
-            ev_x[j].record(s_in)
-            stream.wait_event(ev_x[j])
-            stream.wait_event(ev_y[j])
-            p["M"].spmv(p["x"], p["y"], stream=stream)
-            ev_mv[j].record(stream)
-            s_out.wait_event(ev_mv[j])
-            with torch.cuda.stream(s_out):
-                b.copy_(p["y"], non_blocking=True)
-            ev_y[j].record(s_out)
-
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    for _ in range(2):
-        e2e_step()
-    torch.cuda.synchronize()
-    e0.record(stream)
-    for _ in range(args.steps):
-        e2e_step()
-    for j in range(nmat):  # the last copies out belong to the timed region
-        stream.wait_event(ev_y[j])
-    e1.record(stream)
-    e1.synchronize()
-    torch.cuda.synchronize()
-    e2e_ms = max_over_ranks(e0.elapsed_time(e1), ws, dev)
-    e2e_value = flops_step * args.steps * ws / (e2e_ms * 1e-3) / 1e9
+    e2e = run_e2e(prep64, args.steps, stream, ws, dev, flops_step)
 
     # ---- learned selector vs the paper-style polynomial on the bench matrices
     sel_res = run_selector_section(prep64, dev)
 
-    # ---- float32 storage form
     # float64 products kept to report the error of the low-precision forms
     y64_ref = {p["name"]: p["M"].spmv(p["x"]).clone() for p in prep64}
     for p in prep64:
         p["M"].destroy()
         del p["d"]
     torch.cuda.empty_cache()
-    prep32 = prepare(torch.float32)
-    t32 = run_steps(prep32, args.steps, 1)
-    ms32 = sum(sum(v) for v in t32.values())
-    f32 = {"value": round(flops_step * args.steps / (ms32 * 1e-3) / 1e9, 1), "unit": "GFLOP/s",
-           "per_matrix": [{"matrix": p["name"], "shape": f"{p['r']}x{p['c']}",
-                           "gflops": round(2.0 * p["A"].nnz / statistics.median(t32[p["name"]]) / 1e6, 1),
-                           "gbs": round(beta_bytes(p, 4, 4) / statistics.median(t32[p["name"]]) / 1e6, 1),
-                           "hbm_frac": round(beta_bytes(p, 4, 4) / statistics.median(t32[p["name"]]) / 1e6 / hbm_peak, 4)}
-                          for p in prep32]}
-    csr32_times = run_steps(prep32, args.steps, 1, fn_name="csr")
-    f32["csr_value"] = round(flops_step * args.steps / (sum(sum(v) for v in csr32_times.values()) * 1e-3) / 1e9, 1)
-    f32["error_vs_float64"] = precision_errors(prep32, y64_ref)
-    for p in prep32:
-        p["M"].destroy()
+
+    # ---- float32 and bfloat16 storage forms (x and y float32, float32 accumulation)
+    low = {}
+    for key, dt in (("f32", torch.float32), ("bf16", torch.bfloat16)):
+        prep = prepare(dt)
+        t = run_steps(prep, args.steps, 1)
+        ms = sum(sum(v) for v in t.values())
+        d = max(prep, key=lambda p: statistics.median(t[p["name"]]))
+        sec = {"value": round(flops_step * args.steps / (ms * 1e-3) / 1e9, 1), "unit": "GFLOP/s",
+               "hbm_gbs": round(sum(beta_bytes(p, *VSIZE[key]) for p in prep) * args.steps / (ms * 1e-3) / 1e9, 1),
+               "per_matrix": [matrix_entry(p, t[p["name"]], key, hbm_peak, roofline=roof(p, t[p["name"]], key))
+                              for p in prep],
+               "roofline": roof(d, t[d["name"]], key)}
+        sec["hbm_frac"] = round(sec["hbm_gbs"] / hbm_peak, 4)
+        sec["csr"] = csr_section(prep, args.steps, key, sec["value"])
+        sec["error_vs_float64"] = precision_errors(prep, y64_ref)
+        for p in prep:
+            p["M"].destroy()
+            del p["d"]
+        torch.cuda.empty_cache()
+        low[key] = sec
 
     # ---- precision form: float64 CG vs mixed-precision refinement, 7-point Poisson 96^3
     cg_res = run_cg_section(dev)
@@ -856,19 +957,7 @@ def main():
     batch_res = run_batch_section(dev)
 
     # ---- CPU baseline: the oracle as it stands, on the host cores, bounded sample
-    cpu = None
-    if rank == 0:
-        import oracle
-
-        reps = 2
-        t0 = time.perf_counter()
-        for _ in range(reps):
-            for p in prep64:
-                oracle.csr_spmv_omp(p["A"], p["x"].cpu().numpy() if hasattr(p["x"], "cpu") else p["x"])
-        dt = time.perf_counter() - t0
-        cpu = {"value": round(flops_step * reps / dt / 1e9, 3), "unit": "GFLOP/s", "cores": oracle.omp_threads(),
-               "kind": "oracle",
-               "sample": f"{reps} passes of the 4 float64 CSR SpMVs (plain loop, OpenMP over rows), full matrices"}
+    cpu = run_cpu_baseline(mats, prep64) if rank == 0 else None
 
     line = {
         "metric": METRIC, "value": round(value, 2), "unit": "GFLOP/s", "n_gpus": ws, "steps": args.steps,
@@ -880,15 +969,13 @@ def main():
                    "l2": f"flushed before every SpMV ({L2_FLUSH_BYTES >> 20} MiB copy, outside the events)",
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
         "hbm_gbs": round(sum(beta_bytes(p, 8, 8) for p in prep64) * args.steps / (total_ms * 1e-3) / 1e9, 1),
-        "roofline": roofline, "cpu_baseline": cpu,
-        "e2e": {"value": round(e2e_value, 2), "unit": "GFLOP/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "pipeline": "pinned host x in and y out every step on two copy streams, overlapping the products "
-                            "(spc5_spmv on the compute stream), L2 not flushed"},
+        "hbm_peak": {"measured_gbs": hbm_peak, "measured_source": hbm_src, "nominal_gbs": round(hbm_nominal, 1),
+                     "nominal_source": "2 x memory clock x bus width (driver attributes)"},
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks, "wall_s_timed": round(wall1 - wall0, 3),
-        "csr": {"value": round(csr_value, 2), "unit": "GFLOP/s", "per_matrix": csr_per,
-                "speedup_beta_over_csr": round(value / csr_value, 3)},
-        "per_matrix": per_matrix, "f32": f32, "cg": cg_res, "spmm_f32": spmm_res, "batch_f32": batch_res, "selector": sel_res,
+        "csr": csr64, "per_matrix": per_matrix, "f32": low["f32"], "bf16": low["bf16"], "cg": cg_res,
+        "spmm_f32": spmm_res, "batch_f32": batch_res, "selector": sel_res,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

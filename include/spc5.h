@@ -210,6 +210,18 @@ spc5_status spc5_spmv_noalloc(spc5_handle h, const void* x_d, void* y_d, spc5_st
  * spc5_destroy). No device work. */
 spc5_status spc5_export(spc5_handle h, spc5_arrays* view);
 
+/* spc5_launch_count - number of kernels one spc5_spmv (or spc5_spmv_acc) on
+ * this handle launches with its current variant: the short-interval grid
+ * (shared with the long-interval segments unless variant 1 runs), a separate
+ * segment kernel otherwise, and the segment fix-up. No device work. */
+spc5_status spc5_launch_count(spc5_handle h, int* kernels_out);
+
+/* spc5_device_peaks - properties of the current device for roofline
+ * reports: the nominal DRAM bandwidth in GB/s (2 transfers per memory clock x
+ * bus width, from the driver's attributes), the SM count and the maximum SM
+ * clock in MHz. Any output pointer may be NULL (not all). No device work. */
+spc5_status spc5_device_peaks(double* hbm_gbs_out, int* sm_count_out, int* sm_clock_mhz_out);
+
 /* spc5_destroy - free the handle and its device arrays (synchronises the
  * device first so that no queued kernel still reads them). NULL is allowed. */
 spc5_status spc5_destroy(spc5_handle h);

@@ -153,6 +153,28 @@ spc5_status spc5_export(spc5_handle h, spc5_arrays* v) {
   return SPC5_OK;
 }
 
+spc5_status spc5_launch_count(spc5_handle h, int* kernels_out) {
+  if (!h || !kernels_out) return fail(SPC5_EINVAL, "launch_count: NULL argument");
+  *kernels_out = spmv_launches(h);
+  return SPC5_OK;
+}
+
+spc5_status spc5_device_peaks(double* hbm_gbs_out, int* sm_count_out, int* sm_clock_mhz_out) {
+  if (!hbm_gbs_out && !sm_count_out && !sm_clock_mhz_out) return fail(SPC5_EINVAL, "device_peaks: no output");
+  int dev = 0, mem_khz = 0, bus_bits = 0, sms = 0, sm_khz = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&mem_khz, cudaDevAttrMemoryClockRate, dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&bus_bits, cudaDevAttrGlobalMemoryBusWidth, dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sm_khz, cudaDevAttrClockRate, dev);
+  if (e != cudaSuccess) return cuda_fail(e, "device_peaks");
+  // double data rate: two transfers of bus_bits per memory clock
+  if (hbm_gbs_out) *hbm_gbs_out = 2.0 * (double)mem_khz * 1e3 * (double)bus_bits / 8.0 / 1e9;
+  if (sm_count_out) *sm_count_out = sms;
+  if (sm_clock_mhz_out) *sm_clock_mhz_out = sm_khz / 1000;
+  return SPC5_OK;
+}
+
 spc5_status spc5_destroy(spc5_handle h) {
   if (!h) return SPC5_OK;
   cudaError_t e = cudaDeviceSynchronize();

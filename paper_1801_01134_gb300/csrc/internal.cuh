@@ -141,4 +141,15 @@ spc5_status cg_impl(const spc5_matrix* A, const spc5_matrix* L, const double* b,
 
 int sm_count();
 
+// The segments and the short intervals share one grid unless the plain
+// variant 1 runs or the matrix has only one kind of work.
+inline bool fused_launch(const spc5_matrix* h) { return h->I > 0 && h->nseg > 0 && h->variant != 1; }
+
+// kernels one spc5_spmv launches on this handle (see launch_beta)
+inline int spmv_launches(const spc5_matrix* h) {
+  int k = h->I > 0 ? 1 : 0;
+  if (h->nseg > 0) k += (fused_launch(h) ? 0 : 1) + 1;  // separate segment kernel, then the fix-up
+  return k;
+}
+
 }  // namespace spc5

@@ -807,7 +807,7 @@ cudaError_t launch_beta(const spc5_matrix* h, const void* xv, void* yv, bool acc
   const bool ordered = ordered_variant(v) && h->norder > 0;
   A* part = static_cast<A*>(partials);
   // segments and short intervals in one launch (not for the plain variant 1)
-  const bool fused = h->I > 0 && h->nseg > 0 && v != 1;
+  const bool fused = fused_launch(h);
   const int64_t seg_ctas = (h->nseg * kWarp + threads - 1) / threads;
   bool rows_done = false;  // the short intervals already launched (G lanes per row)
   if constexpr (R == 1) {

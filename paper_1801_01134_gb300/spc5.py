@@ -101,6 +101,8 @@ def load(build_if_missing: bool = False):
     lib.spc5_fma_rate.argtypes = [i32, i64, vp, vp, vp]
     lib.spc5_fma_rate_lanes.argtypes = [i32, i64, i32, vp, vp, vp]
     lib.spc5_spmv_noalloc.argtypes = [vp, vp, vp, vp]
+    lib.spc5_launch_count.argtypes = [vp, ctypes.POINTER(i32)]
+    lib.spc5_device_peaks.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32), ctypes.POINTER(i32)]
     lib.spc5_cg.argtypes = [vp, vp, vp, vp, ctypes.POINTER(CgOpts), ctypes.POINTER(CgInfo), vp]
     lib.spc5_spmm.argtypes = [vp, i32, vp, i64, vp, i64, i32, vp]
     lib.spc5_features.argtypes = [i64, i64, i64, vp, vp, vp, vp]
@@ -119,7 +121,7 @@ def load(build_if_missing: bool = False):
     lib.spc5_select.argtypes = [i64, i64, i64, vp, vp, vp, i32, i32, ctypes.POINTER(Selector), vp, vp, vp, vp]
     for f in (lib.spc5_convert, lib.spc5_assemble, lib.spc5_autotune, lib.spc5_spmv, lib.spc5_spmv_acc, lib.spc5_export, lib.spc5_destroy, lib.spc5_set_variant,
               lib.spc5_count_blocks, lib.spc5_csr_spmv, lib.spc5_copy, lib.spc5_fma_rate, lib.spc5_fma_rate_lanes,
-              lib.spc5_spmv_noalloc, lib.spc5_cg, lib.spc5_spmm, lib.spc5_features,
+              lib.spc5_spmv_noalloc, lib.spc5_launch_count, lib.spc5_device_peaks, lib.spc5_cg, lib.spc5_spmm, lib.spc5_features,
               lib.spc5_time_formats, lib.spc5_mlp_train, lib.spc5_mlp_grad, lib.spc5_mlp_infer, lib.spc5_poly_fit,
               lib.spc5_select, lib.spc5_batch_create, lib.spc5_batch_spmv, lib.spc5_batch_spmv_direct,
               lib.spc5_batch_destroy, lib.spc5_partition):
@@ -224,6 +226,12 @@ class Matrix:
         _check(load().spc5_set_variant(self._h, variant, _stream_ptr(stream)), "spc5_set_variant")
         self.variant = variant
 
+    def launch_count(self) -> int:
+        """Kernels one spmv() launches with the current variant."""
+        k = ctypes.c_int()
+        _check(load().spc5_launch_count(self._h, ctypes.byref(k)), "spc5_launch_count")
+        return k.value
+
     def arrays(self) -> Arrays:
         a = Arrays()
         _check(load().spc5_export(self._h, ctypes.byref(a)), "spc5_export")
@@ -316,6 +324,13 @@ def count_blocks(rowptr: torch.Tensor, colidx: torch.Tensor, n: int, m: int, str
     _check(load().spc5_count_blocks(n, m, colidx.numel(), _ptr(rowptr), _ptr(colidx), out.ctypes.data,
                                     _stream_ptr(stream)), "spc5_count_blocks")
     return out
+
+
+def device_peaks() -> dict:
+    """Nominal DRAM GB/s, SM count and maximum SM MHz of the current device."""
+    g, sms, mhz = ctypes.c_double(), ctypes.c_int(), ctypes.c_int()
+    _check(load().spc5_device_peaks(ctypes.byref(g), ctypes.byref(sms), ctypes.byref(mhz)), "spc5_device_peaks")
+    return {"hbm_gbs_nominal": g.value, "sm_count": sms.value, "sm_max_mhz": mhz.value}
 
 
 def copy_raw(src_ptr: int, dst_ptr: int, nbytes: int, stream=None):

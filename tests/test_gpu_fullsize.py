@@ -1,0 +1,139 @@
+"""Parity at the benchmarked sizes: the four matrices the bench times, at full size.
+
+The small parity tests never reach several paths that only large inputs take:
+the multi-step scan of the tile sums (more than 4096 tiles of 2048 counts, e.g.
+the r = 1 block numbering over the 162 M entries of the FEM matrix), the
+fix-up's warp path for long intervals of more than 32 segments (R-MAT hubs of
+~10^5 entries), and the segment + short-interval grid at hundreds of thousands
+of segments. Here every conversion is compared with the oracle bit for bit,
+float64 products with the compensated oracle within 1e-13 (|A||x|)_i, and the
+float32 / bfloat16 storage forms with an oracle fed the same rounded values
+within gamma_{L_i+1} (|A||x|)_i (u = 2^-24, L_i = row length), for the block
+shapes and kernel variants the bench selects and the default variant.
+
+Matrices (section "Test matrices" stand-ins; values N(0,1) seed 1, x uniform
+[-1,1] seed 0): 27-point stencil 128^3, 3x3-block FEM n = 3e6, R-MAT scale 22,
+uniform n = 1e6 with 8 entries per row.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1801_01134_gb300 import inputs, spc5
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-13
+U32 = 2.0**-24
+
+# (r, c, variant) per matrix and value type: the bench's tuned choices, the
+# default decode and a second shape
+CASES = {
+    "stencil27_128^3": {"f64": [(4, 8, 5), (4, 8, 15), (2, 4, 5)], "f32": [(2, 4, 18), (4, 8, 16)],
+                        "bf16": [(2, 4, 18), (4, 8, 5)]},
+    "fem3x3_n3M": {"f64": [(1, 8, 22), (1, 8, 5), (4, 4, 5)], "f32": [(1, 4, 16), (1, 8, 22)],
+                   "bf16": [(1, 8, 22), (2, 8, 18)]},
+    "rmat_s22": {"f64": [(1, 4, 15), (1, 4, 5), (1, 8, 13)], "f32": [(1, 4, 15), (1, 8, 22)],
+                 "bf16": [(1, 4, 15)]},
+    "uniform_n1M": {"f64": [(1, 4, 22), (1, 4, 5)], "f32": [(1, 4, 22), (1, 4, 16)], "bf16": [(1, 4, 16)]},
+}
+
+
+def _make(name):
+    if name == "stencil27_128^3":
+        return inputs.stencil3d(128, 128, 128, points=27, seed=1)
+    if name == "fem3x3_n3M":
+        return inputs.block_fem(1000000, bs=3, bmin=9, bmax=27, band_frac=0.05, seed=1)
+    if name == "rmat_s22":
+        return inputs.rmat(22, 16, 0.57, 0.19, 0.19, relabel=True, seed=1)
+    return inputs.uniform(1000000, 1000000, 8, seed=1)
+
+
+@pytest.fixture(scope="module", params=list(CASES))
+def full(request, cuda_device):
+    A = _make(request.param)
+    x = inputs.vec_uniform(A.m, seed=0)
+    yield request.param, A, x
+    torch.cuda.empty_cache()
+
+
+def _rounded(A, kind):
+    vals = oracle.round_f32(A.values) if kind == "f32" else oracle.round_bf16(A.values)
+    return inputs.CSR(A.n, A.m, A.rowptr, A.colidx, vals)
+
+
+def _check_convert(M, B, rowptr, raw_values):
+    got = M.export()
+    assert got["nblocks"] == B.nblocks
+    assert np.array_equal(got["block_rowptr"], B.block_rowptr)
+    assert np.array_equal(got["block_colidx"], B.block_colidx)
+    assert np.array_equal(got["block_masks"], B.block_masks)
+    assert np.array_equal(got["values_raw"], raw_values)
+    assert np.array_equal(got["valptr"], B.valptr(rowptr))
+    return got
+
+
+def test_float64_convert_and_spmv(full):
+    name, A, x = full
+    y_ref, absy = oracle.csr_spmv_dot2(A, x)
+    d = spc5.upload_csr(A, torch.float64, "cuda")
+    xd = torch.from_numpy(x).cuda()
+    checked = set()
+    for r, c, v in CASES[name]["f64"]:
+        M = spc5.convert(d.rowptr, d.colidx, d.values, A.n, A.m, r, c, variant=v)
+        if (r, c) not in checked:
+            B = oracle.beta_convert(A, r, c)
+            got = _check_convert(M, B, A.rowptr, B.values.view(np.uint64))
+            if name == "rmat_s22" and r == 1:
+                # hubs: intervals with more than 32 segments of 384 blocks take the fix-up's warp path
+                assert got["nsegments"] > 0 and int(np.diff(B.block_rowptr).max()) > 32 * 384
+            del B
+            checked.add((r, c))
+        buf = torch.full((A.n + 64,), float("nan"), dtype=torch.float64, device="cuda")
+        M.spmv(xd, buf[:A.n])
+        y = buf[:A.n].cpu().numpy()
+        err = np.abs(y - y_ref)
+        bad = err > TOL64 * absy
+        assert not bad.any(), f"beta({r},{c}) variant {v}: {bad.sum()} rows over 1e-13 (|A||x|)_i"
+        assert np.all(y[absy == 0] == 0)
+        assert torch.isnan(buf[A.n:]).all(), "wrote past the end of y"
+        M.destroy()
+    del d
+
+
+@pytest.mark.parametrize("kind", ["f32", "bf16"])
+def test_low_precision_convert_and_spmv(full, kind):
+    name, A, x = full
+    Ar = _rounded(A, kind)
+    xr = oracle.round_f32(x)
+    y_ref, absy = oracle.csr_spmv_dot2(Ar, xr)
+    vdt = torch.float32 if kind == "f32" else torch.bfloat16
+    vals = torch.from_numpy(Ar.values).to(vdt)
+    rowptr = torch.from_numpy(np.ascontiguousarray(A.rowptr)).cuda()
+    colidx = torch.from_numpy(np.ascontiguousarray(A.colidx)).cuda()
+    vd = vals.cuda()
+    xd = torch.from_numpy(xr).float().cuda()
+    L = np.diff(A.rowptr).astype(np.float64)
+    bound = (L + 1) * U32 / (1 - (L + 1) * U32) * absy
+    checked = set()
+    for r, c, v in CASES[name][kind]:
+        M = spc5.convert(rowptr, colidx, vd, A.n, A.m, r, c, variant=v)
+        if (r, c) not in checked:
+            # the block structure depends only on the pattern; the values move as they are
+            B = oracle.beta_convert(A, r, c)
+            got = M.export()
+            assert np.array_equal(got["block_colidx"], B.block_colidx)
+            assert np.array_equal(got["block_masks"], B.block_masks)
+            assert np.array_equal(got["block_rowptr"], B.block_rowptr)
+            Br = oracle.beta_convert(Ar, r, c)
+            want = torch.from_numpy(Br.values).to(vdt)
+            want = want.view(torch.int32 if kind == "f32" else torch.int16).numpy()
+            assert np.array_equal(got["values_raw"].view(want.dtype), want)
+            del B, Br
+            checked.add((r, c))
+        y = M.spmv(xd).double().cpu().numpy()
+        err = np.abs(y - y_ref)
+        bad = err > bound + 1e-45
+        assert not bad.any(), f"{kind} beta({r},{c}) variant {v}: {bad.sum()} rows over gamma_(L+1) (|A||x|)_i"
+        M.destroy()

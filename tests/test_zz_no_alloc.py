@@ -25,33 +25,37 @@ def _call_noalloc(M, x, y):
     assert st == spc5.OK, spc5.last_error()
 
 
-@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32, torch.bfloat16])
 def test_noalloc_matches_spmv_two_calls_in_a_row(cuda_device, dtype):
+    # two matrices whose segment scratch differs in size and layout (8 rows per
+    # interval, then 1), called alternately: whatever one call leaves in the
+    # shared array must not show in the next. The kernels are those of
+    # spc5_spmv with only the scratch address changed, so the results must be
+    # the same bits.
     A = inputs.rmat(11, seed=2)
-    d = spc5.upload_csr(A, dtype, "cuda")
-    # every interval with more than one block goes through the segment path,
-    # so the fixed scratch array is exercised
-    M = spc5.convert(d.rowptr, d.colidx, d.values, A.n, A.m, 1, 8, long_blocks=1, seg_blocks=3)
-    assert M.export()["nsegments"] > 0
+    B = inputs.stencil3d(9, 8, 7, points=27, seed=3)
+    da = spc5.upload_csr(A, dtype, "cuda")
+    db = spc5.upload_csr(B, dtype, "cuda")
+    # every interval with more than one block goes through the segment path
+    Ma = spc5.convert(da.rowptr, da.colidx, da.values, A.n, A.m, 8, 4, long_blocks=1, seg_blocks=2)
+    Mb = spc5.convert(db.rowptr, db.colidx, db.values, B.n, B.m, 1, 8, long_blocks=1, seg_blocks=1)
+    na, nb = Ma.export()["nsegments"], Mb.export()["nsegments"]
+    assert na > 0 and nb > 0 and na * 8 != nb
     xdt = torch.float64 if dtype == torch.float64 else torch.float32
-    for seed in (0, 1):  # two calls in a row, different inputs
-        xh = inputs.vec_uniform(A.m, seed=seed)
-        x = torch.from_numpy(xh).to(xdt).cuda()
-        y_ref = M.spmv(x)
-        y = torch.full((A.n,), float("nan"), dtype=xdt, device="cuda")
-        _call_noalloc(M, x, y)
-        torch.cuda.synchronize()
-        a, b = y.double().cpu().numpy(), y_ref.double().cpu().numpy()
-        if dtype == torch.float64:
-            # the test suite's float64 tolerance, against the existing entry point and the oracle
-            ref, absy = oracle.csr_spmv_dot2(A, xh)
-            assert np.all(np.abs(a - b) <= 1e-13 * absy)
-            assert np.all(np.abs(a - ref) <= 1e-13 * absy)
-        else:
-            L = np.diff(A.rowptr).astype(np.float64)
-            absy = oracle.csr_spmv_dot2(A, xh)[1]
-            assert np.all(np.abs(a - b) <= 2 * (L + 1) * 2.0**-24 * absy + 1e-30)
-    M.destroy()
+    for seed in (0, 1):  # two calls in a row per matrix, different inputs
+        for M, Acsr in ((Ma, A), (Mb, B)):
+            xh = inputs.vec_uniform(Acsr.m, seed=seed)
+            x = torch.from_numpy(xh).to(xdt).cuda()
+            y_ref = M.spmv(x)
+            y = torch.full((Acsr.n,), float("nan"), dtype=xdt, device="cuda")
+            _call_noalloc(M, x, y)
+            torch.cuda.synchronize()
+            assert torch.equal(y, y_ref)
+            if dtype == torch.float64:
+                ref, absy = oracle.csr_spmv_dot2(Acsr, xh)
+                assert np.all(np.abs(y.cpu().numpy() - ref) <= 1e-13 * absy)
+    Ma.destroy()
+    Mb.destroy()
 
 
 def test_noalloc_rejects_oversized_scratch(cuda_device):
