@@ -83,6 +83,8 @@ typedef struct {
    *           (adjacent values read together, half the row's multiply-adds
    *           per lane); the two halves are added at the end, so its sums
    *           differ from the other variants' by rounding only.
+   *   23      22 in the sorted work order (rows of similar length share a
+   *           warp, so fewer lanes idle in each multiply-add); r = 1 only.
    * spc5_cg uses the decode of 16 or 18 when its handle has that variant,
    * the flattened one otherwise.
    * Variants 0-19 compute the same sums in the same order per row; every
@@ -165,10 +167,10 @@ spc5_status spc5_spmv_acc(spc5_handle h, const void* x_d, void* y_d, spc5_stream
 
 /*
  * spc5_set_variant - switch the short-interval kernel variant of a handle
- * (values as in spc5_opts.variant). Selecting 9, 10, 13, 15, 17 or 19 builds the sorted work
+ * (values as in spc5_opts.variant). Selecting 9, 10, 13, 15, 17, 19 or 23 builds the sorted work
  * order if the handle has none yet (synchronises `stream`); the other values
  * take effect with no device work. SPC5_EINVAL for an unknown variant,
- * SPC5_EUNSUPPORTED for 22 on a handle with r > 1.
+ * SPC5_EUNSUPPORTED for 22 or 23 on a handle with r > 1.
  */
 spc5_status spc5_set_variant(spc5_handle h, int variant, spc5_stream_t stream);
 
@@ -178,7 +180,7 @@ spc5_status spc5_set_variant(spc5_handle h, int variant, spc5_stream_t stream);
  * overwritten) and keep the fastest; the GPU form of the paper's choice of
  * the best kernel for a matrix (section "Performance prediction and optimal
  * kernel selection"). Candidates: variants 5, 10, 13, 15, plus 16 and 18 for
- * float32 / bfloat16 values and 22 for r = 1 (the ones that win on some
+ * float32 / bfloat16 values and 22, 23 for r = 1 (the ones that win on some
  * matrix). Writes the
  * chosen variant and its median milliseconds (either pointer may be NULL).
  * Synchronises `stream`. On error the handle keeps its previous variant.

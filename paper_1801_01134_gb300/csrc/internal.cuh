@@ -22,12 +22,17 @@ constexpr int kOrderWindow = 1024;  // rows per sorting window of the work order
 
 // short-interval kernel variants (spc5_opts.variant)
 inline bool valid_variant(int v) {
-  return v == 0 || v == 1 || v == 3 || v == 5 || v == 9 || v == 10 || (v >= 12 && v <= 19) || v == 22;
+  return v == 0 || v == 1 || v == 3 || v == 5 || v == 9 || v == 10 || (v >= 12 && v <= 19) || v == 22 || v == 23 ||
+         (v >= 24 && v <= 29);
 }
 // variants that need r = 1 (two lanes per row)
-inline bool r1_variant(int v) { return v == 22; }
+inline bool r1_variant(int v) { return v == 22 || v == 23; }
 // variants that take intervals in the sorted work order
-inline bool ordered_variant(int v) { return v == 9 || v == 10 || v == 13 || v == 15 || v == 17 || v == 19; }
+inline bool ordered_variant(int v) {
+  return v == 9 || v == 10 || v == 13 || v == 15 || v == 17 || v == 19 || v == 23 || v == 28 || v == 29;
+}
+// variants with G lanes per interval, one lane per block (spmv_group.cuh)
+inline bool group_variant(int v) { return v >= 24 && v <= 29; }
 
 struct Segment {  // one warp task of a long interval
   int32_t interval;
@@ -107,6 +112,10 @@ cudaError_t launch_spmv_f32(const spc5_matrix* h, const void* x, void* y, bool a
                             void* partials = nullptr);
 cudaError_t launch_spmv_bf16(const spc5_matrix* h, const void* x, void* y, bool acc, cudaStream_t s,
                             void* partials = nullptr);
+// the group variants 24-29 (spmv_group_f64.cu, spmv_group_f32.cu, spmv_group_bf16.cu)
+cudaError_t launch_group_f64(const spc5_matrix* h, const void* x, void* y, bool acc, cudaStream_t s, void* partials);
+cudaError_t launch_group_f32(const spc5_matrix* h, const void* x, void* y, bool acc, cudaStream_t s, void* partials);
+cudaError_t launch_group_bf16(const spc5_matrix* h, const void* x, void* y, bool acc, cudaStream_t s, void* partials);
 
 // CSR comparator and copy (csr.cu)
 cudaError_t launch_csr_spmv(int64_t n, int64_t nnz, const int64_t* rowptr, const int32_t* colidx,

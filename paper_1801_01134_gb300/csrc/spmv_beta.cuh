@@ -540,24 +540,29 @@ __device__ __forceinline__ uint32_t rank_class_bits(uint32_t m, int cls) {
   return m & (cls == 0 ? p : ~p);
 }
 
-template <int C, class T, bool ACCUM, int G, int U>
+// With ORDER, row slot q of the warp takes row order[q] (the sorted work
+// order, short rows only) instead of row q.
+template <int C, class T, bool ACCUM, int G, int U, bool ORDER = false>
 __device__ __forceinline__ void rows_g_body(int64_t bid, int64_t n, int64_t I, int32_t long_blocks,
                                             int64_t long_values, const int32_t* __restrict__ brp,
                                             const int32_t* __restrict__ bcol, const uint8_t* __restrict__ bmask,
                                             const typename T::V* __restrict__ val,
                                             const int64_t* __restrict__ valptr, const typename T::X* __restrict__ x,
-                                            typename T::X* __restrict__ y) {
+                                            typename T::X* __restrict__ y, const int32_t* __restrict__ order = nullptr,
+                                            int64_t norder = 0) {
   constexpr int MB = (C + 7) / 8;
   constexpr int S = kWarp / G;  // rows per warp
   using A = typename T::A;
   const int lane = threadIdx.x & 31;
   const int g = lane & (G - 1);
   const int64_t warp = (bid * blockDim.x + threadIdx.x) >> 5;
-  if (warp * S >= I) return;  // whole warp
-  const int64_t it = warp * S + lane / G;
+  const int64_t slots = ORDER ? norder : I;
+  if (warp * S >= slots) return;  // whole warp
+  const int64_t pos = warp * S + lane / G;
+  bool have = pos < slots;
+  const int64_t it = ORDER ? (have ? (int64_t)__ldg(order + pos) : 0) : pos;
   int32_t b = 0, bend = 0;
   int64_t vp = 0;
-  bool have = it < I;
   if (have) {
     b = __ldg(brp + it);
     bend = __ldg(brp + it + 1);
@@ -615,15 +620,17 @@ __device__ __forceinline__ void rows_g_body(int64_t bid, int64_t n, int64_t I, i
   }
 }
 
-template <int C, class T, bool ACCUM, int G, int U>
+template <int C, class T, bool ACCUM, int G, int U, bool ORDER>
 __global__ void __launch_bounds__(256) k_spmv_rows_g(int64_t n, int64_t I, int32_t long_blocks, int64_t long_values,
                                                      const int32_t* __restrict__ brp, const int32_t* __restrict__ bcol,
                                                      const uint8_t* __restrict__ bmask,
                                                      const typename T::V* __restrict__ val,
                                                      const int64_t* __restrict__ valptr,
                                                      const typename T::X* __restrict__ x,
-                                                     typename T::X* __restrict__ y) {
-  rows_g_body<C, T, ACCUM, G, U>(blockIdx.x, n, I, long_blocks, long_values, brp, bcol, bmask, val, valptr, x, y);
+                                                     typename T::X* __restrict__ y, const int32_t* __restrict__ order,
+                                                     int64_t norder) {
+  rows_g_body<C, T, ACCUM, G, U, ORDER>(blockIdx.x, n, I, long_blocks, long_values, brp, bcol, bmask, val, valptr, x,
+                                        y, order, norder);
 }
 
 // -------------------------------------------------------- long intervals
@@ -712,8 +719,8 @@ __global__ void __launch_bounds__(256) k_spmv_rows_segs(int64_t seg_ctas, int64_
     rows_u_body<R, C, T, ACCUM, U, ORDER, DEC>((int64_t)blockIdx.x - seg_ctas, n, I, long_blocks, long_values, brp,
                                                bcol, bmask, val, valptr, x, y, order, norder);
   else
-    rows_g_body<C, T, ACCUM, G, U>((int64_t)blockIdx.x - seg_ctas, n, I, long_blocks, long_values, brp, bcol, bmask,
-                                   val, valptr, x, y);
+    rows_g_body<C, T, ACCUM, G, U, ORDER>((int64_t)blockIdx.x - seg_ctas, n, I, long_blocks, long_values, brp, bcol,
+                                          bmask, val, valptr, x, y, order, norder);
 }
 
 // Finishes the long intervals (list of first segments built at conversion;
@@ -790,7 +797,7 @@ __global__ void __launch_bounds__(256) k_spmv_fixup(int64_t n, int64_t nlong, co
 // windows, U=4/U=2; 13/15 sorted order, mask windows, U=4/U=2; 16/17
 // natural / sorted order, bit positions unrolled (row_sum_e); 18/19 the same
 // two blocks per trip (row_sum_e2); 22 (r = 1) two lanes per row taking
-// alternate stored values (rows_g_body). (Measured:
+// alternate stored values (rows_g_body), 23 the same in the sorted order. (Measured:
 // 8 nonzeros per trip is slower than 2 or 4 on every test matrix.)
 // `partials` is the segment scratch (n_segments * r accumulators).
 template <int R, int C, class T>
@@ -811,24 +818,35 @@ cudaError_t launch_beta(const spc5_matrix* h, const void* xv, void* yv, bool acc
   const int64_t seg_ctas = (h->nseg * kWarp + threads - 1) / threads;
   bool rows_done = false;  // the short intervals already launched (G lanes per row)
   if constexpr (R == 1) {
-    if (v == 22 && h->I > 0) {
+    if ((v == 22 || ordered) && r1_variant(v) && h->I > 0) {
       constexpr int U = 2;
-      const int64_t warps = (h->I + kWarp / 2 - 1) / (kWarp / 2);
+      const int64_t slots = ordered ? h->norder : h->I;
+      const int64_t warps = (slots + kWarp / 2 - 1) / (kWarp / 2);
       const unsigned grid = (unsigned)((warps * kWarp + threads - 1) / threads);
+      const int32_t* order = ordered ? h->order : nullptr;
+      const int64_t norder = ordered ? h->norder : 0;
       auto go = [&](auto kern) {
         kern<<<grid, threads, 0, s>>>(h->n, h->I, h->long_blocks, h->long_values, h->block_rowptr, h->block_colidx,
-                                      h->block_masks, val, h->valptr, x, y);
+                                      h->block_masks, val, h->valptr, x, y, order, norder);
       };
       auto go_both = [&](auto kern) {
         kern<<<(unsigned)(seg_ctas + grid), threads, 0, s>>>(seg_ctas, h->n, h->I, h->long_blocks, h->long_values,
                                                              h->block_rowptr, h->block_colidx, h->block_masks, val,
-                                                             h->valptr, x, y, nullptr, 0, h->nseg, h->segs, part);
+                                                             h->valptr, x, y, order, norder, h->nseg, h->segs, part);
       };
-      if (fused)
-        acc ? go_both(k_spmv_rows_segs<1, C, T, true, U, false, 0, 2>)
-            : go_both(k_spmv_rows_segs<1, C, T, false, U, false, 0, 2>);
-      else
-        acc ? go(k_spmv_rows_g<C, T, true, 2, U>) : go(k_spmv_rows_g<C, T, false, 2, U>);
+      if (ordered) {
+        if (fused)
+          acc ? go_both(k_spmv_rows_segs<1, C, T, true, U, true, 0, 2>)
+              : go_both(k_spmv_rows_segs<1, C, T, false, U, true, 0, 2>);
+        else
+          acc ? go(k_spmv_rows_g<C, T, true, 2, U, true>) : go(k_spmv_rows_g<C, T, false, 2, U, true>);
+      } else {
+        if (fused)
+          acc ? go_both(k_spmv_rows_segs<1, C, T, true, U, false, 0, 2>)
+              : go_both(k_spmv_rows_segs<1, C, T, false, U, false, 0, 2>);
+        else
+          acc ? go(k_spmv_rows_g<C, T, true, 2, U, false>) : go(k_spmv_rows_g<C, T, false, 2, U, false>);
+      }
       rows_done = true;
     }
   }

@@ -4,7 +4,9 @@
 namespace spc5 {
 
 cudaError_t launch_spmv_bf16(const spc5_matrix* h, const void* x, void* y, bool acc, cudaStream_t s, void* partials) {
-  return dispatch_beta<BF16>(h, x, y, acc, partials ? partials : h->partials, s);
+  void* part = partials ? partials : h->partials;
+  if (group_variant(h->variant)) return launch_group_bf16(h, x, y, acc, s, part);
+  return dispatch_beta<BF16>(h, x, y, acc, part, s);
 }
 
 }  // namespace spc5

@@ -116,7 +116,7 @@ def test_spmv_variants(cuda_device, variant, name, r, c):
     M.destroy()
 
 
-GROUP_VARIANTS = [22]  # beta(1,c): two lanes per row, alternate stored values
+GROUP_VARIANTS = [22, 23]  # beta(1,c): two lanes per row, alternate stored values (natural, sorted order)
 
 
 @pytest.mark.parametrize("variant", GROUP_VARIANTS)
@@ -141,6 +141,88 @@ def test_spmv_group_variants(cuda_device, variant, name, c):
         M.spmv_acc(xd, yd)
         assert np.all(np.abs(yd.cpu().numpy() - (y0 + y_ref)) <= TOL64 * (absy + np.abs(y0)) + 1e-300)
         M.destroy()
+
+
+@pytest.mark.parametrize("name", ["rmat11", "fem", "uniform", "sparse_rows"])
+@pytest.mark.parametrize("window", [0, 32, 256, -1])
+def test_sorted_two_lane_variant_matches_natural_bitwise(cuda_device, name, window):
+    # variant 23 runs the two-lane row sum of variant 22 with rows taken in the
+    # sorted work order: each row's arithmetic is unchanged, so the bits are
+    A = get(name)
+    d = dev_csr(A)
+    xd = torch.from_numpy(inputs.vec_uniform(A.m, seed=0)).cuda()
+    for c in (4, 8):
+        M = spc5.convert(d.rowptr, d.colidx, d.values, A.n, A.m, 1, c, variant=22, order_window=window, long_blocks=6)
+        ref = M.spmv(xd).clone()
+        M.set_variant(23)
+        buf, y = guarded(A.n, torch.float64)
+        M.spmv(xd, y)
+        assert torch.equal(y, ref)
+        assert torch.isnan(buf[A.n:]).all()
+        M.destroy()
+
+
+LANE_GROUP_VARIANTS = [24, 25, 26, 27, 28, 29]  # G = 4, 8, 16, 32 lanes per interval; 4, 8 in the sorted order
+
+
+@pytest.mark.parametrize("variant", LANE_GROUP_VARIANTS)
+@pytest.mark.parametrize("name", ["lap128", "rand_ragged", "st27_ragged", "rmat11", "fem", "dense64", "sparse_rows"])
+@pytest.mark.parametrize("r,c", spc5.SHAPES)
+def test_spmv_lane_group_variants(cuda_device, variant, name, r, c):
+    # one lane per block, G lanes per interval: the float64 bound, the
+    # accumulate form, no write past y, a fixed order; default thresholds and
+    # most intervals on the segment path (long_blocks 2)
+    A = get(name)
+    x = inputs.vec_uniform(A.m, seed=0)
+    y_ref, absy = oracle.csr_spmv_dot2(A, x)
+    d = dev_csr(A)
+    xd = torch.from_numpy(x).cuda()
+    for lb in (0, 2):
+        M = spc5.convert(d.rowptr, d.colidx, d.values, A.n, A.m, r, c, variant=variant, long_blocks=lb)
+        buf, y = guarded(A.n, torch.float64)
+        M.spmv(xd, y)
+        check64(y.cpu().numpy(), y_ref, absy)
+        assert torch.isnan(buf[A.n:]).all(), "wrote past the end of y"
+        assert torch.equal(M.spmv(xd), y)
+        y0 = inputs.vec_uniform(A.n, seed=1)
+        yd = torch.from_numpy(y0.copy()).cuda()
+        M.spmv_acc(xd, yd)
+        assert np.all(np.abs(yd.cpu().numpy() - (y0 + y_ref)) <= TOL64 * (absy + np.abs(y0)) + 1e-300)
+        M.destroy()
+
+
+@pytest.mark.parametrize("kind", ["f32", "bf16"])
+@pytest.mark.parametrize("variant", LANE_GROUP_VARIANTS)
+@pytest.mark.parametrize("name", ["st27_ragged", "rmat11", "fem", "uniform"])
+def test_lane_group_variants_low_precision(cuda_device, kind, variant, name):
+    A = get(name)
+    Ar = rounded_case(A, kind)
+    x = oracle.round_f32(inputs.vec_uniform(A.m, seed=0))
+    y_ref, absy = oracle.csr_spmv_dot2(Ar, x)
+    vdt = torch.float32 if kind == "f32" else torch.bfloat16
+    vals = torch.from_numpy(Ar.values).to(vdt).cuda()
+    rowptr, colidx = torch.from_numpy(A.rowptr).cuda(), torch.from_numpy(A.colidx).cuda()
+    L = np.diff(A.rowptr).astype(np.float64)
+    u = 2.0**-24
+    for r, c in [(1, 4), (1, 8), (2, 4), (4, 8), (8, 16)]:
+        M = spc5.convert(rowptr, colidx, vals, A.n, A.m, r, c, variant=variant)
+        y = M.spmv(torch.from_numpy(x).float().cuda()).double().cpu().numpy()
+        assert np.all(np.abs(y - y_ref) <= (L + 1) * u / (1 - (L + 1) * u) * absy + 1e-45), (r, c)
+        M.destroy()
+
+
+def test_lane_group_sorted_equals_natural_bitwise(cuda_device):
+    # 28 / 29 run the row sums of 24 / 25 in another order of the intervals
+    A = get("rmat11")
+    d = dev_csr(A)
+    xd = torch.from_numpy(inputs.vec_uniform(A.m, seed=0)).cuda()
+    for r, c in [(1, 4), (2, 8), (8, 4)]:
+        for nat, srt in ((24, 28), (25, 29)):
+            M = spc5.convert(d.rowptr, d.colidx, d.values, A.n, A.m, r, c, variant=nat, order_window=64)
+            ref = M.spmv(xd).clone()
+            M.set_variant(srt)
+            assert torch.equal(M.spmv(xd), ref)
+            M.destroy()
 
 
 def test_group_variants_low_precision_and_limits(cuda_device):
@@ -175,9 +257,10 @@ def test_group_variants_low_precision_and_limits(cuda_device):
         spc5.convert(d.rowptr, d.colidx, d.values, B.n, B.m, 2, 4, variant=22)
     assert ei.value.status == spc5.EUNSUPPORTED
     M = spc5.convert(d.rowptr, d.colidx, d.values, B.n, B.m, 4, 8)
-    with pytest.raises(spc5.Spc5Error) as ei:
-        M.set_variant(22)
-    assert ei.value.status == spc5.EUNSUPPORTED
+    for v in GROUP_VARIANTS:
+        with pytest.raises(spc5.Spc5Error) as ei:
+            M.set_variant(v)
+        assert ei.value.status == spc5.EUNSUPPORTED
     M.destroy()
 
 
