@@ -39,8 +39,9 @@ L2_FLUSH_BYTES = 512 << 20
 FP64_PEAK_GFLOPS = 1250.0  # nominal GB300 float64 rate (2 FMA lanes/clk/SM x 152 SMs x 2.07 GHz x 2)
 # short-interval kernel variants the tuner tries per shape: float64 keeps to the
 # flattened decodes (16's unrolled positions cost float64 pipe slots when empty)
-VARIANTS = {"f64": (5, 10, 13, 15, 24, 25, 26, 27, 28, 29), "f32": (5, 10, 13, 15, 16, 18, 24, 25, 26, 27, 28, 29)}
-GROUP_VARIANTS = (22, 23)  # beta(1,c) only: two lanes per row (natural, sorted order)
+VARIANTS = {"f64": (5, 10, 13, 15, 24), "f32": (5, 10, 13, 15, 16, 18, 24, 28)}
+# beta(1,c) only: two lanes per row (natural, sorted order), Algorithm 2's single-value test (sorted, natural)
+GROUP_VARIANTS = (22, 23, 30, 31)
 CG_INNER_VARIANT = 18  # decode of the float32 / bfloat16 inner CG handle (unrolled positions, two blocks a trip)
 
 

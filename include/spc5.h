@@ -85,10 +85,20 @@ typedef struct {
    *           differ from the other variants' by rounding only.
    *   23      22 in the sorted work order (rows of similar length share a
    *           warp, so fewer lanes idle in each multiply-add); r = 1 only.
+   *   24-27   G = 4 / 8 / 16 / 32 lanes per interval, one lane per block:
+   *           the group reads G consecutive masks and column indices, a scan
+   *           of their popcounts places each block's values, a shuffle tree
+   *           adds the row sums (sums differ from 0-19 by rounding only);
+   *   28 / 29 24 / 25 in the sorted work order.
+   *   30 / 31 r = 1 only: Algorithm 2's single-value test, made once per
+   *           row (a class bit built when the variant is selected): a row
+   *           whose blocks all hold one value is read like CSR (no mask
+   *           decode), other rows with the mask windows; sorted / natural
+   *           order. Same sums as 0-19.
    * spc5_cg uses the decode of 16 or 18 when its handle has that variant,
    * the flattened one otherwise.
-   * Variants 0-19 compute the same sums in the same order per row; every
-   * variant repeats its own results bit for bit. */
+   * Variants 0-19, 30 and 31 compute the same sums in the same order per
+   * row; every variant repeats its own results bit for bit. */
   int32_t variant;
   /* Rows per sorting window of the work order of the sorted variants:
    * 0 selects 1024; a negative value sorts all intervals together. */
@@ -167,10 +177,11 @@ spc5_status spc5_spmv_acc(spc5_handle h, const void* x_d, void* y_d, spc5_stream
 
 /*
  * spc5_set_variant - switch the short-interval kernel variant of a handle
- * (values as in spc5_opts.variant). Selecting 9, 10, 13, 15, 17, 19 or 23 builds the sorted work
- * order if the handle has none yet (synchronises `stream`); the other values
- * take effect with no device work. SPC5_EINVAL for an unknown variant,
- * SPC5_EUNSUPPORTED for 22 or 23 on a handle with r > 1.
+ * (values as in spc5_opts.variant). Selecting 9, 10, 13, 15, 17, 19, 23, 28, 29 or 30
+ * builds the sorted work order, and 30 or 31 the single-value class bits, if
+ * the handle has none yet (synchronises `stream`); the other values take
+ * effect with no device work. SPC5_EINVAL for an unknown variant,
+ * SPC5_EUNSUPPORTED for 22, 23, 30 or 31 on a handle with r > 1.
  */
 spc5_status spc5_set_variant(spc5_handle h, int variant, spc5_stream_t stream);
 

@@ -630,6 +630,7 @@ void count_r(int r, int64_t n, int64_t I, int c, const int64_t* rowptr, const in
 void free_matrix(spc5_matrix* h) {
   if (!h) return;
   cudaFree(h->order);
+  cudaFree(h->single_bits);
   cudaFree(h->spmm_scratch);
   cudaFree(h->block_rowptr);
   cudaFree(h->seg_first);
@@ -727,6 +728,36 @@ void launch_order_key(int c, const spc5_matrix* h, int32_t* key, cudaStream_t s)
   }
 }
 
+// Algorithm 2's test made once per interval (r = 1): bit it is set when
+// every block of short interval it holds a single value. Under greedy
+// leftmost cover a single-value block of one row has mask 1 (its value sits
+// at the block's first column), so such a row reads like CSR: value j of the
+// row belongs to block b0 + j at column block_colidx[b0 + j]. One warp forms
+// each 32-interval word with a ballot; the count of set bits goes to *nset.
+template <int MB>
+__global__ void k_single_bits(int64_t I, int32_t long_blocks, int64_t long_values, const int32_t* __restrict__ brp,
+                              const uint8_t* __restrict__ masks, const int64_t* __restrict__ valptr,
+                              uint32_t* __restrict__ bits, unsigned long long* __restrict__ nset) {
+  const int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  bool one = false;
+  if (it < I) {
+    const int32_t b0 = brp[it], b1 = brp[it + 1];
+    const bool lng = b1 - b0 > long_blocks || valptr[it + 1] - valptr[it] > long_values;
+    // a single-value row has as many values as blocks; then every mask is 1
+    one = !lng && b1 > b0 && valptr[it + 1] - valptr[it] == (int64_t)(b1 - b0);
+    for (int32_t b = b0; one && b < b1; ++b) {
+      uint32_t w = masks[(int64_t)b * MB];
+      if (MB == 2) w |= (uint32_t)masks[(int64_t)b * MB + 1] << 8;
+      one = w == 1u;
+    }
+  }
+  const unsigned word = __ballot_sync(0xffffffffu, one);
+  if ((threadIdx.x & 31) == 0 && it < I) {
+    bits[it >> 5] = word;
+    atomicAdd(nset, (unsigned long long)__popc(word));
+  }
+}
+
 // Sorting of the work order on the device, one thread block per window of at
 // most kSortWindow intervals: each short interval becomes the 64-bit word
 // (INT32_MAX - key) << 32 | position, so that an ascending bitonic sort in
@@ -798,6 +829,37 @@ __global__ void __launch_bounds__(1024) k_order_sort(int64_t I, int64_t wiv, int
 // sort, or handing whole thread blocks out heaviest first, is slower on
 // power-law graphs than 1024-row windows). The storage is untouched; only the
 // assignment of intervals to lanes changes.
+spc5_status build_single_bits(spc5_matrix* h, cudaStream_t s) {
+  if (h->single_bits || h->I == 0 || h->r != 1) return SPC5_OK;
+  const int64_t words = (h->I + 31) / 32;
+  uint32_t* d = nullptr;
+  cudaError_t e = alloc_padded((void**)&d, sizeof(uint32_t) * (size_t)words, s);
+  if (e != cudaSuccess) return cuda_fail(e, "single-value bits: allocation");
+  DeviceBuf cnt;
+  e = cnt.alloc(sizeof(unsigned long long), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(cnt.p, 0, sizeof(unsigned long long), s);
+  if (e == cudaSuccess) {
+    const unsigned grid = (unsigned)((h->I + 255) / 256);
+    if (h->mb == 1)
+      k_single_bits<1><<<grid, 256, 0, s>>>(h->I, h->long_blocks, h->long_values, h->block_rowptr, h->block_masks,
+                                             h->valptr, d, (unsigned long long*)cnt.p);
+    else
+      k_single_bits<2><<<grid, 256, 0, s>>>(h->I, h->long_blocks, h->long_values, h->block_rowptr, h->block_masks,
+                                             h->valptr, d, (unsigned long long*)cnt.p);
+    e = cudaGetLastError();
+  }
+  unsigned long long nset = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&nset, cnt.p, sizeof(nset), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    cudaFree(d);
+    return cuda_fail(e, "single-value bits");
+  }
+  h->single_bits = d;
+  h->nsingle = (int64_t)nset;
+  return SPC5_OK;
+}
+
 spc5_status build_order(spc5_matrix* h, cudaStream_t s) {
   if (h->order || h->I == 0) return SPC5_OK;
   const int64_t I = h->I;
@@ -1103,6 +1165,10 @@ spc5_status assemble_impl(int64_t n, int64_t m, int64_t nnz, int64_t nb, int r, 
     spc5_status st2 = build_order(h, s);
     if (st2 != SPC5_OK) return bail(st2);
   }
+  if (single_variant(h->variant)) {
+    spc5_status st2 = build_single_bits(h, s);
+    if (st2 != SPC5_OK) return bail(st2);
+  }
   *out = h;
   return SPC5_OK;
 }
@@ -1284,6 +1350,10 @@ spc5_status convert_impl(int64_t n, int64_t m, int64_t nnz, const int64_t* rowpt
 
   if (ordered_variant(h->variant)) {
     spc5_status st2 = build_order(h, s);
+    if (st2 != SPC5_OK) return bail(st2);
+  }
+  if (single_variant(h->variant)) {
+    spc5_status st2 = build_single_bits(h, s);
     if (st2 != SPC5_OK) return bail(st2);
   }
   *out = h;

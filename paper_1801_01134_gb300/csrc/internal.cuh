@@ -23,16 +23,18 @@ constexpr int kOrderWindow = 1024;  // rows per sorting window of the work order
 // short-interval kernel variants (spc5_opts.variant)
 inline bool valid_variant(int v) {
   return v == 0 || v == 1 || v == 3 || v == 5 || v == 9 || v == 10 || (v >= 12 && v <= 19) || v == 22 || v == 23 ||
-         (v >= 24 && v <= 29);
+         (v >= 24 && v <= 31);
 }
 // variants that need r = 1 (two lanes per row)
-inline bool r1_variant(int v) { return v == 22 || v == 23; }
+inline bool r1_variant(int v) { return v == 22 || v == 23 || v == 30 || v == 31; }
 // variants that take intervals in the sorted work order
 inline bool ordered_variant(int v) {
-  return v == 9 || v == 10 || v == 13 || v == 15 || v == 17 || v == 19 || v == 23 || v == 28 || v == 29;
+  return v == 9 || v == 10 || v == 13 || v == 15 || v == 17 || v == 19 || v == 23 || v == 28 || v == 29 || v == 30;
 }
 // variants with G lanes per interval, one lane per block (spmv_group.cuh)
 inline bool group_variant(int v) { return v >= 24 && v <= 29; }
+// variants that read the single-value class bits (Algorithm 2's test)
+inline bool single_variant(int v) { return v == 30 || v == 31; }
 
 struct Segment {  // one warp task of a long interval
   int32_t interval;
@@ -76,6 +78,10 @@ struct spc5_matrix {
   int64_t norder = 0;
   int32_t* order = nullptr;            // [norder] interval indices
   int32_t order_window = spc5::kOrderWindow;  // rows per sorting window; <= 0: all intervals
+  // Algorithm 2's test, per interval (r = 1): bit it of single_bits is set when
+  // every block of short interval it holds one value (mask 1); built on demand
+  uint32_t* single_bits = nullptr;     // [(I + 31) / 32]
+  int64_t nsingle = 0;                 // intervals with the bit set
 };
 
 namespace spc5 {
@@ -99,6 +105,7 @@ spc5_status assemble_impl(int64_t n, int64_t m, int64_t nnz, int64_t nb, int r, 
                           const int32_t* brp, const int32_t* bcol, const uint8_t* bmask, const void* vals,
                           const spc5_opts* opt, cudaStream_t s, spc5_matrix** out);
 spc5_status build_order(spc5_matrix* h, cudaStream_t s);
+spc5_status build_single_bits(spc5_matrix* h, cudaStream_t s);
 // block counts of the twelve shapes without conversion (counts.cu)
 cudaError_t launch_block_counts(int64_t n, int64_t nnz, const int64_t* rowptr, const int32_t* colidx,
                                 unsigned long long* acc, cudaStream_t s);

@@ -633,6 +633,75 @@ __global__ void __launch_bounds__(256) k_spmv_rows_g(int64_t n, int64_t I, int32
                                         y, order, norder);
 }
 
+// ------------------------------------- Algorithm 2's test (beta(1,c))
+// Variants 30 (sorted work order) and 31 (natural order), r = 1: the paper
+// gives blocks holding a single value (mask 1) a scalar loop of their own, so
+// that very sparse rows do not pay for the expand of a whole block. Here the
+// test is made once per row at set-up (single_bits): in a row whose blocks all
+// hold one value, value j belongs to block b0 + j and sits at its first
+// column, so the lane reads the row like CSR - U column indices and U values
+// per trip, no mask read, no popcount; other rows take the mask-window decode.
+// Both paths add the row's products in storage order, so the results equal
+// the other one-lane variants' bit for bit.
+template <int C, class T, bool ACCUM, int U, bool ORDER>
+__device__ __forceinline__ void rows_t_body(int64_t bid, int64_t n, int64_t I, int32_t long_blocks,
+                                            int64_t long_values, const int32_t* __restrict__ brp,
+                                            const int32_t* __restrict__ bcol, const uint8_t* __restrict__ bmask,
+                                            const typename T::V* __restrict__ val,
+                                            const int64_t* __restrict__ valptr, const typename T::X* __restrict__ x,
+                                            typename T::X* __restrict__ y, const int32_t* __restrict__ order,
+                                            int64_t norder, const uint32_t* __restrict__ single) {
+  using A = typename T::A;
+  const int64_t slot = bid * blockDim.x + threadIdx.x;  // one lane per row
+  if (slot >= (ORDER ? norder : I)) return;
+  const int64_t it = ORDER ? (int64_t)__ldg(order + slot) : slot;
+  const int32_t b0 = __ldg(brp + it), b1 = __ldg(brp + it + 1);
+  const int64_t v0 = __ldg(valptr + it);
+  if (b1 - b0 > long_blocks || __ldg(valptr + it + 1) - v0 > long_values) return;  // the segment path's
+  const typename T::V* __restrict__ vrow = val + v0;
+  A acc = 0;
+  if ((__ldg(single + (it >> 5)) >> (it & 31)) & 1u) {
+    const int32_t* __restrict__ crow = bcol + b0;
+    const int32_t len = b1 - b0;
+    int32_t j = 0;
+    for (; j + U <= len; j += U) {
+      int32_t cc[U];
+      A v[U], xx[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        cc[u] = __ldg(crow + j + u);
+        v[u] = T::val(vrow, j + u);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) xx[u] = T::xv(x, cc[u]);
+#pragma unroll
+      for (int u = 0; u < U; ++u) acc = fmadd<T>(v[u], xx[u], acc);
+    }
+    for (; j < len; ++j) acc = fmadd<T>(T::val(vrow, j), T::xv(x, __ldg(crow + j)), acc);
+  } else {
+    acc = row_sum<1, C, T, 2, 1>(0, b0, b1, vrow, bcol, bmask, x);
+  }
+  if (it < n) {
+    if (ACCUM)
+      y[it] = y[it] + acc;
+    else
+      y[it] = acc;
+  }
+}
+
+template <int C, class T, bool ACCUM, int U, bool ORDER>
+__global__ void __launch_bounds__(256) k_spmv_rows_t(int64_t n, int64_t I, int32_t long_blocks, int64_t long_values,
+                                                     const int32_t* __restrict__ brp, const int32_t* __restrict__ bcol,
+                                                     const uint8_t* __restrict__ bmask,
+                                                     const typename T::V* __restrict__ val,
+                                                     const int64_t* __restrict__ valptr,
+                                                     const typename T::X* __restrict__ x,
+                                                     typename T::X* __restrict__ y, const int32_t* __restrict__ order,
+                                                     int64_t norder, const uint32_t* __restrict__ single) {
+  rows_t_body<C, T, ACCUM, U, ORDER>(blockIdx.x, n, I, long_blocks, long_values, brp, bcol, bmask, val, valptr, x, y,
+                                     order, norder, single);
+}
+
 // -------------------------------------------------------- long intervals
 // A warp per segment (at most seg_blocks blocks of one long interval). The
 // segment's blocks are cut into S = 32/r contiguous runs, one per group of r
@@ -723,6 +792,26 @@ __global__ void __launch_bounds__(256) k_spmv_rows_segs(int64_t seg_ctas, int64_
                                           bmask, val, valptr, x, y, order, norder);
 }
 
+// segments and the single-value test kernel in one grid (variants 30 / 31)
+template <int C, class T, bool ACCUM, int U, bool ORDER>
+__global__ void __launch_bounds__(256) k_spmv_t_segs(int64_t seg_ctas, int64_t n, int64_t I, int32_t long_blocks,
+                                                     int64_t long_values, const int32_t* __restrict__ brp,
+                                                     const int32_t* __restrict__ bcol,
+                                                     const uint8_t* __restrict__ bmask,
+                                                     const typename T::V* __restrict__ val,
+                                                     const int64_t* __restrict__ valptr,
+                                                     const typename T::X* __restrict__ x, typename T::X* __restrict__ y,
+                                                     const int32_t* __restrict__ order, int64_t norder,
+                                                     const uint32_t* __restrict__ single, int64_t nseg,
+                                                     const Segment* __restrict__ segs,
+                                                     typename T::A* __restrict__ partials) {
+  if ((int64_t)blockIdx.x < seg_ctas)
+    segments_body<1, C, T, 4, 1>(blockIdx.x, nseg, segs, bcol, bmask, val, x, partials);
+  else
+    rows_t_body<C, T, ACCUM, U, ORDER>((int64_t)blockIdx.x - seg_ctas, n, I, long_blocks, long_values, brp, bcol,
+                                       bmask, val, valptr, x, y, order, norder, single);
+}
+
 // Finishes the long intervals (list of first segments built at conversion;
 // the first segment holds the interval's segment count). One lane per long
 // interval: with at most kFixupSerial segments it adds their partials row by
@@ -797,7 +886,9 @@ __global__ void __launch_bounds__(256) k_spmv_fixup(int64_t n, int64_t nlong, co
 // windows, U=4/U=2; 13/15 sorted order, mask windows, U=4/U=2; 16/17
 // natural / sorted order, bit positions unrolled (row_sum_e); 18/19 the same
 // two blocks per trip (row_sum_e2); 22 (r = 1) two lanes per row taking
-// alternate stored values (rows_g_body), 23 the same in the sorted order. (Measured:
+// alternate stored values (rows_g_body), 23 the same in the sorted order;
+// 30 / 31 (r = 1) Algorithm 2's single-value test in sorted / natural order
+// (rows_t_body). (Measured:
 // 8 nonzeros per trip is slower than 2 or 4 on every test matrix.)
 // `partials` is the segment scratch (n_segments * r accumulators).
 template <int R, int C, class T>
@@ -818,6 +909,37 @@ cudaError_t launch_beta(const spc5_matrix* h, const void* xv, void* yv, bool acc
   const int64_t seg_ctas = (h->nseg * kWarp + threads - 1) / threads;
   bool rows_done = false;  // the short intervals already launched (G lanes per row)
   if constexpr (R == 1) {
+    if (single_variant(v) && h->I > 0 && h->single_bits) {
+      constexpr int U = 4;
+      const bool ord = v == 30 && ordered;
+      const int64_t slots = ord ? h->norder : h->I;
+      const unsigned grid = (unsigned)((slots + threads - 1) / threads);
+      const int32_t* order = ord ? h->order : nullptr;
+      const int64_t norder = ord ? h->norder : 0;
+      auto go = [&](auto kern) {
+        if (grid > 0)
+          kern<<<grid, threads, 0, s>>>(h->n, h->I, h->long_blocks, h->long_values, h->block_rowptr, h->block_colidx,
+                                        h->block_masks, val, h->valptr, x, y, order, norder, h->single_bits);
+      };
+      auto go_both = [&](auto kern) {
+        kern<<<(unsigned)(seg_ctas + grid), threads, 0, s>>>(seg_ctas, h->n, h->I, h->long_blocks, h->long_values,
+                                                             h->block_rowptr, h->block_colidx, h->block_masks, val,
+                                                             h->valptr, x, y, order, norder, h->single_bits, h->nseg,
+                                                             h->segs, part);
+      };
+      if (ord) {
+        if (fused)
+          acc ? go_both(k_spmv_t_segs<C, T, true, U, true>) : go_both(k_spmv_t_segs<C, T, false, U, true>);
+        else
+          acc ? go(k_spmv_rows_t<C, T, true, U, true>) : go(k_spmv_rows_t<C, T, false, U, true>);
+      } else {
+        if (fused)
+          acc ? go_both(k_spmv_t_segs<C, T, true, U, false>) : go_both(k_spmv_t_segs<C, T, false, U, false>);
+        else
+          acc ? go(k_spmv_rows_t<C, T, true, U, false>) : go(k_spmv_rows_t<C, T, false, U, false>);
+      }
+      rows_done = true;
+    }
     if ((v == 22 || ordered) && r1_variant(v) && h->I > 0) {
       constexpr int U = 2;
       const int64_t slots = ordered ? h->norder : h->I;

@@ -225,6 +225,45 @@ def test_lane_group_sorted_equals_natural_bitwise(cuda_device):
             M.destroy()
 
 
+@pytest.mark.parametrize("name", ["lap128", "rand_ragged", "rmat11", "uniform", "fem", "sparse_rows", "dense64"])
+@pytest.mark.parametrize("c", [4, 8, 16])
+@pytest.mark.parametrize("lb", [0, 6])
+def test_single_value_test_variants(cuda_device, name, c, lb):
+    # Algorithm 2's test (variants 30 sorted, 31 natural): rows whose blocks
+    # all hold one value are read like CSR, the others with the mask decode;
+    # both add in storage order, so the bits equal the one-lane variants'
+    A = get(name)
+    x = inputs.vec_uniform(A.m, seed=0)
+    y_ref, absy = oracle.csr_spmv_dot2(A, x)
+    for vdt, xdt in ((torch.float64, torch.float64), (torch.float32, torch.float32), (torch.bfloat16, torch.float32)):
+        d = dev_csr(A, vdt)
+        xd = torch.from_numpy(x).to(xdt).cuda()
+        M = spc5.convert(d.rowptr, d.colidx, d.values, A.n, A.m, 1, c, variant=5, long_blocks=lb)
+        ref = M.spmv(xd).clone()
+        for v in (30, 31):
+            M.set_variant(v)
+            buf, y = guarded(A.n, xdt)
+            M.spmv(xd, y)
+            assert torch.equal(y, ref), (v, vdt)
+            assert torch.isnan(buf[A.n:]).all()
+            if vdt == torch.float64:
+                check64(y.cpu().numpy(), y_ref, absy)
+                y0 = inputs.vec_uniform(A.n, seed=1)
+                yd = torch.from_numpy(y0.copy()).cuda()
+                M.spmv_acc(xd, yd)
+                assert np.all(np.abs(yd.cpu().numpy() - (y0 + y_ref)) <= TOL64 * (absy + np.abs(y0)) + 1e-300)
+        M.destroy()
+
+
+def test_single_value_class_needs_r1(cuda_device):
+    A = get("rmat11")
+    d = dev_csr(A)
+    for v in (30, 31):
+        with pytest.raises(spc5.Spc5Error) as ei:
+            spc5.convert(d.rowptr, d.colidx, d.values, A.n, A.m, 2, 8, variant=v)
+        assert ei.value.status == spc5.EUNSUPPORTED
+
+
 def test_group_variants_low_precision_and_limits(cuda_device):
     # dyadic Laplacian: exact partial sums, so any order gives the oracle's bits
     A = get("lap128")
