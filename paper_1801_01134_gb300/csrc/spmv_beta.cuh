@@ -940,7 +940,7 @@ cudaError_t launch_beta(const spc5_matrix* h, const void* xv, void* yv, bool acc
       }
       rows_done = true;
     }
-    if ((v == 22 || ordered) && r1_variant(v) && h->I > 0) {
+    if (!rows_done && (v == 22 || v == 23) && h->I > 0) {
       constexpr int U = 2;
       const int64_t slots = ordered ? h->norder : h->I;
       const int64_t warps = (slots + kWarp / 2 - 1) / (kWarp / 2);
