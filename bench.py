@@ -359,15 +359,17 @@ def precision_errors(prep, y64_ref):
     return out
 
 
-def run_spmm_section(mats, dev, ks=(1, 4, 8, 16, 32), tiles=(4, -8, -16, -32, 8, 16, 32), reps: int = 5):
-    """float32 Y = A X for k right-hand sides on the stencil and R-MAT matrices,
-    best (shape, k-tile) per k from a small tuning sweep; GFLOP/s = 2 nnz k / t."""
+def run_spmm_section(mats, dev, ks=(1, 4, 8, 16, 32), reps: int = 5):
+    """float32 Y = A X for k right-hand sides on the stencil and R-MAT matrices, in the
+    (shape, column tile) the library's tuner picks per k (spc5_tune); GFLOP/s = 2 nnz k / t,
+    HBM fraction with X and Y counted k-fold."""
     import torch
 
     from paper_1801_01134_gb300 import spc5
 
     fa = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
     fb = torch.empty_like(fa)
+    hbm_peak, _ = measured_hbm_peak()
 
     def timed(fn):
         ts = []
@@ -379,7 +381,7 @@ def run_spmm_section(mats, dev, ks=(1, 4, 8, 16, 32), tiles=(4, -8, -16, -32, 8,
             e1.record()
             e1.synchronize()
             ts.append(e0.elapsed_time(e1))
-        return min(ts[1:]) if len(ts) > 1 else ts[0]
+        return statistics.median(ts[1:]) if len(ts) > 1 else ts[0]
 
     out = {}
     for mt in mats:
@@ -388,24 +390,23 @@ def run_spmm_section(mats, dev, ks=(1, 4, 8, 16, 32), tiles=(4, -8, -16, -32, 8,
         A = mt["A"]
         d = spc5.upload_csr(A, torch.float32, dev)
         res = {}
-        Ms = {rc: spc5.convert(d.rowptr, d.colidx, d.values, A.n, A.m, *rc) for rc in ((1, 8), (2, 4), (4, 8))}
         for k in ks:
+            tn = spc5.tune(d, k_spmm=k, reps=3)
+            M = spc5.convert(d.rowptr, d.colidx, d.values, A.n, A.m, tn["spmm_r"], tn["spmm_c"])
             X = torch.rand(A.m, k, dtype=torch.float32, device=dev)
             Y = torch.empty(A.n, k, dtype=torch.float32, device=dev)
-            best = None
-            for rc, M in Ms.items():
-                for kt in (tiles if k > 1 else (1,)):
-                    if abs(kt) > 1 and abs(kt) > 2 * k:
-                        continue
-                    t = timed(lambda: M.spmm(X, Y, ktile=kt))
-                    if best is None or t < best[0]:
-                        best = (t, rc, kt)
-            t, rc, kt = best
+            t = timed(lambda: M.spmm(X, Y, ktile=tn["ktile"]))
+            p = {"A": A, "r": tn["spmm_r"], "c": tn["spmm_c"], "nblocks": M.export()["nblocks"]}
+            r, c = tn["spmm_r"], tn["spmm_c"]
+            I = (A.n + r - 1) // r
+            nbytes = 4 * A.nnz + (4 + (r * c + 7) // 8) * p["nblocks"] + 12 * (I + 1) + 4 * k * (A.m + A.n)
             res[f"k{k}"] = {"ms": round(t, 4), "gflops": round(2.0 * A.nnz * k / t / 1e6, 1),
-                            "shape": f"{rc[0]}x{rc[1]}", "ktile": kt}
-        for M in Ms.values():
+                            "shape": f"{r}x{c}", "ktile": tn["ktile"], "gbs": round(nbytes / t / 1e6, 1),
+                            "hbm_frac": round(nbytes / t / 1e6 / hbm_peak, 4)}
             M.destroy()
+            del X, Y
         out[mt["name"]] = res
+        del d
     return out
 
 
@@ -446,22 +447,27 @@ def run_selector_section(prep, dev):
 
 def run_batch_section(dev, count: int = 256, reps: int = 20):
     """256 uneven float32 matrices (n lognormal in [1k, 64k], 3..60 per row,
-    stencil / banded / uniform, seed 2), each in the shape exhaustive timing
-    picks for it: one graph-replayed persistent launch vs one SpMV launch per
-    matrix. GFLOP/s = sum(2 nnz) / t."""
+    stencil / banded / uniform, seed 2), each in the shape and kernel variant the
+    library's tuner picks for it (spc5_tune): one graph-replayed persistent launch vs
+    one SpMV launch per matrix. GFLOP/s = sum(2 nnz) / t."""
     import torch
 
     from paper_1801_01134_gb300 import inputs, spc5
 
-    mats, keep, xs, ys, shapes = [], [], [], [], {}
+    mats, keep, xs, ys, shapes, variants = [], [], [], [], {}, {}
     flops = 0.0
+    nbytes = 0
     t_tune = time.time()
     for j in range(count):
         A = inputs.batch_matrix(j, seed=2)
         d = spc5.upload_csr(A, torch.float32, dev)
-        r, c, _ = spc5.select(d, spc5.SELECT_EXHAUSTIVE)
+        tn = spc5.tune(d, reps=3)
+        r, c, v = tn["r"], tn["c"], tn["variant"]
         shapes[f"{r}x{c}"] = shapes.get(f"{r}x{c}", 0) + 1
-        mats.append(spc5.convert(d.rowptr, d.colidx, d.values, A.n, A.m, r, c))
+        variants[str(v)] = variants.get(str(v), 0) + 1
+        M = spc5.convert(d.rowptr, d.colidx, d.values, A.n, A.m, r, c, variant=v)
+        mats.append(M)
+        nbytes += beta_bytes({"A": A, "r": r, "c": c, "nblocks": M.export()["nblocks"]}, 4, 4)
         keep.append(d)
         xs.append(torch.rand(A.m, dtype=torch.float32, device=dev))
         ys.append(torch.empty(A.n, dtype=torch.float32, device=dev))
@@ -492,12 +498,16 @@ def run_batch_section(dev, count: int = 256, reps: int = 20):
     B.destroy()
     for M in mats:
         M.destroy()
+    hbm_peak, _ = measured_hbm_peak()
     return {"workload": f"{count} float32 matrices, n lognormal in [1k, 64k], 3..60 per row, seed 2",
-            "nnz_total": int(flops / 2), "shapes": shapes, "tune_s": round(t_tune, 2),
+            "nnz_total": int(flops / 2), "shapes": shapes, "variants": variants, "tune_s": round(t_tune, 2),
+            "tuner": "spc5_tune per matrix (shape x variant, timed, cached per signature)",
             "graph_ms": round(t_graph, 4), "gflops_graph": round(flops / t_graph / 1e6, 1),
+            "gbs_graph": round(nbytes / t_graph / 1e6, 1), "hbm_frac_graph": round(nbytes / t_graph / 1e6 / hbm_peak, 4),
             "direct_ms": round(t_direct, 4), "gflops_direct": round(flops / t_direct / 1e6, 1),
             "per_matrix_launches_ms": round(t_each, 4), "gflops_per_matrix_launches": round(flops / t_each / 1e6, 1),
-            "speedup_vs_per_matrix": round(t_each / t_graph, 3)}
+            "speedup_vs_per_matrix": round(t_each / t_graph, 3),
+            "l2": "not flushed between replays (the batch's arrays, ~0.5 GB, exceed L2)"}
 
 
 # ------------------------------------------------------------------------ CG

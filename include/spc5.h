@@ -306,6 +306,45 @@ spc5_status spc5_copy(const void* src_d, void* dst_d, int64_t bytes, spc5_stream
 spc5_status spc5_spmm(spc5_handle h, int k, const void* X_d, int64_t ldx, void* Y_d, int64_t ldy, int ktile,
                       spc5_stream_t stream);
 
+/* ------------------------------------------------------------------ tuner */
+#define SPC5_TUNE_NO_CACHE 1 /* spc5_tune flag: time again even when the signature is known */
+
+typedef struct {
+  int32_t r, c;       /* SpMV: fastest block shape */
+  int32_t variant;    /* SpMV: fastest kernel variant on that shape (spc5_opts.variant) */
+  float spmv_ms;      /* SpMV: its median milliseconds */
+  int32_t spmm_r, spmm_c, ktile; /* SpMM (k_spmm > 0): fastest shape and column tile */
+  float spmm_ms;      /* SpMM: its median milliseconds (-1 when k_spmm == 0) */
+  int32_t from_cache; /* 1 when the result came from the signature cache */
+  uint64_t signature; /* the matrix signature the cache is keyed on */
+} spc5_tune_result;
+
+/*
+ * spc5_tune - the library's autotuner: times every block shape (twelve) x the
+ * kernel variants that win on some matrix (float64: 5, 10, 13, 15, 24;
+ * float32 / bfloat16 also 16, 18; r = 1 also 22, 23, 30, 31) and, when
+ * k_spmm > 0, every shape x SpMM column tile for k_spmm right-hand sides, on
+ * this GPU (median of `reps` products after one untimed product, no cache
+ * flush between them), and returns the fastest choices - the GPU form of the
+ * paper's choice of the best kernel per matrix (section "Performance
+ * prediction and optimal kernel selection"). The result is remembered per
+ * matrix signature (n, m, nnz, value type, k_spmm, SM count, the twelve
+ * N_blocks(r,c), the longest row): a later call with an equal signature
+ * returns it without timing (from_cache = 1) unless flags has
+ * SPC5_TUNE_NO_CACHE. The cache lives until spc5_tune_cache_clear or the end
+ * of the process and is shared by all host threads.
+ *   CSR arguments as spc5_convert (checked there: SPC5_EUNSORTED, ...);
+ *   reps >= 1; 0 <= k_spmm <= 1024.
+ * Allocates its work vectors from the stream-ordered pool; synchronises
+ * `stream`.
+ */
+spc5_status spc5_tune(int64_t n, int64_t m, int64_t nnz, const int64_t* rowptr_d, const int32_t* colidx_d,
+                      const void* values_d, spc5_dtype vt, int k_spmm, int reps, int flags, spc5_tune_result* out,
+                      spc5_stream_t stream);
+
+/* spc5_tune_cache_clear - forget every remembered tuning result. */
+spc5_status spc5_tune_cache_clear(void);
+
 /* ----------------------------------------------------------------- batches */
 typedef struct spc5_batch_s* spc5_batch; /* opaque batched product */
 

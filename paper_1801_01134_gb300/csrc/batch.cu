@@ -4,10 +4,11 @@
 // Many small products launched one by one leave the GPU idle between tiny
 // kernels. Here every short interval of every matrix belongs to a work item
 // of 32/r consecutive intervals (one warp's worth, lane per row as in the
-// single-matrix kernel); persistent warps take items from a global counter
-// with one atomicAdd each (no waiting on other warps), so uneven matrices
-// balance themselves. Each matrix keeps its own block shape (a run-time
-// argument here), chosen per matrix by the caller's tuner or selector. Long
+// single-matrix kernel); persistent warps take kGrab items at a time from a
+// global counter with one atomicAdd (no waiting on other warps), so uneven
+// matrices balance themselves. Each matrix keeps its own block shape and the
+// row decode of its tuned variant (both run-time arguments here, chosen per
+// matrix by spc5_tune or the caller's selector). Long
 // intervals are items of a second kind - one warp per segment, partials into
 // the matrix's scratch - followed by one fix-up kernel over the long
 // intervals.
@@ -30,9 +31,26 @@ struct MatDesc {  // one matrix of the batch (device copy)
   void* partials;
   const void* x;
   void* y;
+  const uint32_t* single;  // single-value class bits (variants 30 / 31), or NULL
   int64_t n, I, nseg, long_values;
-  int32_t r, c, mb, long_blocks, log2r, pad;
+  int32_t r, c, mb, long_blocks, log2r;
+  int32_t dec;  // row decode of the matrix's tuned variant (see decode_of)
 };
+
+// items a warp takes per atomic on the shared counter: same-address atomics
+// serialise (a few ns each), so one per 32-row item cost about a third of the
+// batch on 256 matrices of ~3 M rows in total
+constexpr int kGrab = 8;
+
+// The decode of a matrix's short intervals, from its variant: 1 mask
+// windows, 4 Algorithm 2's single-value test (r = 1) with the mask windows
+// for the other rows, 0 the flattened decode for every other variant (the
+// batch maps one lane to one row).
+inline int decode_of(int v, int r) {
+  if (v == 12 || v == 13 || v == 14 || v == 15) return 1;
+  if ((v == 30 || v == 31) && r == 1) return 4;
+  return 0;
+}
 
 struct Item {  // kind 0: intervals [i0, i0 + 32/r) of matrix mat; kind 1: segment i0 of mat
   int32_t mat;
@@ -76,6 +94,51 @@ __device__ __forceinline__ void ldmask(const uint8_t* __restrict__ m, int64_t b,
   }
 }
 
+// one row of a short interval with the shape and decode known at compile time
+template <int R, int C, class T, int DEC>
+__device__ __forceinline__ typename T::A batch_row(const MatDesc& d, int64_t it, int i, int32_t b, int32_t bend,
+                                                   int64_t v0) {
+  const typename T::V* __restrict__ vrow = static_cast<const typename T::V*>(d.val) + v0;
+  const typename T::X* __restrict__ x = static_cast<const typename T::X*>(d.x);
+  if constexpr (DEC == 4) {
+    if (d.single && ((__ldg(d.single + (it >> 5)) >> (it & 31)) & 1u)) {
+      typename T::A acc = 0;
+      const int32_t* __restrict__ crow = d.bcol + b;
+      for (int32_t j = 0; j < bend - b; ++j) acc = fmadd<T>(T::val(vrow, j), T::xv(x, __ldg(crow + j)), acc);
+      return acc;
+    }
+    return row_sum<R, C, T, 2, 1>(i, b, bend, vrow, d.bcol, d.bmask, x);
+  } else {
+    return row_sum<R, C, T, 2, DEC>(i, b, bend, vrow, d.bcol, d.bmask, x);
+  }
+}
+
+// The unrolled-position decodes (2, 3) are left out here: with all twelve
+// shapes inlined into the one persistent kernel they would set its register
+// count (and occupancy) for every matrix; such matrices take the flattened
+// decode in the batch.
+template <int R, int C, class T>
+__device__ __forceinline__ typename T::A batch_row_dec(const MatDesc& d, int64_t it, int i, int32_t b, int32_t bend,
+                                                       int64_t v0) {
+  if (d.dec == 1) return batch_row<R, C, T, 1>(d, it, i, b, bend, v0);
+  if constexpr (R == 1)
+    if (d.dec == 4) return batch_row<R, C, T, 4>(d, it, i, b, bend, v0);
+  return batch_row<R, C, T, 0>(d, it, i, b, bend, v0);
+}
+
+template <class T>
+__device__ __forceinline__ typename T::A batch_row_any(const MatDesc& d, int64_t it, int i, int32_t b, int32_t bend,
+                                                       int64_t v0) {
+#define SPC5_BCASE(RR, CC) \
+  if (d.r == RR && d.c == CC) return batch_row_dec<RR, CC, T>(d, it, i, b, bend, v0);
+  SPC5_BCASE(1, 4) SPC5_BCASE(1, 8) SPC5_BCASE(1, 16)
+  SPC5_BCASE(2, 4) SPC5_BCASE(2, 8) SPC5_BCASE(2, 16)
+  SPC5_BCASE(4, 4) SPC5_BCASE(4, 8) SPC5_BCASE(4, 16)
+  SPC5_BCASE(8, 4) SPC5_BCASE(8, 8)
+#undef SPC5_BCASE
+  return batch_row_dec<8, 16, T>(d, it, i, b, bend, v0);
+}
+
 template <class T>
 __global__ void __launch_bounds__(256) k_batch(const MatDesc* __restrict__ mats, const Item* __restrict__ items,
                                                int64_t nitems, unsigned long long* __restrict__ counter) {
@@ -84,10 +147,12 @@ __global__ void __launch_bounds__(256) k_batch(const MatDesc* __restrict__ mats,
   using A = typename T::A;
   const int lane = threadIdx.x & 31;
   for (;;) {
-    unsigned long long k = 0;
-    if (lane == 0) k = atomicAdd(counter, 1ull);
-    k = __shfl_sync(0xffffffffu, k, 0);
-    if (k >= (unsigned long long)nitems) break;
+    unsigned long long k0 = 0;
+    if (lane == 0) k0 = atomicAdd(counter, (unsigned long long)kGrab);
+    k0 = __shfl_sync(0xffffffffu, k0, 0);
+    if (k0 >= (unsigned long long)nitems) break;
+    const unsigned long long kend = k0 + kGrab < (unsigned long long)nitems ? k0 + kGrab : nitems;
+    for (unsigned long long k = k0; k < kend; ++k) {
     const Item itm = items[k];
     const MatDesc& d = mats[itm.mat];
     const int r = d.r, c = d.c, mb = d.mb;
@@ -97,26 +162,11 @@ __global__ void __launch_bounds__(256) k_batch(const MatDesc* __restrict__ mats,
       const int64_t it = (int64_t)itm.i0 + (lane >> d.log2r);
       const int i = lane & (r - 1);
       if (it >= d.I) continue;
-      int32_t b = __ldg(d.brp + it);
+      const int32_t b = __ldg(d.brp + it);
       const int32_t bend = __ldg(d.brp + it + 1);
       const int64_t v0 = __ldg(d.valptr + it);
       if (bend - b > d.long_blocks || __ldg(d.valptr + it + 1) - v0 > d.long_values) continue;
-      A acc = 0;
-      int32_t vbase = 0;
-      for (; b < bend; ++b) {
-        uint32_t w[4];
-        ldmask(d.bmask, b, mb, w);
-        uint32_t bits = rb(w, i * c, c);
-        int32_t vo = vbase + pb(w, i * c);
-        vbase += __popc(w[0]) + __popc(w[1]) + __popc(w[2]) + __popc(w[3]);
-        if (!bits) continue;
-        const int64_t col0 = __ldg(d.bcol + b);
-        while (bits) {
-          const int kb = __ffs(bits) - 1;
-          bits &= bits - 1;
-          acc = fma(T::val(val + v0, vo++), T::xv(x, col0 + kb), acc);
-        }
-      }
+      const A acc = batch_row_any<T>(d, it, i, b, bend, v0);
       const int64_t row = it * r + i;
       if (row < d.n) static_cast<X*>(d.y)[row] = acc;
     } else {
@@ -159,6 +209,7 @@ __global__ void __launch_bounds__(256) k_batch(const MatDesc* __restrict__ mats,
       }
       for (int dd = kWarp / 2; dd >= r; dd >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, dd);
       if (lane < r) static_cast<A*>(d.partials)[(int64_t)itm.i0 * r + lane] = acc;
+    }
     }
   }
 }
@@ -269,7 +320,8 @@ spc5_status batch_create_impl(const spc5_handle* mats, const void* const* xs, vo
     d.mb = h->mb;
     d.long_blocks = h->long_blocks;
     d.log2r = h->r == 1 ? 0 : h->r == 2 ? 1 : h->r == 4 ? 2 : 3;
-    d.pad = 0;
+    d.dec = decode_of(h->variant, h->r);
+    d.single = d.dec == 4 ? h->single_bits : nullptr;
     const int S = kWarp / h->r;
     for (int64_t i0 = 0; i0 < h->I; i0 += S) items.push_back(Item{j, (int32_t)i0, 0, 0});
     if (h->nseg > 0) {
@@ -312,7 +364,7 @@ spc5_status batch_create_impl(const spc5_handle* mats, const void* const* xs, vo
     if (oe == cudaSuccess && v > 0) per_sm = v;
   }
   int64_t blocks = (int64_t)sm_count() * per_sm;
-  const int64_t need = (b->nitems + 7) / 8;
+  const int64_t need = (b->nitems + 8 * kGrab - 1) / (8 * kGrab);
   if (blocks > need) blocks = need > 0 ? need : 1;
   b->blocks = (int)blocks;
   // capture the whole batched product once; replays reuse it

@@ -57,6 +57,15 @@ class Selector(ctypes.Structure):
                 ("feat_mean", ctypes.c_float * NFEATURES), ("feat_scale", ctypes.c_float * NFEATURES)]
 
 
+class TuneResult(ctypes.Structure):
+    _fields_ = [("r", ctypes.c_int32), ("c", ctypes.c_int32), ("variant", ctypes.c_int32), ("spmv_ms", ctypes.c_float),
+                ("spmm_r", ctypes.c_int32), ("spmm_c", ctypes.c_int32), ("ktile", ctypes.c_int32),
+                ("spmm_ms", ctypes.c_float), ("from_cache", ctypes.c_int32), ("signature", ctypes.c_uint64)]
+
+
+TUNE_NO_CACHE = 1
+
+
 class Arrays(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("m", ctypes.c_int64), ("nnz", ctypes.c_int64), ("nblocks", ctypes.c_int64),
                 ("nintervals", ctypes.c_int64), ("r", ctypes.c_int32), ("c", ctypes.c_int32),
@@ -102,6 +111,8 @@ def load(build_if_missing: bool = False):
     lib.spc5_fma_rate_lanes.argtypes = [i32, i64, i32, vp, vp, vp]
     lib.spc5_spmv_noalloc.argtypes = [vp, vp, vp, vp]
     lib.spc5_launch_count.argtypes = [vp, ctypes.POINTER(i32)]
+    lib.spc5_tune.argtypes = [i64, i64, i64, vp, vp, vp, i32, i32, i32, i32, ctypes.POINTER(TuneResult), vp]
+    lib.spc5_tune_cache_clear.argtypes = []
     lib.spc5_device_peaks.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32), ctypes.POINTER(i32)]
     lib.spc5_cg.argtypes = [vp, vp, vp, vp, ctypes.POINTER(CgOpts), ctypes.POINTER(CgInfo), vp]
     lib.spc5_spmm.argtypes = [vp, i32, vp, i64, vp, i64, i32, vp]
@@ -121,7 +132,8 @@ def load(build_if_missing: bool = False):
     lib.spc5_select.argtypes = [i64, i64, i64, vp, vp, vp, i32, i32, ctypes.POINTER(Selector), vp, vp, vp, vp]
     for f in (lib.spc5_convert, lib.spc5_assemble, lib.spc5_autotune, lib.spc5_spmv, lib.spc5_spmv_acc, lib.spc5_export, lib.spc5_destroy, lib.spc5_set_variant,
               lib.spc5_count_blocks, lib.spc5_csr_spmv, lib.spc5_copy, lib.spc5_fma_rate, lib.spc5_fma_rate_lanes,
-              lib.spc5_spmv_noalloc, lib.spc5_launch_count, lib.spc5_device_peaks, lib.spc5_cg, lib.spc5_spmm, lib.spc5_features,
+              lib.spc5_spmv_noalloc, lib.spc5_launch_count, lib.spc5_device_peaks, lib.spc5_tune,
+              lib.spc5_tune_cache_clear, lib.spc5_cg, lib.spc5_spmm, lib.spc5_features,
               lib.spc5_time_formats, lib.spc5_mlp_train, lib.spc5_mlp_grad, lib.spc5_mlp_infer, lib.spc5_poly_fit,
               lib.spc5_select, lib.spc5_batch_create, lib.spc5_batch_spmv, lib.spc5_batch_spmv_direct,
               lib.spc5_batch_destroy, lib.spc5_partition):
@@ -316,6 +328,20 @@ def csr_spmv(rowptr: torch.Tensor, colidx: torch.Tensor, values: torch.Tensor, n
     _check(load().spc5_csr_spmv(n, m, values.numel(), _ptr(rowptr), _ptr(colidx), _ptr(values), vt, _ptr(x), _ptr(y),
                                 group, _stream_ptr(stream)), "spc5_csr_spmv")
     return y
+
+
+def tune(d: "DeviceCSR", k_spmm: int = 0, reps: int = 5, use_cache: bool = True, stream=None) -> dict:
+    """Fastest (shape, variant) for the SpMV and, for k_spmm > 0, (shape, column tile) for the
+    SpMM of a device CSR, timed on this GPU and remembered per matrix signature."""
+    res = TuneResult()
+    vt = _VALUE_DTYPE[d.values.dtype]
+    _check(load().spc5_tune(d.n, d.m, d.nnz, _ptr(d.rowptr), _ptr(d.colidx), _ptr(d.values), vt, k_spmm, reps,
+                            0 if use_cache else TUNE_NO_CACHE, ctypes.byref(res), _stream_ptr(stream)), "spc5_tune")
+    return {f: getattr(res, f) for f, _ in TuneResult._fields_}
+
+
+def tune_cache_clear():
+    _check(load().spc5_tune_cache_clear(), "spc5_tune_cache_clear")
 
 
 def count_blocks(rowptr: torch.Tensor, colidx: torch.Tensor, n: int, m: int, stream=None) -> np.ndarray:

@@ -68,6 +68,15 @@ def test_host_side_argument_checks(lib):
         opts = spc5.Opts(0, 0, v, 0)
         assert lib.spc5_convert(4, 4, 0, 1, None, None, 0, r, 8, ctypes.byref(opts), None, ctypes.byref(h)) == code, v
     assert lib.spc5_set_variant(None, 22, None) == spc5.EINVAL
+    # the tuner checks its arguments before any device work
+    res = spc5.TuneResult()
+    assert lib.spc5_tune(4, 4, 0, 1, None, None, 0, 0, 3, 0, None, None) == spc5.EINVAL  # no output
+    assert lib.spc5_tune(4, 4, 0, 1, None, None, 0, 0, 0, 0, ctypes.byref(res), None) == spc5.EINVAL  # reps
+    assert lib.spc5_tune(4, 4, 0, 1, None, None, 0, 2000, 3, 0, ctypes.byref(res), None) == spc5.EINVAL  # k
+    assert lib.spc5_tune(4, 4, 0, 1, None, None, 0, 0, 3, 4, ctypes.byref(res), None) == spc5.EINVAL  # flag
+    assert lib.spc5_tune(4, 4, 0, None, None, None, 0, 0, 3, 0, ctypes.byref(res), None) == spc5.EINVAL
+    assert lib.spc5_tune(4, 4, 0, 1, None, None, 9, 0, 3, 0, ctypes.byref(res), None) == spc5.EUNSUPPORTED
+    assert lib.spc5_tune_cache_clear() == spc5.OK
     assert lib.spc5_autotune(None, None, None, 3, None, None, None) == spc5.EINVAL
 
 

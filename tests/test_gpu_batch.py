@@ -74,3 +74,18 @@ def test_batch_rejects_mixed_types(cuda_device):
     x32 = torch.zeros(A.m, dtype=torch.float32, device="cuda")
     with pytest.raises(spc5.Spc5Error):
         spc5.Batch([M64, M32], [x64, x32], [torch.empty_like(x64), torch.empty_like(x32)])
+
+
+def test_batch_keeps_each_matrix_decode_bitwise(cuda_device):
+    # per-matrix tuned variants: the batch uses the matrix's mask-window or
+    # single-value decode, which add in storage order like the single product
+    As, mats, hs, xs, ys = build(36, torch.float32, seed=7)
+    for j, M in enumerate(mats):
+        choices = (13, 15, 30, 31, 12, 5) if M.r == 1 else (12, 13, 15, 5)
+        M.set_variant(choices[j % len(choices)])
+    B = spc5.Batch(mats, xs, ys)
+    B.run()
+    torch.cuda.synchronize()
+    for j, M in enumerate(mats):
+        assert torch.equal(ys[j], M.spmv(xs[j])), (j, M.r, M.c)
+    B.destroy()
