@@ -298,8 +298,10 @@ spc5_status spc5_copy(const void* src_d, void* dst_d, int64_t bytes, spc5_stream
  *   k     1..1024; ktile = column tile: 1, 4, -8, -16 or -32 (one lane per
  *         row holding 1 to 32 columns; X rows read as 16-byte vectors when
  *         X_d is 16-byte aligned and ldx a multiple of 16 bytes), 8, 16 or 32
- *         (that many lanes per row, one column each); 0 = choose from k. The
- *         grid covers ceil(k / |ktile|) tiles.
+ *         (ktile / 4 lanes per row interval, 4 columns each: the X rows a
+ *         block's columns need are read once and applied to all r rows of
+ *         the block); 0 = choose from k. The grid covers ceil(k / |ktile|)
+ *         tiles.
  * A handle with long intervals keeps n_segments * r * k partial sums; the first
  * call with a larger k grows that buffer (cudaMalloc, device synchronisation).
  */

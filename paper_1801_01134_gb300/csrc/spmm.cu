@@ -9,8 +9,9 @@
 //   ktile 1, 4, -8, -16, -32   one lane per row keeps 1 to 32 accumulators
 //                  and, per nonzero, reads one matrix value and that wide a
 //                  slice of an X row (16-byte loads when X rows are aligned);
-//   ktile 8/16/32  ktile lanes per row, one column each: the X values of a
-//                  nonzero are one coalesced load (better for large k).
+//   ktile 8/16/32  ktile / 4 lanes per interval, 4 columns each: the X rows
+//                  a block needs are read once (coalesced) and applied to all
+//                  of the block's rows (for large k, where X dominates).
 // The grid's y dimension covers the column tiles. Long intervals go through
 // warp segments and a fix-up, as in the SpMV, with per-row partials per
 // segment and column.
@@ -156,48 +157,154 @@ __global__ void __launch_bounds__(256) k_spmm_rows(int64_t n, int64_t I, int r, 
   }
 }
 
-// short intervals, G lanes per row: lane g of a group takes column j0 + g, so
-// the G values of X a nonzero needs are one coalesced load; every lane of the
-// group decodes the same blocks (the decode is redundant, the loads are not)
-template <class T, int G>
-__global__ void __launch_bounds__(256) k_spmm_rows_cols(int64_t n, int64_t I, int r, int c, int mb,
-                                                        int32_t long_blocks, int64_t long_values,
-                                                        const int32_t* __restrict__ brp,
-                                                        const int32_t* __restrict__ bcol,
-                                                        const uint8_t* __restrict__ bmask,
-                                                        const typename T::V* __restrict__ val,
-                                                        const int64_t* __restrict__ valptr,
-                                                        const typename T::X* __restrict__ X, int64_t ldx,
-                                                        typename T::X* __restrict__ Y, int64_t ldy, int k) {
+// short intervals, G lanes per interval (ktile 8 / 16 / 32, G = ktile / 4):
+// lane g of a group owns the 4 columns j = tile * ktile + 4 g .. + 3 of X and
+// Y and keeps the interval's R row sums for each. Per block the group reads
+// the rows of X that the block's nonzero columns need once - 4 values per
+// lane (one 16-byte load when X rows are aligned), a coalesced stretch of
+// ktile values per group - and applies them to every row of the block, so X
+// moves (columns used per block) x ktile values instead of (nonzeros) x
+// ktile; the mask, the column index and each value are one address for the
+// whole group (broadcast loads), and each decoded value feeds 4 multiply-adds.
+// Two blocks per trip for small blocks (one for large ones), the next
+// trip's masks and columns read one trip ahead. No lane talks to another. Each (row, column) sum adds the row's products in
+// storage order, as the SpMV does.
+template <class T, int V>
+struct XQuad {
+  typename T::A v[V];
+};
+
+template <class T, int V>
+__device__ __forceinline__ XQuad<T, V> load_xq(const typename T::X* __restrict__ p, int nv, bool vec) {
+  XQuad<T, V> q;
+  if constexpr (sizeof(typename T::X) == 4 && V == 4) {
+    if (vec) {
+      const float4 t = __ldg(reinterpret_cast<const float4*>(p));
+      q.v[0] = t.x;
+      q.v[1] = t.y;
+      q.v[2] = t.z;
+      q.v[3] = t.w;
+      return q;
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < V; ++t) q.v[t] = t < nv ? (typename T::A)__ldg(p + t) : typename T::A(0);
+  return q;
+}
+
+template <class T, int R, int C, int G>
+__global__ void __launch_bounds__(256) k_spmm_blk(int64_t n, int64_t I, int32_t long_blocks, int64_t long_values,
+                                                  const int32_t* __restrict__ brp, const int32_t* __restrict__ bcol,
+                                                  const uint8_t* __restrict__ bmask,
+                                                  const typename T::V* __restrict__ val,
+                                                  const int64_t* __restrict__ valptr,
+                                                  const typename T::X* __restrict__ X, int64_t ldx,
+                                                  typename T::X* __restrict__ Y, int64_t ldy, int k, bool vec) {
   using A = typename T::A;
+  constexpr int MB = (R * C + 7) / 8;
+  constexpr int V = 4;  // columns per lane
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t row = t / G;  // rows in order: interval it = row / r, block row i = row % r
-  const int g = (int)(t % G);
-  const int j = blockIdx.y * G + g;
-  if (row >= n || j >= k) return;
-  const int64_t it = row / r;
-  const int i = (int)(row % r);
+  const int64_t it = t / G;
+  const int j = blockIdx.y * (G * V) + (int)(t % G) * V;
+  if (it >= I || j >= k) return;
+  const int nv = k - j < V ? k - j : V;
+  const bool full = vec && nv == V;
   int32_t b = __ldg(brp + it);
   const int32_t bend = __ldg(brp + it + 1);
   const int64_t v0 = __ldg(valptr + it);
   if (bend - b > long_blocks || __ldg(valptr + it + 1) - v0 > long_values) return;  // the segment path's
   const typename T::V* __restrict__ vrow = val + v0;
-  A acc = 0;
-  int32_t vbase = 0;
-  for (; b < bend; ++b) {
-    const RtMask mk = load_mask_rt(bmask, b, mb);
-    uint32_t bits = row_bits_rt(mk, i, c);
-    int32_t vo = vbase + popc_below_rt(mk, i, c);
-    vbase += popc_all_rt(mk);
-    if (!bits) continue;
-    const int64_t col0 = __ldg(bcol + b);
-    while (bits) {
-      const int kb = __ffs(bits) - 1;
-      bits &= bits - 1;
-      acc = fma(T::val(vrow, vo++), (A)__ldg(X + (col0 + kb) * ldx + j), acc);
+  const typename T::X* __restrict__ xcol = X + j;
+  A acc[R][V];
+#pragma unroll
+  for (int i = 0; i < R; ++i)
+#pragma unroll
+    for (int q = 0; q < V; ++q) acc[i][q] = A(0);
+  int32_t vo = 0;  // first value of block b inside the interval
+  Mask<MB> m0 = b < bend ? load_mask<MB>(bmask, b) : zero_mask<MB>();
+  Mask<MB> m1 = b + 1 < bend ? load_mask<MB>(bmask, b + 1) : zero_mask<MB>();
+  int64_t c0 = b < bend ? __ldg(bcol + b) : 0, c1 = b + 1 < bend ? __ldg(bcol + b + 1) : 0;
+  // two blocks per trip while their X rows fit in registers, one otherwise
+  constexpr int NB = R * C * V * sizeof(A) <= 256 ? 2 : 1;
+  if (NB == 1) m1 = zero_mask<MB>();
+  for (; b < bend; b += NB) {
+    const Mask<MB> mk[2] = {m0, m1};
+    const int64_t cl[2] = {c0, c1};
+    if (NB == 1) {
+      if (b + 1 < bend) {
+        m0 = load_mask<MB>(bmask, b + 1);
+        c0 = __ldg(bcol + b + 1);
+      }
+    } else {
+      if (b + 2 < bend) {
+        m0 = load_mask<MB>(bmask, b + 2);
+        c0 = __ldg(bcol + b + 2);
+      }
+      if (b + 3 < bend) {
+        m1 = load_mask<MB>(bmask, b + 3);
+        c1 = __ldg(bcol + b + 3);
+      } else {  // the next pair has no second block
+        m1 = zero_mask<MB>();
+        c1 = 0;
+      }
+    }
+    XQuad<T, V> xr[NB][C];
+#pragma unroll
+    for (int h = 0; h < NB; ++h) {
+      uint32_t used = 0;  // zero for a second block past the interval
+#pragma unroll
+      for (int i = 0; i < R; ++i) used |= row_bits<C>(mk[h], i);
+#pragma unroll
+      for (int kk = 0; kk < C; ++kk)
+        xr[h][kk] = (used >> kk) & 1u ? load_xq<T, V>(xcol + (cl[h] + kk) * ldx, nv, full) : XQuad<T, V>{};
+    }
+#pragma unroll
+    for (int h = 0; h < NB; ++h) {
+#pragma unroll
+      for (int i = 0; i < R; ++i) {
+        const uint32_t rb = row_bits<C>(mk[h], i);
+        int32_t vv = vo + popc_below<C>(mk[h], i);
+#pragma unroll
+        for (int kk = 0; kk < C; ++kk)
+          if ((rb >> kk) & 1u) {
+            const A v = T::val(vrow, vv);
+#pragma unroll
+            for (int q = 0; q < V; ++q) acc[i][q] = fma(v, xr[h][kk].v[q], acc[i][q]);
+            ++vv;
+          }
+      }
+      vo += popc_all(mk[h]);
     }
   }
-  Y[row * ldy + j] = acc;
+#pragma unroll
+  for (int i = 0; i < R; ++i) {
+    const int64_t row = it * R + i;
+    if (row < n)
+#pragma unroll
+      for (int q = 0; q < V; ++q)
+        if (q < nv) Y[row * ldy + j + q] = acc[i][q];
+  }
+}
+
+template <class T, int G>
+void launch_spmm_blk(const spc5_matrix* h, int k, const typename T::X* Xm, int64_t ldx, typename T::X* Ym,
+                     int64_t ldy, cudaStream_t s) {
+  const typename T::V* val = static_cast<const typename T::V*>(h->values);
+  dim3 grid((unsigned)((h->I * G + 255) / 256), (unsigned)((k + 4 * G - 1) / (4 * G)));
+  // 16-byte X loads when every lane's 4 columns start on a 16-byte boundary
+  const bool vec = sizeof(typename T::X) == 4 && ldx % 4 == 0 && (reinterpret_cast<uintptr_t>(Xm) & 15u) == 0;
+#define SPC5_BLK(RR, CC)                                                                                            \
+  if (h->r == RR && h->c == CC) {                                                                                   \
+    k_spmm_blk<T, RR, CC, G><<<grid, 256, 0, s>>>(h->n, h->I, h->long_blocks, h->long_values, h->block_rowptr,     \
+                                                  h->block_colidx, h->block_masks, val, h->valptr, Xm, ldx, Ym, ldy, \
+                                                  k, vec);                                                          \
+    return;                                                                                                         \
+  }
+  SPC5_BLK(1, 4) SPC5_BLK(1, 8) SPC5_BLK(1, 16)
+  SPC5_BLK(2, 4) SPC5_BLK(2, 8) SPC5_BLK(2, 16)
+  SPC5_BLK(4, 4) SPC5_BLK(4, 8) SPC5_BLK(4, 16)
+  SPC5_BLK(8, 4) SPC5_BLK(8, 8) SPC5_BLK(8, 16)
+#undef SPC5_BLK
 }
 
 // long intervals: a warp per segment, lane = (block slot, row); KT partials
@@ -306,8 +413,8 @@ cudaError_t spmm_launch(const spc5_matrix* h, int k, const void* Xv, int64_t ldx
   return cudaGetLastError();
 }
 
-// G lanes per row for the short intervals; the long ones keep the segment
-// path with 8 columns per lane
+// ktile columns per interval for the short intervals; the long ones keep the
+// segment path with 8 columns per lane
 template <class T, int G>
 cudaError_t spmm_launch_cols(const spc5_matrix* h, int k, const void* Xv, int64_t ldx, void* Yv, int64_t ldy,
                              void* part, cudaStream_t s) {
@@ -316,12 +423,7 @@ cudaError_t spmm_launch_cols(const spc5_matrix* h, int k, const void* Xv, int64_
   const X* Xm = static_cast<const X*>(Xv);
   X* Ym = static_cast<X*>(Yv);
   const typename T::V* val = static_cast<const typename T::V*>(h->values);
-  if (h->n > 0) {
-    dim3 grid((unsigned)((h->n * G + 255) / 256), (unsigned)((k + G - 1) / G));
-    k_spmm_rows_cols<T, G><<<grid, 256, 0, s>>>(h->n, h->I, h->r, h->c, h->mb, h->long_blocks, h->long_values,
-                                                h->block_rowptr, h->block_colidx, h->block_masks, val, h->valptr, Xm,
-                                                ldx, Ym, ldy, k);
-  }
+  if (h->I > 0) launch_spmm_blk<T, G / 4>(h, k, Xm, ldx, Ym, ldy, s);
   if (h->nseg > 0) {
     constexpr int KT = 8;
     dim3 grid((unsigned)((h->nseg * kWarp + 255) / 256), (unsigned)((k + KT - 1) / KT));
@@ -335,7 +437,7 @@ cudaError_t spmm_launch_cols(const spc5_matrix* h, int k, const void* Xv, int64_
 }
 
 // ktile 1 or 4, and -8 / -16 / -32: one lane per row holding 1, 4, 8, 16 or
-// 32 columns; 8, 16, 32: that many lanes per row, one column each
+// 32 columns; 8, 16, 32: ktile / 4 lanes per interval, 4 columns each
 template <class T>
 cudaError_t spmm_tile(int kt, const spc5_matrix* h, int k, const void* X, int64_t ldx, void* Y, int64_t ldy,
                       void* part, cudaStream_t s) {
