@@ -103,7 +103,12 @@ typedef struct {
   /* Rows per sorting window of the work order of the sorted variants:
    * 0 selects 1024; a negative value sorts all intervals together. */
   int32_t order_window;
-  int32_t reserved[4];
+  /* An interval holding more than long_values stored values is long too.
+   * 0 selects max(8 x mean values per interval, 2048 r). Shards of one
+   * matrix (spc5_convert_rows) given the same long_blocks and long_values
+   * classify their intervals as the whole matrix would. */
+  int32_t long_values;
+  int32_t reserved[3];
 } spc5_opts;
 
 /* Read-only device views of a handle's arrays (layout of Eq. 1 plus derived
@@ -140,6 +145,23 @@ typedef struct {
 spc5_status spc5_convert(int64_t n, int64_t m, int64_t nnz, const int64_t* rowptr_d, const int32_t* colidx_d,
                          const void* values_d, spc5_dtype vt, int r, int c, const spc5_opts* opt,
                          spc5_stream_t stream, spc5_handle* out);
+
+/*
+ * spc5_convert_rows - CSR rows [row_begin, row_end) -> a beta(r,c) handle of
+ * their own: one shard of the row-interval partition of section
+ * "Parallelization" (each worker owns consecutive row intervals, balanced by
+ * block count, see spc5_partition, and writes disjoint rows of y). The shard
+ * keeps the full column space (x has m entries); its rows are numbered from
+ * 0, so spc5_spmv(shard, x, y_d + row_begin) writes rows row_begin..row_end-1
+ * of A x. row_begin must be a multiple of r (shards start at interval
+ * boundaries), so a shard's intervals and blocks are those of the whole
+ * matrix; with the same opt->long_blocks its products equal the rows of the
+ * whole matrix's product bit for bit. Other arguments and errors as
+ * spc5_convert (plus SPC5_EINVAL for bad bounds). Synchronises `stream`.
+ */
+spc5_status spc5_convert_rows(int64_t n, int64_t m, int64_t nnz, const int64_t* rowptr_d, const int32_t* colidx_d,
+                              const void* values_d, spc5_dtype vt, int r, int c, int64_t row_begin, int64_t row_end,
+                              const spc5_opts* opt, spc5_stream_t stream, spc5_handle* out);
 
 /*
  * spc5_assemble - a handle from beta(r,c) arrays the caller built directly,

@@ -59,12 +59,68 @@ spc5_status spmv_common(spc5_handle h, const void* x, void* y, bool acc, cudaStr
   return SPC5_OK;
 }
 
+__global__ void k_rebase_rows(int64_t rows, int64_t row_begin, const int64_t* __restrict__ rowptr,
+                              int64_t* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i <= rows) out[i] = rowptr[row_begin + i] - rowptr[row_begin];
+}
+
 }  // namespace
 }  // namespace spc5
 
 using namespace spc5;
 
 extern "C" {
+
+spc5_status spc5_convert_rows(int64_t n, int64_t m, int64_t nnz, const int64_t* rowptr_d, const int32_t* colidx_d,
+                              const void* values_d, spc5_dtype vt, int r, int c, int64_t row_begin, int64_t row_end,
+                              const spc5_opts* opt, spc5_stream_t stream, spc5_handle* out) {
+  if (!out) return fail(SPC5_EINVAL, "convert_rows: out is NULL");
+  *out = nullptr;
+  spc5_status st = check_csr_args(n, m, nnz, rowptr_d, colidx_d, values_d);
+  if (st != SPC5_OK) return st;
+  if (!shape_supported(r, c)) return fail(SPC5_EUNSUPPORTED, "convert_rows: block shape must be r in {1,2,4,8}, c in {4,8,16}");
+  if (vt != SPC5_F64 && vt != SPC5_F32 && vt != SPC5_BF16) return fail(SPC5_EUNSUPPORTED, "convert_rows: value type");
+  if (row_begin < 0 || row_end < row_begin || row_end > n)
+    return fail(SPC5_EINVAL, "convert_rows: rows must satisfy 0 <= row_begin <= row_end <= n");
+  if (row_begin % r != 0) return fail(SPC5_EINVAL, "convert_rows: row_begin must be a multiple of r");
+  if (opt && (opt->long_blocks < 0 || opt->seg_blocks < 0 || opt->long_values < 0)) return fail(SPC5_EINVAL, "convert_rows: negative option");
+  if (opt && !valid_variant(opt->variant)) return fail(SPC5_EINVAL, "convert_rows: unknown variant");
+  if (opt && r1_variant(opt->variant) && r != 1) return fail(SPC5_EUNSUPPORTED, "convert_rows: variant needs r = 1");
+  const cudaStream_t s = (cudaStream_t)stream;
+  const int64_t rows = row_end - row_begin;
+  int64_t ends[2] = {0, 0};
+  if (rows > 0) {
+    cudaError_t e = cudaMemcpyAsync(&ends[0], rowptr_d + row_begin, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&ends[1], rowptr_d + row_end, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "convert_rows: row bounds");
+    if (ends[0] < 0 || ends[1] < ends[0] || ends[1] > nnz) return fail(SPC5_EINVAL, "convert_rows: bad row pointer");
+  }
+  // the rows' own CSR: a rebased row pointer, the column and value arrays
+  // from the shard's first entry; the column space stays [0, m)
+  int64_t* rp = nullptr;
+  cudaError_t e = cudaMallocAsync((void**)&rp, sizeof(int64_t) * (size_t)(rows + 1), s);
+  if (e != cudaSuccess) return cuda_fail(e, "convert_rows: row pointer");
+  if (rows > 0)
+    k_rebase_rows<<<(unsigned)((rows + 1 + 255) / 256), 256, 0, s>>>(rows, row_begin, rowptr_d, rp);
+  else
+    e = cudaMemsetAsync(rp, 0, sizeof(int64_t), s);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    cudaFreeAsync(rp, s);
+    return cuda_fail(e, "convert_rows: row pointer");
+  }
+  const int64_t snnz = ends[1] - ends[0];
+  const int32_t* col = snnz > 0 ? colidx_d + ends[0] : nullptr;
+  const void* val = snnz > 0 ? static_cast<const char*>(values_d) + (size_t)ends[0] * value_size(vt) : nullptr;
+  spc5_matrix* h = nullptr;
+  st = convert_impl(rows, m, snnz, rp, col, val, vt, r, c, opt, s, &h);
+  cudaFreeAsync(rp, s);
+  if (st != SPC5_OK) return st;
+  *out = h;
+  return SPC5_OK;
+}
 
 spc5_status spc5_convert(int64_t n, int64_t m, int64_t nnz, const int64_t* rowptr_d, const int32_t* colidx_d,
                          const void* values_d, spc5_dtype vt, int r, int c, const spc5_opts* opt,
@@ -75,7 +131,7 @@ spc5_status spc5_convert(int64_t n, int64_t m, int64_t nnz, const int64_t* rowpt
   if (st != SPC5_OK) return st;
   if (!shape_supported(r, c)) return fail(SPC5_EUNSUPPORTED, "convert: block shape must be r in {1,2,4,8}, c in {4,8,16}");
   if (vt != SPC5_F64 && vt != SPC5_F32 && vt != SPC5_BF16) return fail(SPC5_EUNSUPPORTED, "convert: value type");
-  if (opt && (opt->long_blocks < 0 || opt->seg_blocks < 0)) return fail(SPC5_EINVAL, "convert: negative option");
+  if (opt && (opt->long_blocks < 0 || opt->seg_blocks < 0 || opt->long_values < 0)) return fail(SPC5_EINVAL, "convert: negative option");
   if (opt && !valid_variant(opt->variant))
     return fail(SPC5_EINVAL, "convert: variant must be 0, 1, 3, 5, 9, 10, 12..19 or 22..31");
   if (opt && r1_variant(opt->variant) && r != 1)
@@ -99,7 +155,7 @@ spc5_status spc5_assemble(int64_t n, int64_t m, int64_t nnz, int64_t nblocks, co
   if (vt != SPC5_F64 && vt != SPC5_F32 && vt != SPC5_BF16) return fail(SPC5_EUNSUPPORTED, "assemble: value type");
   if (!block_rowptr_d || (nblocks > 0 && (!block_colidx_d || !block_masks_d)) || (nnz > 0 && !values_d))
     return fail(SPC5_EINVAL, "assemble: NULL array");
-  if (opt && (opt->long_blocks < 0 || opt->seg_blocks < 0)) return fail(SPC5_EINVAL, "assemble: negative option");
+  if (opt && (opt->long_blocks < 0 || opt->seg_blocks < 0 || opt->long_values < 0)) return fail(SPC5_EINVAL, "assemble: negative option");
   if (opt && !valid_variant(opt->variant))
     return fail(SPC5_EINVAL, "assemble: variant must be 0, 1, 3, 5, 9, 10, 12..19 or 22..31");
   if (opt && r1_variant(opt->variant) && r != 1)

@@ -1124,7 +1124,9 @@ spc5_status assemble_impl(int64_t n, int64_t m, int64_t nnz, int64_t nb, int r, 
     const double lim = 4.0 * mean;
     h->long_blocks = lim > kLongBlocks ? (lim < (double)INT_MAX ? (int32_t)lim : INT_MAX) : kLongBlocks;
   }
-  {
+  if (opt && opt->long_values > 0) {
+    h->long_values = opt->long_values;
+  } else {
     const double mean_v = I > 0 ? (double)nnz / (double)I : 0.0;
     const double lv = 8.0 * mean_v;
     h->long_values = lv > 2048.0 * r ? (int64_t)lv : (int64_t)2048 * r;
@@ -1276,7 +1278,9 @@ spc5_status convert_impl(int64_t n, int64_t m, int64_t nnz, const int64_t* rowpt
     const double lim = 4.0 * mean;
     h->long_blocks = lim > kLongBlocks ? (lim < (double)INT_MAX ? (int32_t)lim : INT_MAX) : kLongBlocks;
   }
-  {
+  if (opt && opt->long_values > 0) {
+    h->long_values = opt->long_values;
+  } else {
     // an interval is also long when it holds many more values than the mean
     const double mean_v = I > 0 ? (double)nnz / (double)I : 0.0;
     const double lv = 8.0 * mean_v;

@@ -34,7 +34,7 @@ class Spc5Error(RuntimeError):
 
 class Opts(ctypes.Structure):
     _fields_ = [("long_blocks", ctypes.c_int32), ("seg_blocks", ctypes.c_int32), ("variant", ctypes.c_int32),
-                ("order_window", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+                ("order_window", ctypes.c_int32), ("long_values", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 class CgOpts(ctypes.Structure):
@@ -111,6 +111,8 @@ def load(build_if_missing: bool = False):
     lib.spc5_fma_rate_lanes.argtypes = [i32, i64, i32, vp, vp, vp]
     lib.spc5_spmv_noalloc.argtypes = [vp, vp, vp, vp]
     lib.spc5_launch_count.argtypes = [vp, ctypes.POINTER(i32)]
+    lib.spc5_convert_rows.argtypes = [i64, i64, i64, vp, vp, vp, i32, i32, i32, i64, i64, ctypes.POINTER(Opts), vp,
+                                      ctypes.POINTER(vp)]
     lib.spc5_tune.argtypes = [i64, i64, i64, vp, vp, vp, i32, i32, i32, i32, ctypes.POINTER(TuneResult), vp]
     lib.spc5_tune_cache_clear.argtypes = []
     lib.spc5_device_peaks.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32), ctypes.POINTER(i32)]
@@ -133,7 +135,7 @@ def load(build_if_missing: bool = False):
     for f in (lib.spc5_convert, lib.spc5_assemble, lib.spc5_autotune, lib.spc5_spmv, lib.spc5_spmv_acc, lib.spc5_export, lib.spc5_destroy, lib.spc5_set_variant,
               lib.spc5_count_blocks, lib.spc5_csr_spmv, lib.spc5_copy, lib.spc5_fma_rate, lib.spc5_fma_rate_lanes,
               lib.spc5_spmv_noalloc, lib.spc5_launch_count, lib.spc5_device_peaks, lib.spc5_tune,
-              lib.spc5_tune_cache_clear, lib.spc5_cg, lib.spc5_spmm, lib.spc5_features,
+              lib.spc5_tune_cache_clear, lib.spc5_convert_rows, lib.spc5_cg, lib.spc5_spmm, lib.spc5_features,
               lib.spc5_time_formats, lib.spc5_mlp_train, lib.spc5_mlp_grad, lib.spc5_mlp_infer, lib.spc5_poly_fit,
               lib.spc5_select, lib.spc5_batch_create, lib.spc5_batch_spmv, lib.spc5_batch_spmv_direct,
               lib.spc5_batch_destroy, lib.spc5_partition):
@@ -286,7 +288,7 @@ class Matrix:
 
 def convert(rowptr: torch.Tensor, colidx: torch.Tensor, values: torch.Tensor, n: int, m: int, r: int, c: int,
             long_blocks: int = 0, seg_blocks: int = 0, variant: int = 0, order_window: int = 0,
-            stream=None) -> Matrix:
+            long_values: int = 0, stream=None) -> Matrix:
     """CSR (device tensors: int64 rowptr, int32 colidx, values) -> beta(r,c)."""
     if rowptr.dtype != torch.int64 or colidx.dtype != torch.int32:
         raise TypeError("rowptr must be int64 and colidx int32")
@@ -294,11 +296,28 @@ def convert(rowptr: torch.Tensor, colidx: torch.Tensor, values: torch.Tensor, n:
         raise TypeError("values must be float64, float32 or bfloat16")
     vt = _VALUE_DTYPE[values.dtype]
     nnz = values.numel()
-    opts = Opts(long_blocks, seg_blocks, variant, order_window)
+    opts = Opts(long_blocks, seg_blocks, variant, order_window, long_values)
     h = ctypes.c_void_p()
     _check(load().spc5_convert(n, m, nnz, _ptr(rowptr), _ptr(colidx), _ptr(values), vt, r, c, ctypes.byref(opts),
                                _stream_ptr(stream), ctypes.byref(h)), "spc5_convert")
     return Matrix(h.value, n, m, nnz, r, c, vt)
+
+
+def convert_rows(rowptr: torch.Tensor, colidx: torch.Tensor, values: torch.Tensor, n: int, m: int, r: int, c: int,
+                 row_begin: int, row_end: int, long_blocks: int = 0, seg_blocks: int = 0, variant: int = 0,
+                 order_window: int = 0, long_values: int = 0, stream=None) -> Matrix:
+    """Rows [row_begin, row_end) of a device CSR -> a shard handle (full column space, rows from 0)."""
+    if rowptr.dtype != torch.int64 or colidx.dtype != torch.int32:
+        raise TypeError("rowptr must be int64 and colidx int32")
+    vt = _VALUE_DTYPE[values.dtype]
+    opts = Opts(long_blocks, seg_blocks, variant, order_window, long_values)
+    h = ctypes.c_void_p()
+    _check(load().spc5_convert_rows(n, m, values.numel(), _ptr(rowptr), _ptr(colidx), _ptr(values), vt, r, c,
+                                    row_begin, row_end, ctypes.byref(opts), _stream_ptr(stream), ctypes.byref(h)),
+           "spc5_convert_rows")
+    M = Matrix(h.value, row_end - row_begin, m, 0, r, c, vt)
+    M.nnz = int(M.arrays().nnz)
+    return M
 
 
 def assemble(n: int, m: int, r: int, c: int, block_rowptr: torch.Tensor, block_colidx: torch.Tensor,
