@@ -328,6 +328,7 @@ def matrix_entry(p, tlist, key, hbm_peak, roofline=None):
     A = p["A"]
     gbs = beta_bytes(p, *VSIZE[key]) / t / 1e6
     e = {"matrix": p["name"], "n": A.n, "nnz": A.nnz, "shape": f"{p['r']}x{p['c']}", "variant": p["variant"],
+         "convert_ms": round(p["convert_ms"], 3), "convert_over_spmv": round(p["convert_ms"] / t, 2),
          "avg_nnz_per_block": round(A.nnz / max(p["nblocks"], 1), 3), "segments": p["nseg"], "ms": round(t, 4),
          "gflops": round(2.0 * A.nnz / t / 1e6, 1), "gbs": round(gbs, 1), "hbm_frac": round(gbs / hbm_peak, 4),
          "sweep_gflops": p["sweep_gflops"]}
@@ -783,9 +784,18 @@ def main():
                     csr_best = (t, g)
             _, M, r, c, v = best
             ex = M.export()
+            # conversion cost of the selected form (wall clock of spc5_convert, best of 3)
+            conv = []
+            for _ in range(3):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                M2 = spc5.convert(d.rowptr, d.colidx, d.values, A.n, A.m, r, c, variant=v)
+                torch.cuda.synchronize()
+                conv.append((time.perf_counter() - t0) * 1e3)
+                M2.destroy()
             out.append({"name": mt["name"], "A": A, "d": d, "x": xd, "y": yd, "M": M, "r": r, "c": c, "variant": v,
                         "nblocks": ex["nblocks"], "nseg": ex["nsegments"], "csr_group": csr_best[1],
-                        "sweep_gflops": sweep})
+                        "sweep_gflops": sweep, "convert_ms": min(conv)})
         return out
 
     def run_steps(prep, K, W, fn_name="beta", sampler=None):

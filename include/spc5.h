@@ -258,8 +258,15 @@ spc5_status spc5_launch_count(spc5_handle h, int* kernels_out);
 spc5_status spc5_device_peaks(double* hbm_gbs_out, int* sm_count_out, int* sm_clock_mhz_out);
 
 /* spc5_destroy - free the handle and its device arrays (synchronises the
- * device first so that no queued kernel still reads them). NULL is allowed. */
+ * device first so that no queued kernel still reads them). NULL is allowed.
+ * The arrays of converted handles go back to a memory pool of the library's
+ * own (one per device), which keeps them for the next conversion instead of
+ * returning them to the driver; see spc5_pool_trim. */
 spc5_status spc5_destroy(spc5_handle h);
+
+/* spc5_pool_trim - return the memory the library's handle pools keep for
+ * reuse to the driver (the arrays of live handles stay). No device work. */
+spc5_status spc5_pool_trim(void);
 
 /* spc5_last_error - message of the last failed call on this host thread. */
 const char* spc5_last_error(void);

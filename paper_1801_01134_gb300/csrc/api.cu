@@ -213,6 +213,12 @@ spc5_status spc5_export(spc5_handle h, spc5_arrays* v) {
   return SPC5_OK;
 }
 
+spc5_status spc5_pool_trim(void) {
+  cudaError_t e = trim_pools();
+  if (e != cudaSuccess) return cuda_fail(e, "pool_trim");
+  return SPC5_OK;
+}
+
 spc5_status spc5_launch_count(spc5_handle h, int* kernels_out) {
   if (!h || !kernels_out) return fail(SPC5_EINVAL, "launch_count: NULL argument");
   *kernels_out = spmv_launches(h);

@@ -10,7 +10,10 @@
 //   2. k_count      (r > 1) one thread per interval: greedy leftmost cover of
 //                   the merged columns of the interval's r rows -> blocks per
 //                   interval, and the number of warp segments of long ones.
-//      k_r1_flags   (r = 1) block starts marked over the entries (see there).
+//      k_r1_flags   (r = 1) block starts marked over the entries, one bit
+//                   each (see there); the block index of an entry is then
+//                   the scanned popcount of the mark words before it plus
+//                   the marks below it in its word.
 //   3. scan         exclusive prefix sums -> block_rowptr, segment pointers.
 //   4. k_fill       (r > 1) one thread per interval: the same cover again,
 //                   emitting block_colidx, the r*c-bit masks, each block's
@@ -23,6 +26,7 @@
 // for r > 1, the same marks for r = 1), so the two passes agree.
 #include <algorithm>
 #include <climits>
+#include <mutex>
 #include <vector>
 
 #include "internal.cuh"
@@ -142,19 +146,23 @@ __global__ void __launch_bounds__(256) k_validate_cols(int64_t n, int64_t m, int
 // right one, so the right column starts a block in any cover. The runs
 // between such gaps are covered independently, so the work spreads over the
 // entries (one thread per kEntriesPerThread entries, each walking the runs
-// that start in its range) instead of one thread per row. Pass 1 marks the
-// entries that start a block; an exclusive scan of the marks numbers the
-// blocks in storage order (rows in order, blocks by column); pass 2 writes
-// each block's column, mask and, for long rows, its segment record. With one
-// row per interval the values keep CSR order and are copied as they are.
+// that start in its range) instead of one thread per row. Pass 1 sets one
+// bit per entry that starts a block (nnz/8 bytes of marks); an exclusive scan
+// of the popcounts of the 32-bit mark words numbers the blocks in storage
+// order (rows in order, blocks by column), the block of a marked entry being
+// the prefix of its word plus the marks below it; pass 2 writes each block's
+// column, mask and, for long rows, its segment record. With one row per
+// interval the values keep CSR order and are copied as they are.
 __global__ void k_r1_flags(int64_t n, int64_t nnz, int c, const int64_t* __restrict__ rowptr,
-                           const int32_t* __restrict__ colidx, int32_t* __restrict__ flags) {
+                           const int32_t* __restrict__ colidx, uint32_t* __restrict__ marks) {
+  static_assert(32 % kEntriesPerThread == 0, "a thread's entries share one mark word");
   const int64_t j0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * kEntriesPerThread;
   if (j0 >= nnz) return;
   const int64_t j1 = j0 + kEntriesPerThread < nnz ? j0 + kEntriesPerThread : nnz;
   int64_t row = row_of_entry(rowptr, n, j0);
   int64_t rs = rowptr[row], re = rowptr[row + 1];
   int32_t prev = j0 > rs ? colidx[j0 - 1] : 0;
+  uint32_t mine = 0u;  // marks of this thread's own entries (one word); others by atomicOr
   for (int64_t j = j0; j < j1; ++j) {
     while (j >= re) {
       ++row;
@@ -167,32 +175,50 @@ __global__ void k_r1_flags(int64_t n, int64_t nnz, int c, const int64_t* __restr
     if (!run_start) continue;
     // greedy cover of the run that starts here
     int32_t s0 = col, last = col;
-    flags[j] = 1;
+    mine |= 1u << (j & 31);
     for (int64_t k = j + 1; k < re; ++k) {
       const int32_t ck = colidx[k];
       if (ck - last >= c) break;  // the next run
       if (ck - s0 >= c) {
         s0 = ck;
-        flags[k] = 1;
+        if (k < j1)
+          mine |= 1u << (k & 31);
+        else
+          atomicOr(marks + (k >> 5), 1u << (k & 31));
       }
       last = ck;
     }
   }
+  if (mine) atomicOr(marks + (j0 >> 5), mine);
 }
 
-// block_rowptr[i] = blocks before row i; counts[i] = blocks of row i
-__global__ void k_r1_rowptr(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ bidx,
+// popcount of every mark word (the scan input)
+__global__ void k_mark_counts(int64_t nwords, const uint32_t* __restrict__ marks, int32_t* __restrict__ counts) {
+  const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (w < nwords) counts[w] = __popc(marks[w]);
+}
+
+// blocks that start before entry e: marks in whole words before e's word
+// (prefix) plus those below e in its word
+__device__ __forceinline__ int32_t blocks_before(int64_t e, int64_t nwords, const uint32_t* __restrict__ marks,
+                                                 const int32_t* __restrict__ prefix) {
+  const int64_t w = e >> 5;
+  if (w >= nwords) return prefix[nwords];
+  return prefix[w] + __popc(marks[w] & ((1u << (e & 31)) - 1u));
+}
+
+__global__ void k_r1_rowptr(int64_t n, const int64_t* __restrict__ rowptr, int64_t nwords,
+                            const uint32_t* __restrict__ marks, const int32_t* __restrict__ prefix,
                             int32_t* __restrict__ brp, int32_t* __restrict__ counts) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i > n) return;
-  const int32_t b = bidx[rowptr[i]];
+  const int32_t b = blocks_before(rowptr[i], nwords, marks, prefix);
   brp[i] = b;
-  if (i < n) counts[i] = bidx[rowptr[i + 1]] - b;
+  if (i < n) counts[i] = blocks_before(rowptr[i + 1], nwords, marks, prefix) - b;
 }
-
 __global__ void k_r1_fill(int64_t n, int64_t nnz, int c, int mb, int seg_blocks, const int64_t* __restrict__ rowptr,
-                          const int32_t* __restrict__ colidx, const int32_t* __restrict__ flags,
-                          const int32_t* __restrict__ bidx, const int32_t* __restrict__ brp,
+                          const int32_t* __restrict__ colidx, int64_t nwords, const uint32_t* __restrict__ marks,
+                          const int32_t* __restrict__ prefix, const int32_t* __restrict__ brp,
                           const int32_t* __restrict__ segptr, int32_t* __restrict__ bcol,
                           uint8_t* __restrict__ bmask, Segment* __restrict__ segs) {
   const int64_t j0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * kEntriesPerThread;
@@ -205,8 +231,9 @@ __global__ void k_r1_fill(int64_t n, int64_t nnz, int c, int mb, int seg_blocks,
       ++row;
       re = rowptr[row + 1];
     }
-    if (!flags[j]) continue;
-    const int32_t b = bidx[j];
+    const uint32_t word = marks[j >> 5];
+    if (!((word >> (j & 31)) & 1u)) continue;
+    const int32_t b = prefix[j >> 5] + __popc(word & ((1u << (j & 31)) - 1u));
     const int32_t s0 = colidx[j];
     uint32_t mask = 0u;
     for (int64_t k = j; k < re; ++k) {
@@ -635,7 +662,9 @@ void free_matrix(spc5_matrix* h) {
   cudaFree(h->block_rowptr);
   cudaFree(h->seg_first);
   if (h->arena) {
-    cudaFree(h->arena);
+    // pool memory: freed in stream order (the conversion's stream while a
+    // conversion fails, the legacy stream after spc5_destroy's device sync)
+    cudaFreeAsync(h->arena, h->arena_stream);
   } else {
     cudaFree(h->block_colidx);
     cudaFree(h->block_masks);
@@ -645,6 +674,42 @@ void free_matrix(spc5_matrix* h) {
     cudaFree(h->partials);
   }
   delete h;
+}
+
+// The handles' arenas come from a memory pool of the library's own (one per
+// device) that keeps freed memory for the next handle instead of returning
+// it to the driver: a fresh cudaMalloc of a 1.6 GB handle costs more than
+// its conversion kernels, and conversions of one matrix to several shapes,
+// or of one structure at every time step, come in series. spc5_pool_trim
+// hands the kept memory back.
+constexpr int kMaxPoolDevices = 64;
+std::mutex g_pool_mu;
+cudaMemPool_t g_pools[kMaxPoolDevices] = {};
+
+cudaError_t handle_pool(cudaMemPool_t* out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxPoolDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_pool_mu);
+  if (!g_pools[dev]) {
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t p = nullptr;
+    e = cudaMemPoolCreate(&p, &props);
+    if (e != cudaSuccess) return e;
+    uint64_t keep = UINT64_MAX;  // never release on synchronisation
+    e = cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+    if (e != cudaSuccess) {
+      cudaMemPoolDestroy(p);
+      return e;
+    }
+    g_pools[dev] = p;
+  }
+  *out = g_pools[dev];
+  return cudaSuccess;
 }
 
 // One allocation for the arrays whose sizes are known once the blocks are
@@ -662,9 +727,12 @@ cudaError_t alloc_arena(spc5_matrix* h, int64_t nb, int64_t nnz, int64_t ns, cud
     total += ((bytes[q] + 16 + 255) / 256) * 256;
   }
   uint8_t* base = nullptr;
-  cudaError_t e = cudaMalloc((void**)&base, total);
+  cudaMemPool_t pool = nullptr;
+  cudaError_t e = handle_pool(&pool);
+  if (e == cudaSuccess) e = cudaMallocFromPoolAsync((void**)&base, total, pool, s);
   if (e != cudaSuccess) return e;
   h->arena = base;
+  h->arena_stream = s;
   h->block_colidx = reinterpret_cast<int32_t*>(base + off[0]);
   h->block_masks = base + off[1];
   h->values = base + off[2];
@@ -1025,7 +1093,21 @@ __global__ void k_asm_seg_fill(int64_t I, int seg_blocks, const int32_t* __restr
   }
 }
 
-void destroy_matrix(spc5_matrix* h) { free_matrix(h); }
+void destroy_matrix(spc5_matrix* h) {
+  h->arena_stream = nullptr;  // the caller synchronised the device; its stream may be gone
+  free_matrix(h);
+}
+
+cudaError_t trim_pools() {
+  std::lock_guard<std::mutex> lock(g_pool_mu);
+  cudaError_t e = cudaSuccess;
+  for (int d = 0; d < kMaxPoolDevices; ++d)
+    if (g_pools[d]) {
+      const cudaError_t e2 = cudaMemPoolTrimTo(g_pools[d], 0);
+      if (e == cudaSuccess) e = e2;
+    }
+  return e;
+}
 
 spc5_status assemble_impl(int64_t n, int64_t m, int64_t nnz, int64_t nb, int r, int c, spc5_dtype vt,
                           const int32_t* brp_in, const int32_t* bcol_in, const uint8_t* bmask_in, const void* vals_in,
@@ -1242,21 +1324,27 @@ spc5_status convert_impl(int64_t n, int64_t m, int64_t nnz, const int64_t* rowpt
   if (e != cudaSuccess) return bail(cuda_fail(e, "convert: block_rowptr"));
   int64_t nb = 0, ns = 0;
   spc5_status st = SPC5_OK;
-  DeviceBuf flags, bidx;  // r = 1: block-start marks over the entries and their scan
+  DeviceBuf marks, wcount, wprefix;  // r = 1: one block-start bit per entry, prefix of the word popcounts
   const int64_t eth = (nnz + kEntriesPerThread - 1) / kEntriesPerThread;
+  const int64_t nwords = (nnz + 31) / 32;
   if (r == 1) {
-    e = flags.alloc(sizeof(int32_t) * (size_t)(nnz + 1), s);
-    if (e == cudaSuccess) e = bidx.alloc(sizeof(int32_t) * (size_t)(nnz + 1), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(flags.p, 0, sizeof(int32_t) * (size_t)(nnz + 1), s);
+    e = marks.alloc(sizeof(uint32_t) * (size_t)(nwords + 1), s);
+    if (e == cudaSuccess) e = wcount.alloc(sizeof(int32_t) * (size_t)(nwords + 1), s);
+    if (e == cudaSuccess) e = wprefix.alloc(sizeof(int32_t) * (size_t)(nwords + 1), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(marks.p, 0, sizeof(uint32_t) * (size_t)(nwords + 1), s);
     if (e != cudaSuccess)
       return bail(e == cudaErrorMemoryAllocation ? fail(SPC5_ENOMEM, "convert: out of device memory")
                                                  : cuda_fail(e, "convert: block marks"));
     if (eth > 0)
-      k_r1_flags<<<(unsigned)((eth + 255) / 256), 256, 0, s>>>(n, nnz, c, rowptr, colidx, (int32_t*)flags.p);
-    st = scan_counts((const int32_t*)flags.p, nnz, (int32_t*)bidx.p, &nb, s);
+      k_r1_flags<<<(unsigned)((eth + 255) / 256), 256, 0, s>>>(n, nnz, c, rowptr, colidx, (uint32_t*)marks.p);
+    if (nwords > 0)
+      k_mark_counts<<<(unsigned)((nwords + 255) / 256), 256, 0, s>>>(nwords, (const uint32_t*)marks.p,
+                                                                     (int32_t*)wcount.p);
+    st = scan_counts((const int32_t*)wcount.p, nwords, (int32_t*)wprefix.p, &nb, s);
     if (st != SPC5_OK) return bail(st);
     if (n > 0)
-      k_r1_rowptr<<<(unsigned)((n + 1 + 255) / 256), 256, 0, s>>>(n, rowptr, (const int32_t*)bidx.p, h->block_rowptr,
+      k_r1_rowptr<<<(unsigned)((n + 1 + 255) / 256), 256, 0, s>>>(n, rowptr, nwords, (const uint32_t*)marks.p,
+                                                                  (const int32_t*)wprefix.p, h->block_rowptr,
                                                                   (int32_t*)counts.p);
     e = cudaGetLastError();
     if (e != cudaSuccess) return bail(cuda_fail(e, "convert: block numbering"));
@@ -1305,9 +1393,9 @@ spc5_status convert_impl(int64_t n, int64_t m, int64_t nnz, const int64_t* rowpt
   if (r == 1) {
     if (eth > 0)
       k_r1_fill<<<(unsigned)((eth + 255) / 256), 256, 0, s>>>(n, nnz, c, h->mb, h->seg_blocks, rowptr, colidx,
-                                                              (const int32_t*)flags.p, (const int32_t*)bidx.p,
-                                                              h->block_rowptr, sp, h->block_colidx, h->block_masks,
-                                                              h->segs);
+                                                              nwords, (const uint32_t*)marks.p,
+                                                              (const int32_t*)wprefix.p, h->block_rowptr, sp,
+                                                              h->block_colidx, h->block_masks, h->segs);
     if (nnz > 0) {
       e = cudaGetLastError();
       if (e == cudaSuccess)

@@ -74,6 +74,7 @@ struct spc5_matrix {
   // when not NULL, one allocation holding block_colidx, block_masks, values,
   // valptr, segs and partials (freed as a whole)
   void* arena = nullptr;
+  cudaStream_t arena_stream = nullptr;  // stream of the arena's pool allocation
   // work order of the lane-per-row kernel (short intervals only)
   int64_t norder = 0;
   int32_t* order = nullptr;            // [norder] interval indices
@@ -131,6 +132,7 @@ cudaError_t launch_csr_spmv_group(int group, int64_t n, int64_t nnz, const int64
                                   const void* values, spc5_dtype vt, const void* x, void* y, cudaStream_t s);
 int csr_auto_group(int64_t n, int64_t nnz, spc5_dtype vt);
 void destroy_matrix(spc5_matrix* h);
+cudaError_t trim_pools();
 cudaError_t launch_copy(const void* src, void* dst, int64_t bytes, cudaStream_t s);
 cudaError_t launch_fma_rate(spc5_dtype vt, int64_t iters, int lanes, void* sink, int64_t* fmas, cudaStream_t s);
 

@@ -111,6 +111,7 @@ def load(build_if_missing: bool = False):
     lib.spc5_fma_rate_lanes.argtypes = [i32, i64, i32, vp, vp, vp]
     lib.spc5_spmv_noalloc.argtypes = [vp, vp, vp, vp]
     lib.spc5_launch_count.argtypes = [vp, ctypes.POINTER(i32)]
+    lib.spc5_pool_trim.argtypes = []
     lib.spc5_convert_rows.argtypes = [i64, i64, i64, vp, vp, vp, i32, i32, i32, i64, i64, ctypes.POINTER(Opts), vp,
                                       ctypes.POINTER(vp)]
     lib.spc5_tune.argtypes = [i64, i64, i64, vp, vp, vp, i32, i32, i32, i32, ctypes.POINTER(TuneResult), vp]
@@ -135,7 +136,7 @@ def load(build_if_missing: bool = False):
     for f in (lib.spc5_convert, lib.spc5_assemble, lib.spc5_autotune, lib.spc5_spmv, lib.spc5_spmv_acc, lib.spc5_export, lib.spc5_destroy, lib.spc5_set_variant,
               lib.spc5_count_blocks, lib.spc5_csr_spmv, lib.spc5_copy, lib.spc5_fma_rate, lib.spc5_fma_rate_lanes,
               lib.spc5_spmv_noalloc, lib.spc5_launch_count, lib.spc5_device_peaks, lib.spc5_tune,
-              lib.spc5_tune_cache_clear, lib.spc5_convert_rows, lib.spc5_cg, lib.spc5_spmm, lib.spc5_features,
+              lib.spc5_tune_cache_clear, lib.spc5_convert_rows, lib.spc5_pool_trim, lib.spc5_cg, lib.spc5_spmm, lib.spc5_features,
               lib.spc5_time_formats, lib.spc5_mlp_train, lib.spc5_mlp_grad, lib.spc5_mlp_infer, lib.spc5_poly_fit,
               lib.spc5_select, lib.spc5_batch_create, lib.spc5_batch_spmv, lib.spc5_batch_spmv_direct,
               lib.spc5_batch_destroy, lib.spc5_partition):
@@ -357,6 +358,11 @@ def tune(d: "DeviceCSR", k_spmm: int = 0, reps: int = 5, use_cache: bool = True,
     _check(load().spc5_tune(d.n, d.m, d.nnz, _ptr(d.rowptr), _ptr(d.colidx), _ptr(d.values), vt, k_spmm, reps,
                             0 if use_cache else TUNE_NO_CACHE, ctypes.byref(res), _stream_ptr(stream)), "spc5_tune")
     return {f: getattr(res, f) for f, _ in TuneResult._fields_}
+
+
+def pool_trim():
+    """Return the memory the library keeps for reuse by later conversions."""
+    _check(load().spc5_pool_trim(), "spc5_pool_trim")
 
 
 def tune_cache_clear():

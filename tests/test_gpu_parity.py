@@ -565,3 +565,18 @@ def test_copy_kernel(cuda_device):
     b = torch.zeros_like(a)
     spc5.copy(a, b)
     assert torch.equal(a, b)
+
+
+def test_pool_trim_between_conversions(cuda_device):
+    # handle memory kept by the library's pool is reused, and can be handed back
+    A = get("fem")
+    d = dev_csr(A)
+    x = torch.from_numpy(inputs.vec_uniform(A.m, seed=0)).cuda()
+    M = spc5.convert(d.rowptr, d.colidx, d.values, A.n, A.m, 1, 8)
+    ref = M.spmv(x).clone()
+    M.destroy()
+    for _ in range(2):
+        M = spc5.convert(d.rowptr, d.colidx, d.values, A.n, A.m, 1, 8)
+        assert torch.equal(M.spmv(x), ref)
+        M.destroy()
+        spc5.pool_trim()
