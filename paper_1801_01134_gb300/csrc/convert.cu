@@ -91,6 +91,32 @@ __device__ __forceinline__ int64_t row_of_entry(const int64_t* __restrict__ rowp
   return lo;
 }
 
+// Row hints: the row of the first entry of every chunk of kHintChunk entries
+// (and of entry nnz), so that an entry's row is searched between the rows of
+// its chunk's ends - a few steps - instead of over all rows.
+constexpr int kHintShift = 8;
+constexpr int64_t kHintChunk = int64_t(1) << kHintShift;
+
+__global__ void k_row_hints(int64_t n, int64_t nnz, const int64_t* __restrict__ rowptr, int64_t* __restrict__ hints) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nch = (nnz + kHintChunk - 1) / kHintChunk;
+  if (k > nch) return;
+  const int64_t j = k * kHintChunk < nnz ? k * kHintChunk : (nnz > 0 ? nnz - 1 : 0);
+  hints[k] = row_of_entry(rowptr, n, j);
+}
+
+// the row of entry j (same result as row_of_entry) from the hints
+__device__ __forceinline__ int64_t row_of_entry_hint(const int64_t* __restrict__ rowptr, int64_t n,
+                                                     const int64_t* __restrict__ hints, int64_t j) {
+  int64_t lo = hints[j >> kHintShift], hi = hints[(j >> kHintShift) + 1] + 1;
+  if (hi > n) hi = n;
+  while (hi - lo > 1) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (rowptr[mid] <= j) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
 // A warp checks 2048 consecutive entries with coalesced loads: the rows that
 // start inside the chunk become a bitmap (from the row pointers), then each
 // entry is checked for range and, unless it starts a row, against its left
@@ -154,12 +180,13 @@ __global__ void __launch_bounds__(256) k_validate_cols(int64_t n, int64_t m, int
 // column, mask and, for long rows, its segment record. With one row per
 // interval the values keep CSR order and are copied as they are.
 __global__ void k_r1_flags(int64_t n, int64_t nnz, int c, const int64_t* __restrict__ rowptr,
-                           const int32_t* __restrict__ colidx, uint32_t* __restrict__ marks) {
+                           const int32_t* __restrict__ colidx, const int64_t* __restrict__ hints,
+                           uint32_t* __restrict__ marks) {
   static_assert(32 % kEntriesPerThread == 0, "a thread's entries share one mark word");
   const int64_t j0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * kEntriesPerThread;
   if (j0 >= nnz) return;
   const int64_t j1 = j0 + kEntriesPerThread < nnz ? j0 + kEntriesPerThread : nnz;
-  int64_t row = row_of_entry(rowptr, n, j0);
+  int64_t row = row_of_entry_hint(rowptr, n, hints, j0);
   int64_t rs = rowptr[row], re = rowptr[row + 1];
   int32_t prev = j0 > rs ? colidx[j0 - 1] : 0;
   uint32_t mine = 0u;  // marks of this thread's own entries (one word); others by atomicOr
@@ -216,15 +243,25 @@ __global__ void k_r1_rowptr(int64_t n, const int64_t* __restrict__ rowptr, int64
   brp[i] = b;
   if (i < n) counts[i] = blocks_before(rowptr[i + 1], nwords, marks, prefix) - b;
 }
+template <class W>
 __global__ void k_r1_fill(int64_t n, int64_t nnz, int c, int mb, int seg_blocks, const int64_t* __restrict__ rowptr,
-                          const int32_t* __restrict__ colidx, int64_t nwords, const uint32_t* __restrict__ marks,
-                          const int32_t* __restrict__ prefix, const int32_t* __restrict__ brp,
+                          const int32_t* __restrict__ colidx, const int64_t* __restrict__ hints,
+                          const W* __restrict__ vin, W* __restrict__ vout, int64_t nwords,
+                          const uint32_t* __restrict__ marks, const int32_t* __restrict__ prefix,
+                          const int32_t* __restrict__ brp,
                           const int32_t* __restrict__ segptr, int32_t* __restrict__ bcol,
                           uint8_t* __restrict__ bmask, Segment* __restrict__ segs) {
+  // the values keep CSR order (one row per interval): the warp copies its
+  // 32 x kEntriesPerThread entries' values with coalesced accesses
+  {
+    const int64_t wbase = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * (32 * kEntriesPerThread);
+    for (int64_t q = wbase + (threadIdx.x & 31); q < wbase + 32 * kEntriesPerThread && q < nnz; q += 32)
+      vout[q] = vin[q];
+  }
   const int64_t j0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * kEntriesPerThread;
   if (j0 >= nnz) return;
   const int64_t j1 = j0 + kEntriesPerThread < nnz ? j0 + kEntriesPerThread : nnz;
-  int64_t row = row_of_entry(rowptr, n, j0);
+  int64_t row = row_of_entry_hint(rowptr, n, hints, j0);
   int64_t re = rowptr[row + 1];
   for (int64_t j = j0; j < j1; ++j) {
     while (j >= re) {
@@ -389,14 +426,15 @@ __global__ void k_fill(int64_t n, int64_t I, int c, int mb, int seg_blocks, cons
 // through the interval's blocks in order, so only the first needs a search.
 template <int R, class VT>
 __global__ void k_fill_values(int64_t n, int64_t nnz, int c, int mb, const int64_t* __restrict__ rowptr,
-                              const int32_t* __restrict__ colidx, const VT* __restrict__ values,
+                              const int32_t* __restrict__ colidx, const int64_t* __restrict__ hints,
+                              const VT* __restrict__ values,
                               const int32_t* __restrict__ brp, const int32_t* __restrict__ bcol,
                               const uint8_t* __restrict__ bmask, const int32_t* __restrict__ bvo,
                               VT* __restrict__ bval) {
   const int64_t j0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * kEntriesPerThread;
   if (j0 >= nnz) return;
   const int64_t j1 = j0 + kEntriesPerThread < nnz ? j0 + kEntriesPerThread : nnz;
-  int64_t row = row_of_entry(rowptr, n, j0);
+  int64_t row = row_of_entry_hint(rowptr, n, hints, j0);
   int64_t re = rowptr[row + 1];
   int64_t it = row / R, vstart = rowptr[it * R];
   int i = (int)(row - it * R);
@@ -631,16 +669,17 @@ void launch_fill_r(int r, int64_t n, int64_t I, int c, int mb, int sb, const int
 
 template <class VT>
 void launch_fill_values(int r, int64_t n, int64_t nnz, int c, int mb, const int64_t* rowptr, const int32_t* colidx,
-                        const void* values, const int32_t* bvo, spc5_matrix* h, cudaStream_t s) {
+                        const int64_t* hints, const void* values, const int32_t* bvo, spc5_matrix* h,
+                        cudaStream_t s) {
   const int64_t th = (nnz + kEntriesPerThread - 1) / kEntriesPerThread;
   if (th == 0) return;
   const unsigned grid = (unsigned)((th + 255) / 256);
   const VT* v = (const VT*)values;
   VT* bv = (VT*)h->values;
   switch (r) {
-    case 2: k_fill_values<2, VT><<<grid, 256, 0, s>>>(n, nnz, c, mb, rowptr, colidx, v, h->block_rowptr, h->block_colidx, h->block_masks, bvo, bv); break;
-    case 4: k_fill_values<4, VT><<<grid, 256, 0, s>>>(n, nnz, c, mb, rowptr, colidx, v, h->block_rowptr, h->block_colidx, h->block_masks, bvo, bv); break;
-    default: k_fill_values<8, VT><<<grid, 256, 0, s>>>(n, nnz, c, mb, rowptr, colidx, v, h->block_rowptr, h->block_colidx, h->block_masks, bvo, bv); break;
+    case 2: k_fill_values<2, VT><<<grid, 256, 0, s>>>(n, nnz, c, mb, rowptr, colidx, hints, v, h->block_rowptr, h->block_colidx, h->block_masks, bvo, bv); break;
+    case 4: k_fill_values<4, VT><<<grid, 256, 0, s>>>(n, nnz, c, mb, rowptr, colidx, hints, v, h->block_rowptr, h->block_colidx, h->block_masks, bvo, bv); break;
+    default: k_fill_values<8, VT><<<grid, 256, 0, s>>>(n, nnz, c, mb, rowptr, colidx, hints, v, h->block_rowptr, h->block_colidx, h->block_masks, bvo, bv); break;
   }
 }
 
@@ -1325,8 +1364,13 @@ spc5_status convert_impl(int64_t n, int64_t m, int64_t nnz, const int64_t* rowpt
   int64_t nb = 0, ns = 0;
   spc5_status st = SPC5_OK;
   DeviceBuf marks, wcount, wprefix;  // r = 1: one block-start bit per entry, prefix of the word popcounts
+  DeviceBuf hints;                   // rows of the entry chunks (r = 1 passes, r > 1 value pass)
   const int64_t eth = (nnz + kEntriesPerThread - 1) / kEntriesPerThread;
   const int64_t nwords = (nnz + 31) / 32;
+  const int64_t nhint = (nnz + kHintChunk - 1) / kHintChunk;
+  e = hints.alloc(sizeof(int64_t) * (size_t)(nhint + 2), s);
+  if (e != cudaSuccess) return bail(cuda_fail(e, "convert: row hints"));
+  if (eth > 0) k_row_hints<<<(unsigned)((nhint + 1 + 255) / 256), 256, 0, s>>>(n, nnz, rowptr, (int64_t*)hints.p);
   if (r == 1) {
     e = marks.alloc(sizeof(uint32_t) * (size_t)(nwords + 1), s);
     if (e == cudaSuccess) e = wcount.alloc(sizeof(int32_t) * (size_t)(nwords + 1), s);
@@ -1335,8 +1379,10 @@ spc5_status convert_impl(int64_t n, int64_t m, int64_t nnz, const int64_t* rowpt
     if (e != cudaSuccess)
       return bail(e == cudaErrorMemoryAllocation ? fail(SPC5_ENOMEM, "convert: out of device memory")
                                                  : cuda_fail(e, "convert: block marks"));
-    if (eth > 0)
-      k_r1_flags<<<(unsigned)((eth + 255) / 256), 256, 0, s>>>(n, nnz, c, rowptr, colidx, (uint32_t*)marks.p);
+    if (eth > 0) {
+      k_r1_flags<<<(unsigned)((eth + 255) / 256), 256, 0, s>>>(n, nnz, c, rowptr, colidx, (const int64_t*)hints.p,
+                                                               (uint32_t*)marks.p);
+    }
     if (nwords > 0)
       k_mark_counts<<<(unsigned)((nwords + 255) / 256), 256, 0, s>>>(nwords, (const uint32_t*)marks.p,
                                                                      (int32_t*)wcount.p);
@@ -1392,16 +1438,22 @@ spc5_status convert_impl(int64_t n, int64_t m, int64_t nnz, const int64_t* rowpt
   const int32_t* sp = ns > 0 ? (const int32_t*)segptr.p : nullptr;
   if (r == 1) {
     if (eth > 0)
-      k_r1_fill<<<(unsigned)((eth + 255) / 256), 256, 0, s>>>(n, nnz, c, h->mb, h->seg_blocks, rowptr, colidx,
-                                                              nwords, (const uint32_t*)marks.p,
-                                                              (const int32_t*)wprefix.p, h->block_rowptr, sp,
-                                                              h->block_colidx, h->block_masks, h->segs);
-    if (nnz > 0) {
-      e = cudaGetLastError();
-      if (e == cudaSuccess)
-        e = cudaMemcpyAsync(h->values, values, value_size(vt) * (size_t)nnz, cudaMemcpyDeviceToDevice, s);
-      if (e != cudaSuccess) return bail(cuda_fail(e, "convert: values"));
+    {
+      auto fill = [&](auto w) {
+        using W = decltype(w);
+        k_r1_fill<W><<<(unsigned)((eth + 255) / 256), 256, 0, s>>>(
+            n, nnz, c, h->mb, h->seg_blocks, rowptr, colidx, (const int64_t*)hints.p, static_cast<const W*>(values),
+            static_cast<W*>(h->values), nwords, (const uint32_t*)marks.p, (const int32_t*)wprefix.p,
+            h->block_rowptr, sp, h->block_colidx, h->block_masks, h->segs);
+      };
+      switch (vt) {
+        case SPC5_F64: fill(uint64_t{}); break;
+        case SPC5_F32: fill(uint32_t{}); break;
+        default: fill(uint16_t{}); break;
+      }
     }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return bail(cuda_fail(e, "convert: fill"));
   } else {
     DeviceBuf bvo;  // value offset of each block inside its interval
     e = bvo.alloc(sizeof(int32_t) * (size_t)(nb > 0 ? nb : 1), s);
@@ -1410,9 +1462,9 @@ spc5_status convert_impl(int64_t n, int64_t m, int64_t nnz, const int64_t* rowpt
                                                  : cuda_fail(e, "convert: block offsets"));
     launch_fill_r(r, n, I, c, h->mb, h->seg_blocks, rowptr, colidx, h->block_rowptr, sp, (int32_t*)bvo.p, h, s);
     switch (vt) {
-      case SPC5_F64: launch_fill_values<uint64_t>(r, n, nnz, c, h->mb, rowptr, colidx, values, (const int32_t*)bvo.p, h, s); break;
-      case SPC5_F32: launch_fill_values<uint32_t>(r, n, nnz, c, h->mb, rowptr, colidx, values, (const int32_t*)bvo.p, h, s); break;
-      default: launch_fill_values<uint16_t>(r, n, nnz, c, h->mb, rowptr, colidx, values, (const int32_t*)bvo.p, h, s); break;
+      case SPC5_F64: launch_fill_values<uint64_t>(r, n, nnz, c, h->mb, rowptr, colidx, (const int64_t*)hints.p, values, (const int32_t*)bvo.p, h, s); break;
+      case SPC5_F32: launch_fill_values<uint32_t>(r, n, nnz, c, h->mb, rowptr, colidx, (const int64_t*)hints.p, values, (const int32_t*)bvo.p, h, s); break;
+      default: launch_fill_values<uint16_t>(r, n, nnz, c, h->mb, rowptr, colidx, (const int64_t*)hints.p, values, (const int32_t*)bvo.p, h, s); break;
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return bail(cuda_fail(e, "convert: fill"));
