@@ -612,14 +612,54 @@ __global__ void k_scan_apply(const int32_t* __restrict__ in, int64_t L, const in
   if (blockIdx.x == 0 && threadIdx.x == 0) out[L] = (int32_t)*grand_total;
 }
 
-// Scratch memory taken from the device's stream-ordered pool: allocation and
-// release are queued on the conversion stream, so neither waits for the GPU.
+// The handles' arenas come from a memory pool of the library's own (one per
+// device) that keeps freed memory for the next handle instead of returning
+// it to the driver: a fresh cudaMalloc of a 1.6 GB handle costs more than
+// its conversion kernels, and conversions of one matrix to several shapes,
+// or of one structure at every time step, come in series. spc5_pool_trim
+// hands the kept memory back.
+constexpr int kMaxPoolDevices = 64;
+std::mutex g_pool_mu;
+cudaMemPool_t g_pools[kMaxPoolDevices] = {};
+
+cudaError_t handle_pool(cudaMemPool_t* out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxPoolDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_pool_mu);
+  if (!g_pools[dev]) {
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t p = nullptr;
+    e = cudaMemPoolCreate(&p, &props);
+    if (e != cudaSuccess) return e;
+    uint64_t keep = UINT64_MAX;  // never release on synchronisation
+    e = cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+    if (e != cudaSuccess) {
+      cudaMemPoolDestroy(p);
+      return e;
+    }
+    g_pools[dev] = p;
+  }
+  *out = g_pools[dev];
+  return cudaSuccess;
+}
+
+// Scratch memory taken from the library's pool: allocation and release are
+// queued on the conversion stream, so neither waits for the GPU, and the
+// memory stays in the pool for the next conversion.
 struct DeviceBuf {
   void* p = nullptr;
   cudaStream_t s = nullptr;
   cudaError_t alloc(size_t bytes, cudaStream_t st) {
     s = st;
-    return cudaMallocAsync(&p, bytes > 0 ? bytes : 16, st);
+    cudaMemPool_t pool = nullptr;
+    cudaError_t e = handle_pool(&pool);
+    if (e != cudaSuccess) return e;
+    return cudaMallocFromPoolAsync(&p, bytes > 0 ? bytes : 16, pool, st);
   }
   ~DeviceBuf() {
     if (p) cudaFreeAsync(p, s);
@@ -693,62 +733,31 @@ void count_r(int r, int64_t n, int64_t I, int c, const int64_t* rowptr, const in
   }
 }
 
+// The handle's arrays are pool memory, freed in stream order: on the
+// conversion's stream while a conversion fails, on the legacy stream after
+// spc5_destroy's device synchronisation (the SpMM scratch is cudaMalloc'd).
 void free_matrix(spc5_matrix* h) {
   if (!h) return;
-  cudaFree(h->order);
-  cudaFree(h->single_bits);
+  const cudaStream_t s = h->arena_stream;
+  auto release = [s](void* p) {
+    if (p) cudaFreeAsync(p, s);
+  };
+  release(h->order);
+  release(h->single_bits);
   cudaFree(h->spmm_scratch);
-  cudaFree(h->block_rowptr);
-  cudaFree(h->seg_first);
+  release(h->block_rowptr);
+  release(h->seg_first);
   if (h->arena) {
-    // pool memory: freed in stream order (the conversion's stream while a
-    // conversion fails, the legacy stream after spc5_destroy's device sync)
-    cudaFreeAsync(h->arena, h->arena_stream);
+    release(h->arena);
   } else {
-    cudaFree(h->block_colidx);
-    cudaFree(h->block_masks);
-    cudaFree(h->values);
-    cudaFree(h->valptr);
-    cudaFree(h->segs);
-    cudaFree(h->partials);
+    release(h->block_colidx);
+    release(h->block_masks);
+    release(h->values);
+    release(h->valptr);
+    release(h->segs);
+    release(h->partials);
   }
   delete h;
-}
-
-// The handles' arenas come from a memory pool of the library's own (one per
-// device) that keeps freed memory for the next handle instead of returning
-// it to the driver: a fresh cudaMalloc of a 1.6 GB handle costs more than
-// its conversion kernels, and conversions of one matrix to several shapes,
-// or of one structure at every time step, come in series. spc5_pool_trim
-// hands the kept memory back.
-constexpr int kMaxPoolDevices = 64;
-std::mutex g_pool_mu;
-cudaMemPool_t g_pools[kMaxPoolDevices] = {};
-
-cudaError_t handle_pool(cudaMemPool_t* out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= kMaxPoolDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_pool_mu);
-  if (!g_pools[dev]) {
-    cudaMemPoolProps props = {};
-    props.allocType = cudaMemAllocationTypePinned;
-    props.location.type = cudaMemLocationTypeDevice;
-    props.location.id = dev;
-    cudaMemPool_t p = nullptr;
-    e = cudaMemPoolCreate(&p, &props);
-    if (e != cudaSuccess) return e;
-    uint64_t keep = UINT64_MAX;  // never release on synchronisation
-    e = cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
-    if (e != cudaSuccess) {
-      cudaMemPoolDestroy(p);
-      return e;
-    }
-    g_pools[dev] = p;
-  }
-  *out = g_pools[dev];
-  return cudaSuccess;
 }
 
 // One allocation for the arrays whose sizes are known once the blocks are
@@ -785,10 +794,13 @@ cudaError_t alloc_arena(spc5_matrix* h, int64_t nb, int64_t nnz, int64_t ns, cud
   return e;
 }
 
-// allocation padded to a multiple of 16 bytes plus 16 (bulk copies may round up)
+// allocation padded to a multiple of 16 bytes plus 16 (bulk copies may round
+// up), zeroed, from the library's pool in the order of stream s
 cudaError_t alloc_padded(void** p, size_t bytes, cudaStream_t s) {
   size_t b = ((bytes + 15) / 16) * 16 + 16;
-  cudaError_t e = cudaMalloc(p, b);
+  cudaMemPool_t pool = nullptr;
+  cudaError_t e = handle_pool(&pool);
+  if (e == cudaSuccess) e = cudaMallocFromPoolAsync(p, b, pool, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(*p, 0, b, s);
   return e;
 }
@@ -959,7 +971,7 @@ spc5_status build_single_bits(spc5_matrix* h, cudaStream_t s) {
   if (e == cudaSuccess) e = cudaMemcpyAsync(&nset, cnt.p, sizeof(nset), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
-    cudaFree(d);
+    cudaFreeAsync(d, s);
     return cuda_fail(e, "single-value bits");
   }
   h->single_bits = d;
@@ -1006,7 +1018,7 @@ spc5_status build_order(spc5_matrix* h, cudaStream_t s) {
       }
       if (e == cudaSuccess) e = cudaStreamSynchronize(s);
       if (e != cudaSuccess) {
-        cudaFree(d);
+        cudaFreeAsync(d, s);
         return cuda_fail(e, "work order: sort");
       }
     }
@@ -1040,7 +1052,7 @@ spc5_status build_order(spc5_matrix* h, cudaStream_t s) {
       e = cudaMemcpyAsync(d, order.data(), sizeof(int32_t) * order.size(), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
-      cudaFree(d);
+      cudaFreeAsync(d, s);
       return cuda_fail(e, "work order: upload");
     }
     h->order = d;
@@ -1153,6 +1165,7 @@ spc5_status assemble_impl(int64_t n, int64_t m, int64_t nnz, int64_t nb, int r, 
                           const spc5_opts* opt, cudaStream_t s, spc5_matrix** out) {
   *out = nullptr;
   spc5_matrix* h = new spc5_matrix();
+  h->arena_stream = s;  // failures free the arrays in this stream's order
   h->n = n;
   h->m = m;
   h->nnz = nnz;
@@ -1301,6 +1314,7 @@ spc5_status convert_impl(int64_t n, int64_t m, int64_t nnz, const int64_t* rowpt
                          spc5_matrix** out) {
   *out = nullptr;
   spc5_matrix* h = new spc5_matrix();
+  h->arena_stream = s;  // failures free the arrays in this stream's order
   h->n = n;
   h->m = m;
   h->nnz = nnz;
