@@ -777,11 +777,26 @@ def main():
                     best = (t, M, r, c, v)
                 else:
                     M.destroy()
-            csr_best = None
+            # the CSR comparator: plain (G lanes per row) and with long rows split into
+            # warp segments like the β path (CsrPlan); the fastest is kept
+            csr_best, csr_plain = None, None
             for g in (1, 2, 4, 8, 16, 32):
                 t = time_call(lambda: spc5.csr_spmv(d.rowptr, d.colidx, d.values, A.n, A.m, xd, yd, group=g), 5)
-                if csr_best is None or t < csr_best[0]:
-                    csr_best = (t, g)
+                if csr_plain is None or t < csr_plain[0]:
+                    csr_plain = (t, g)
+                P = spc5.CsrPlan(d, group=g)
+                if P.nsegments > 0:
+                    tp = time_call(lambda: P.spmv(xd, yd), 5)
+                    if csr_best is None or tp < csr_best[0]:
+                        if csr_best is not None and csr_best[2] is not None:
+                            csr_best[2].destroy()
+                        csr_best = (tp, g, P)
+                        continue
+                P.destroy()
+            if csr_best is None or csr_plain[0] <= csr_best[0]:
+                if csr_best is not None:
+                    csr_best[2].destroy()
+                csr_best = (csr_plain[0], csr_plain[1], None)
             _, M, r, c, v = best
             ex = M.export()
             # conversion cost of the selected form (wall clock of spc5_convert, best of 3)
@@ -795,6 +810,7 @@ def main():
                 M2.destroy()
             out.append({"name": mt["name"], "A": A, "d": d, "x": xd, "y": yd, "M": M, "r": r, "c": c, "variant": v,
                         "nblocks": ex["nblocks"], "nseg": ex["nsegments"], "csr_group": csr_best[1],
+                        "csr_plan": csr_best[2], "csr_plain_ms": csr_plain[0],
                         "sweep_gflops": sweep, "convert_ms": min(conv)})
         return out
 
@@ -807,6 +823,8 @@ def main():
                 e0.record(stream)
                 if fn_name == "beta":
                     p["M"].spmv(p["x"], p["y"])
+                elif p["csr_plan"] is not None:
+                    p["csr_plan"].spmv(p["x"], p["y"])
                 else:
                     A, d = p["A"], p["d"]
                     spc5.csr_spmv(d.rowptr, d.colidx, d.values, A.n, A.m, p["x"], p["y"], group=p["csr_group"])
@@ -816,16 +834,20 @@ def main():
         torch.cuda.synchronize()
         return {k: [a.elapsed_time(b) for a, b in v] for k, v in per.items()}
 
-    def csr_section(prep, K, key, beta_value):
-        """The plain CSR kernel (lanes per row tuned per matrix) under the same protocol."""
+    def csr_section(prep, K, key, beta_value, beta_times):
+        """The CSR comparator (lanes per row tuned per matrix, long rows split into warp
+        segments when that is faster) under the same protocol."""
         ct = run_steps(prep, K, 1, fn_name="csr")
         cms = sum(sum(v) for v in ct.values())
         cval = sum(2.0 * p["A"].nnz for p in prep) * K / (cms * 1e-3) / 1e9
         per = {}
         for p in prep:
             tc = statistics.median(ct[p["name"]])
-            per[p["name"]] = {"group": p["csr_group"], "gflops": round(2.0 * p["A"].nnz / tc / 1e6, 1),
-                              "gbs": round(csr_bytes(p, *VSIZE[key]) / tc / 1e6, 1)}
+            per[p["name"]] = {"group": p["csr_group"], "long_rows_split": p["csr_plan"] is not None,
+                              "gflops": round(2.0 * p["A"].nnz / tc / 1e6, 1),
+                              "gbs": round(csr_bytes(p, *VSIZE[key]) / tc / 1e6, 1),
+                              "plain_gflops": round(2.0 * p["A"].nnz / p["csr_plain_ms"] / 1e6, 1),
+                              "beta_over_csr": round(tc / statistics.median(beta_times[p["name"]]), 3)}
         return {"value": round(cval, 2), "unit": "GFLOP/s", "per_matrix": per,
                 "speedup_beta_over_csr": round(beta_value / cval, 3)}
 
@@ -935,7 +957,7 @@ def main():
                        "peak_measured by the library's multiply-add probe in this run"}
 
     # ---- CSR comparator, same protocol
-    csr64 = csr_section(prep64, args.steps, "f64", value)
+    csr64 = csr_section(prep64, args.steps, "f64", value, times)
 
     # ---- end to end: pinned host x -> device, SpMV, y -> pinned host, every step
     e2e = run_e2e(prep64, args.steps, stream, ws, dev, flops_step)
@@ -947,6 +969,8 @@ def main():
     y64_ref = {p["name"]: p["M"].spmv(p["x"]).clone() for p in prep64}
     for p in prep64:
         p["M"].destroy()
+        if p["csr_plan"] is not None:
+            p["csr_plan"].destroy()
         del p["d"]
     torch.cuda.empty_cache()
 
@@ -963,10 +987,12 @@ def main():
                               for p in prep],
                "roofline": roof(d, t[d["name"]], key)}
         sec["hbm_frac"] = round(sec["hbm_gbs"] / hbm_peak, 4)
-        sec["csr"] = csr_section(prep, args.steps, key, sec["value"])
+        sec["csr"] = csr_section(prep, args.steps, key, sec["value"], t)
         sec["error_vs_float64"] = precision_errors(prep, y64_ref)
         for p in prep:
             p["M"].destroy()
+            if p["csr_plan"] is not None:
+                p["csr_plan"].destroy()
             del p["d"]
         torch.cuda.empty_cache()
         low[key] = sec

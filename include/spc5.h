@@ -294,6 +294,34 @@ spc5_status spc5_csr_spmv(int64_t n, int64_t m, int64_t nnz, const int64_t* rowp
                           const void* values_d, spc5_dtype vt, const void* x_d, void* y_d, int group,
                           spc5_stream_t stream);
 
+/* CSR with long rows split (the comparator with the β path's load balancing) */
+typedef struct spc5_csr_plan_s* spc5_csr_plan;
+
+/*
+ * spc5_csr_plan_create - an execution plan for y = A x on plain CSR that
+ * balances power-law rows the way the β path does: rows of more than
+ * long_len entries are cut into segments of seg_len entries, one warp per
+ * segment (partial sums, then a fix-up adds a row's segments in order), and
+ * the other rows take `group` lanes each, all in one grid. rowptr_d (int64,
+ * n + 1) is the caller's and must stay valid and unchanged while the plan
+ * lives. group as spc5_csr_spmv (0 = from the mean row length); long_len 0 =
+ * max(1024, 16 x mean row length); seg_len 0 = 1024. Synchronises `stream`.
+ */
+spc5_status spc5_csr_plan_create(int64_t n, int64_t nnz, const int64_t* rowptr_d, spc5_dtype vt, int group,
+                                 int64_t long_len, int64_t seg_len, spc5_stream_t stream, spc5_csr_plan* out);
+
+/* spc5_csr_spmv_plan - y = A x with a plan (colidx_d, values_d of the
+ * plan's CSR; types and vectors as spc5_csr_spmv). Runs repeat bit for bit. */
+spc5_status spc5_csr_spmv_plan(spc5_csr_plan p, const int32_t* colidx_d, const void* values_d, const void* x_d,
+                               void* y_d, spc5_stream_t stream);
+
+/* spc5_csr_plan_info - the plan's lanes per short row, long-row threshold and
+ * segment count (any output may be NULL). */
+spc5_status spc5_csr_plan_info(spc5_csr_plan p, int* group_out, int64_t* long_len_out, int64_t* nseg_out);
+
+/* spc5_csr_plan_destroy - free the plan (synchronises the device). NULL is allowed. */
+spc5_status spc5_csr_plan_destroy(spc5_csr_plan p);
+
 /*
  * spc5_partition - the static partition of the row intervals among `nparts`
  * workers (section "Parallelization"): walking the intervals in order, the

@@ -1144,6 +1144,17 @@ __global__ void k_asm_seg_fill(int64_t I, int seg_blocks, const int32_t* __restr
   }
 }
 
+spc5_status exclusive_scan_i32(const int32_t* in, int64_t L, int32_t* out, int64_t* total_host, cudaStream_t s) {
+  return scan_counts(in, L, out, total_host, s);
+}
+
+cudaError_t pool_alloc(void** p, size_t bytes, cudaStream_t s) {
+  cudaMemPool_t pool = nullptr;
+  cudaError_t e = handle_pool(&pool);
+  if (e == cudaSuccess) e = cudaMallocFromPoolAsync(p, bytes > 0 ? bytes : 16, pool, s);
+  return e;
+}
+
 void destroy_matrix(spc5_matrix* h) {
   h->arena_stream = nullptr;  // the caller synchronised the device; its stream may be gone
   free_matrix(h);

@@ -133,6 +133,10 @@ cudaError_t launch_csr_spmv_group(int group, int64_t n, int64_t nnz, const int64
 int csr_auto_group(int64_t n, int64_t nnz, spc5_dtype vt);
 void destroy_matrix(spc5_matrix* h);
 cudaError_t trim_pools();
+// exclusive scan of int32 counts into out[0..L] (out[L] = total, returned to
+// the host; synchronises s) and an allocation from the library's pool
+spc5_status exclusive_scan_i32(const int32_t* in, int64_t L, int32_t* out, int64_t* total_host, cudaStream_t s);
+cudaError_t pool_alloc(void** p, size_t bytes, cudaStream_t s);
 cudaError_t launch_copy(const void* src, void* dst, int64_t bytes, cudaStream_t s);
 cudaError_t launch_fma_rate(spc5_dtype vt, int64_t iters, int lanes, void* sink, int64_t* fmas, cudaStream_t s);
 

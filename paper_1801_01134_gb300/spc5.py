@@ -112,6 +112,10 @@ def load(build_if_missing: bool = False):
     lib.spc5_spmv_noalloc.argtypes = [vp, vp, vp, vp]
     lib.spc5_launch_count.argtypes = [vp, ctypes.POINTER(i32)]
     lib.spc5_pool_trim.argtypes = []
+    lib.spc5_csr_plan_create.argtypes = [i64, i64, vp, i32, i32, i64, i64, vp, ctypes.POINTER(vp)]
+    lib.spc5_csr_spmv_plan.argtypes = [vp, vp, vp, vp, vp, vp]
+    lib.spc5_csr_plan_info.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i64), ctypes.POINTER(i64)]
+    lib.spc5_csr_plan_destroy.argtypes = [vp]
     lib.spc5_convert_rows.argtypes = [i64, i64, i64, vp, vp, vp, i32, i32, i32, i64, i64, ctypes.POINTER(Opts), vp,
                                       ctypes.POINTER(vp)]
     lib.spc5_tune.argtypes = [i64, i64, i64, vp, vp, vp, i32, i32, i32, i32, ctypes.POINTER(TuneResult), vp]
@@ -136,7 +140,8 @@ def load(build_if_missing: bool = False):
     for f in (lib.spc5_convert, lib.spc5_assemble, lib.spc5_autotune, lib.spc5_spmv, lib.spc5_spmv_acc, lib.spc5_export, lib.spc5_destroy, lib.spc5_set_variant,
               lib.spc5_count_blocks, lib.spc5_csr_spmv, lib.spc5_copy, lib.spc5_fma_rate, lib.spc5_fma_rate_lanes,
               lib.spc5_spmv_noalloc, lib.spc5_launch_count, lib.spc5_device_peaks, lib.spc5_tune,
-              lib.spc5_tune_cache_clear, lib.spc5_convert_rows, lib.spc5_pool_trim, lib.spc5_cg, lib.spc5_spmm, lib.spc5_features,
+              lib.spc5_tune_cache_clear, lib.spc5_convert_rows, lib.spc5_pool_trim, lib.spc5_csr_plan_create,
+              lib.spc5_csr_spmv_plan, lib.spc5_csr_plan_info, lib.spc5_csr_plan_destroy, lib.spc5_cg, lib.spc5_spmm, lib.spc5_features,
               lib.spc5_time_formats, lib.spc5_mlp_train, lib.spc5_mlp_grad, lib.spc5_mlp_infer, lib.spc5_poly_fit,
               lib.spc5_select, lib.spc5_batch_create, lib.spc5_batch_spmv, lib.spc5_batch_spmv_direct,
               lib.spc5_batch_destroy, lib.spc5_partition):
@@ -367,6 +372,38 @@ def pool_trim():
 
 def tune_cache_clear():
     _check(load().spc5_tune_cache_clear(), "spc5_tune_cache_clear")
+
+
+class CsrPlan:
+    """Plain CSR with long rows split into warp segments (spc5_csr_plan_*)."""
+
+    def __init__(self, d: "DeviceCSR", group: int = 0, long_len: int = 0, seg_len: int = 0, stream=None):
+        vt = _VALUE_DTYPE[d.values.dtype]
+        p = ctypes.c_void_p()
+        _check(load().spc5_csr_plan_create(d.n, d.nnz, _ptr(d.rowptr), vt, group, long_len, seg_len,
+                                           _stream_ptr(stream), ctypes.byref(p)), "spc5_csr_plan_create")
+        self._p, self.d = p.value, d
+        g, ll, ns = ctypes.c_int(), ctypes.c_int64(), ctypes.c_int64()
+        _check(load().spc5_csr_plan_info(self._p, ctypes.byref(g), ctypes.byref(ll), ctypes.byref(ns)), "spc5_csr_plan_info")
+        self.group, self.long_len, self.nsegments = g.value, ll.value, ns.value
+
+    def spmv(self, x: torch.Tensor, y: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        if y is None:
+            y = torch.empty(self.d.n, dtype=x.dtype, device=x.device)
+        _check(load().spc5_csr_spmv_plan(self._p, _ptr(self.d.colidx), _ptr(self.d.values), _ptr(x), _ptr(y),
+                                         _stream_ptr(stream)), "spc5_csr_spmv_plan")
+        return y
+
+    def destroy(self):
+        if self._p is not None:
+            load().spc5_csr_plan_destroy(self._p)
+            self._p = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
 
 
 def count_blocks(rowptr: torch.Tensor, colidx: torch.Tensor, n: int, m: int, stream=None) -> np.ndarray:
