@@ -101,11 +101,21 @@ __device__ __forceinline__ void rows_grp_body(int64_t bid, int64_t n, int64_t I,
   A acc[R];
 #pragma unroll
   for (int i = 0; i < R; ++i) acc[i] = A(0);
+  // the next trip's mask and column are read one trip ahead
+  Mask<MB> nmk = b0 + g < b1 ? load_mask<MB>(bmask, b0 + g) : zero_mask<MB>();
+  int32_t ncol = b0 + g < b1 ? __ldg(bcol + b0 + g) : 0;
   for (int32_t bb = b0; bb < b1; bb += G) {
     const int32_t b = bb + g;
     const bool have = b < b1;
-    const Mask<MB> mk = have ? load_mask<MB>(bmask, b) : zero_mask<MB>();
-    const int32_t col = have ? __ldg(bcol + b) : 0;
+    const Mask<MB> mk = nmk;
+    const int32_t col = ncol;
+    if (b + G < b1) {
+      nmk = load_mask<MB>(bmask, b + G);
+      ncol = __ldg(bcol + b + G);
+    } else {
+      nmk = zero_mask<MB>();
+      ncol = 0;
+    }
     const int cnt = popc_all(mk);
     int incl = cnt;  // inclusive scan of the popcounts over the group
 #pragma unroll

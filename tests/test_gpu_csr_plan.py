@@ -22,7 +22,7 @@ def test_csr_plan_against_oracle(cuda_device, name, group, long_len, seg_len):
     y_ref, absy = oracle.csr_spmv_dot2(A, x)
     d = spc5.upload_csr(A, torch.float64, "cuda")
     P = spc5.CsrPlan(d, group=group, long_len=long_len, seg_len=seg_len)
-    if long_len == 3:
+    if long_len == 3 and np.diff(A.rowptr).max() > 3:
         assert P.nsegments > 0
     xd = torch.from_numpy(x).cuda()
     buf = torch.full((A.n + 16,), float("nan"), dtype=torch.float64, device="cuda")
