@@ -513,21 +513,27 @@ def run_batch_section(dev, count: int = 256, reps: int = 20):
 
 # ------------------------------------------------------------------------ CG
 
-def run_cg_section(dev, reps: int = 3):
+def run_cg_section(dev, reps: int = 3, shifted: bool = False):
     """Time float64 CG and mixed float32 / bfloat16 refinement to ||r|| / ||b|| <= 1e-10
-    on the 7-point Poisson matrix of a 96^3 grid (b uniform[-1,1] seed 0)."""
+    on the 7-point Poisson matrix of a 96^3 grid (b uniform[-1,1] seed 0). Its values
+    6 / -1 are exact in float32 and bfloat16, so the low-precision inner matrices equal
+    the float64 one there; with shifted=True the diagonal is raised by a seeded uniform
+    [0, 1) draw per row, and the inner matrices are rounded copies."""
     import torch
 
     from paper_1801_01134_gb300 import inputs, spc5
 
-    A = inputs.stencil3d(96, 96, 96, points=7, normal_values=False)
+    A = inputs.poisson_shifted(96, 96, 96, seed=4) if shifted else \
+        inputs.stencil3d(96, 96, 96, points=7, normal_values=False)
     b = torch.from_numpy(inputs.vec_uniform(A.n, seed=0)).to(dev)
     hs = {}
     for name, dt in (("f64", torch.float64), ("f32", torch.float32), ("bf16", torch.bfloat16)):
         d = spc5.upload_csr(A, dt, dev)
         hs[name] = spc5.convert(d.rowptr, d.colidx, d.values, A.n, A.m, 2, 4,
                                 variant=0 if name == "f64" else CG_INNER_VARIANT)
-    out = {"workload": "7-point Poisson 96^3 (n=884,736, nnz=6,137,856), b uniform[-1,1] seed 0, tol 1e-10",
+    out = {"workload": ("7-point Poisson 96^3, diagonal 6 + uniform[0,1) seed 4 (values round in bf16 / f32)" if shifted
+                        else "7-point Poisson 96^3 (values 6 / -1, exact in bf16 and f32)") +
+                       " (n=884,736, nnz=6,137,856), b uniform[-1,1] seed 0, tol 1e-10",
            "format": f"beta(2,4); float64 handle variant 5, inner handles variant {CG_INNER_VARIANT}"}
     for label, inner, rel in (("fp64_cg", None, False), ("mixed_f32", hs["f32"], False),
                               ("mixed_bf16", hs["bf16"], False), ("reliable_f32", hs["f32"], True),
@@ -999,6 +1005,7 @@ def main():
 
     # ---- precision form: float64 CG vs mixed-precision refinement, 7-point Poisson 96^3
     cg_res = run_cg_section(dev)
+    cg_res["shifted"] = run_cg_section(dev, shifted=True)
     # ---- batched form: multi-RHS SpMM, float32; many uneven matrices in one launch
     spmm_res = run_spmm_section(mats, dev)
     batch_res = run_batch_section(dev)

@@ -28,6 +28,7 @@ _LIB = os.path.join(_HERE, "libspc5gen.so")
 # streams of the vector generators (the matrix builders use their own)
 STREAM_X = 1
 STREAM_B = 2
+STREAM_SHIFT = 3
 
 
 def build(force: bool = False) -> str:
@@ -170,6 +171,20 @@ def banded(n: int, half_bw: int, density: float, seed: int = 1) -> CSR:
 def random_csr(n: int, m: int, density: float, seed: int = 1) -> CSR:
     """Small Bernoulli(density) sparse matrix for tests."""
     return _take(_load().gen_random(n, m, density, seed))
+
+
+def poisson_shifted(nx: int, ny: int, nz: int, seed: int = 4) -> CSR:
+    """7-point Poisson matrix with its diagonal 6 raised by a seeded uniform
+    draw in [0, 1) per row: still symmetric and strictly diagonally dominant
+    (positive definite), but its diagonal values are no longer exact in
+    bfloat16 or float32."""
+    A = stencil3d(nx, ny, nz, points=7, normal_values=False)
+    shift = vec_uniform(A.n, seed=seed, stream=STREAM_SHIFT, lo=0.0, hi=1.0)
+    rows = np.repeat(np.arange(A.n, dtype=np.int64), np.diff(A.rowptr))
+    on_diag = A.colidx.astype(np.int64) == rows
+    vals = np.array(A.values, dtype=np.float64, copy=True)
+    vals[on_diag] = vals[on_diag] + shift[rows[on_diag]]
+    return CSR(A.n, A.m, A.rowptr, A.colidx, vals)
 
 
 def vec_uniform(n: int, seed: int = 0, stream: int = STREAM_X, lo: float = -1.0, hi: float = 1.0) -> np.ndarray:

@@ -89,6 +89,23 @@ def test_reliable_updates_reach_float64_residual(cuda_device, low):
     assert info2 == info and torch.equal(x, x2)
 
 
+@pytest.mark.parametrize("low", [torch.float32, torch.bfloat16])
+@pytest.mark.parametrize("reliable", [False, True])
+def test_low_precision_cg_on_values_that_round(cuda_device, low, reliable):
+    # the Poisson values 6 / -1 are exact in bfloat16, so the inner matrix of
+    # the tests above equals the float64 one; with a random diagonal shift the
+    # inner matrix is a rounded copy and the float64 residual has to correct it
+    A = inputs.poisson_shifted(24, 24, 24, seed=4)
+    rnd = oracle.round_bf16 if low == torch.bfloat16 else oracle.round_f32
+    assert np.count_nonzero(rnd(A.values) != A.values) > A.n // 2
+    b = inputs.vec_uniform(A.n, seed=0)
+    M64, Ml = handles(A, low=low)
+    x, info = spc5.cg(M64, torch.from_numpy(b).cuda(), A_inner=Ml, tol=1e-10, use_graph=True, reliable=reliable)
+    assert info["converged"] and true_residual(A, x.cpu().numpy(), b) <= 1e-10
+    if not reliable:
+        assert info["outer"] >= 2  # at least one correction of the rounded solve
+
+
 def test_cg_full_size_poisson96(cuda_device):
     # the precision-form CG workload: 7-point Poisson on a 96^3 grid, b uniform[-1,1] seed 0
     A = poisson(96)

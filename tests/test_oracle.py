@@ -436,3 +436,14 @@ def test_spmm_oracle_against_dense_matmul_and_linearity():
         X2 = inputs.vec_dyadic(m * k, seed=seed + 7, bits=10).reshape(m, k)
         Ad = inputs.CSR(A.n, A.m, A.rowptr, A.colidx, inputs.vec_dyadic(A.nnz, seed=3, bits=10))
         assert np.array_equal(oracle.csr_spmm(Ad, X1 + X2), oracle.csr_spmm(Ad, X1) + oracle.csr_spmm(Ad, X2))
+
+
+def test_poisson_shifted_is_symmetric_and_diagonally_dominant():
+    A = inputs.poisson_shifted(5, 4, 3, seed=4)
+    D = A.to_dense()
+    assert np.array_equal(D, D.T)
+    off = np.abs(D).sum(axis=1) - np.abs(np.diag(D))
+    assert np.all(np.diag(D) > off)  # strictly dominant: positive definite
+    assert np.all((np.diag(D) >= 6.0) & (np.diag(D) < 7.0))
+    P = inputs.stencil3d(5, 4, 3, points=7, normal_values=False).to_dense()
+    assert np.array_equal(D - np.diag(np.diag(D)), P - np.diag(np.diag(P)))
