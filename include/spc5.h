@@ -365,6 +365,24 @@ spc5_status spc5_copy(const void* src_d, void* dst_d, int64_t bytes, spc5_stream
 spc5_status spc5_spmm(spc5_handle h, int k, const void* X_d, int64_t ldx, void* Y_d, int64_t ldy, int ktile,
                       spc5_stream_t stream);
 
+/* ------------------------------------------------------- SM-limited streams */
+/*
+ * spc5_sm_stream_create - a stream whose kernels run on about `sms` SMs of the
+ * current device only: the SM-count axis that stands in, on one GPU, for the
+ * thread count of the paper's parallel predictor (section "Performance
+ * prediction and optimal kernel selection"). Built on a green context (a
+ * process-local SM partition; no device setting changes): the count is
+ * rounded up to the driver's partition granularity (a multiple of 8 SMs on
+ * this architecture) and written to *sms_out (nullable); sms at or above the
+ * SM count gives the whole GPU. Any library call may be given the stream.
+ * SPC5_EUNSUPPORTED when the driver offers no green contexts.
+ */
+spc5_status spc5_sm_stream_create(int sms, spc5_stream_t* stream_out, int* sms_out);
+
+/* spc5_sm_stream_destroy - synchronise and free a stream of
+ * spc5_sm_stream_create (and its green context). NULL is allowed. */
+spc5_status spc5_sm_stream_destroy(spc5_stream_t stream);
+
 /* ------------------------------------------------------------------ tuner */
 #define SPC5_TUNE_NO_CACHE 1 /* spc5_tune flag: time again even when the signature is known */
 

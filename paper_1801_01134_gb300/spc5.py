@@ -112,6 +112,8 @@ def load(build_if_missing: bool = False):
     lib.spc5_spmv_noalloc.argtypes = [vp, vp, vp, vp]
     lib.spc5_launch_count.argtypes = [vp, ctypes.POINTER(i32)]
     lib.spc5_pool_trim.argtypes = []
+    lib.spc5_sm_stream_create.argtypes = [i32, ctypes.POINTER(vp), ctypes.POINTER(i32)]
+    lib.spc5_sm_stream_destroy.argtypes = [vp]
     lib.spc5_csr_plan_create.argtypes = [i64, i64, vp, i32, i32, i64, i64, vp, ctypes.POINTER(vp)]
     lib.spc5_csr_spmv_plan.argtypes = [vp, vp, vp, vp, vp, vp]
     lib.spc5_csr_plan_info.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i64), ctypes.POINTER(i64)]
@@ -141,7 +143,8 @@ def load(build_if_missing: bool = False):
               lib.spc5_count_blocks, lib.spc5_csr_spmv, lib.spc5_copy, lib.spc5_fma_rate, lib.spc5_fma_rate_lanes,
               lib.spc5_spmv_noalloc, lib.spc5_launch_count, lib.spc5_device_peaks, lib.spc5_tune,
               lib.spc5_tune_cache_clear, lib.spc5_convert_rows, lib.spc5_pool_trim, lib.spc5_csr_plan_create,
-              lib.spc5_csr_spmv_plan, lib.spc5_csr_plan_info, lib.spc5_csr_plan_destroy, lib.spc5_cg, lib.spc5_spmm, lib.spc5_features,
+              lib.spc5_csr_spmv_plan, lib.spc5_csr_plan_info, lib.spc5_csr_plan_destroy, lib.spc5_sm_stream_create,
+              lib.spc5_sm_stream_destroy, lib.spc5_cg, lib.spc5_spmm, lib.spc5_features,
               lib.spc5_time_formats, lib.spc5_mlp_train, lib.spc5_mlp_grad, lib.spc5_mlp_infer, lib.spc5_poly_fit,
               lib.spc5_select, lib.spc5_batch_create, lib.spc5_batch_spmv, lib.spc5_batch_spmv_direct,
               lib.spc5_batch_destroy, lib.spc5_partition):
@@ -370,6 +373,27 @@ def pool_trim():
     _check(load().spc5_pool_trim(), "spc5_pool_trim")
 
 
+class SmStream:
+    """A torch stream whose kernels run on about `sms` SMs only (spc5_sm_stream_create)."""
+
+    def __init__(self, sms: int, device=None):
+        st, got = ctypes.c_void_p(), ctypes.c_int()
+        _check(load().spc5_sm_stream_create(sms, ctypes.byref(st), ctypes.byref(got)), "spc5_sm_stream_create")
+        self._raw, self.sms = st.value, got.value
+        self.stream = torch.cuda.ExternalStream(self._raw, device=device)
+
+    def destroy(self):
+        if self._raw is not None:
+            load().spc5_sm_stream_destroy(self._raw)
+            self._raw = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
 def tune_cache_clear():
     _check(load().spc5_tune_cache_clear(), "spc5_tune_cache_clear")
 
@@ -461,6 +485,8 @@ def time_formats(d: "DeviceCSR", reps: int = 5, stream=None) -> np.ndarray:
     xdt = _VECTOR_DTYPE[vt]
     x = torch.rand(d.m, dtype=xdt, device=d.values.device)
     y = torch.empty(d.n, dtype=xdt, device=d.values.device)
+    if stream is not None:
+        stream.wait_stream(torch.cuda.current_stream())  # x is written on the current stream
     out = np.zeros(NFORMATS, dtype=np.float32)
     _check(load().spc5_time_formats(d.n, d.m, d.nnz, _ptr(d.rowptr), _ptr(d.colidx), _ptr(d.values), vt, _ptr(x),
                                     _ptr(y), reps, out.ctypes.data, _stream_ptr(stream)), "spc5_time_formats")

@@ -85,6 +85,10 @@ def test_host_side_argument_checks(lib):
     assert lib.spc5_csr_plan_create(4, 0, 1, 7, 0, 0, 0, None, ctypes.byref(plan)) == spc5.EUNSUPPORTED
     assert lib.spc5_csr_spmv_plan(None, None, None, None, None, None) == spc5.EINVAL
     assert lib.spc5_csr_plan_destroy(None) == spc5.OK
+    st = ctypes.c_void_p()
+    assert lib.spc5_sm_stream_create(0, ctypes.byref(st), None) == spc5.EINVAL
+    assert lib.spc5_sm_stream_create(8, None, None) == spc5.EINVAL
+    assert lib.spc5_sm_stream_destroy(None) == spc5.OK
     assert lib.spc5_convert_rows(4, 4, 0, 1, None, None, 0, 2, 8, 1, 4, None, None, ctypes.byref(h)) == spc5.EINVAL
     assert lib.spc5_autotune(None, None, None, 3, None, None, None) == spc5.EINVAL
 
