@@ -569,6 +569,27 @@ spc5_status spc5_mlp_infer(const float* params_d, const float* X_d, int N, float
  */
 spc5_status spc5_poly_fit(const double* avg, const double* perf, int N, int degree, double* coef_out);
 
+/*
+ * spc5_poly2_fit - the paper's parallel predictor (section "Performance
+ * prediction and optimal kernel selection", parallel part: a regression of
+ * each kernel's performance on two parameters, the number of threads and
+ * Avg(r,c)). Here the second parameter is the fraction s of the SMs a product
+ * may use (see spc5_sm_stream_create). For each format f, least-squares
+ * coefficients of perf[:, f] ~ sum of c_q Avg^a s^b over a + b <= degree,
+ * the terms ordered by total degree t = a + b, then by b (so q = 0 is 1,
+ * q = 1 Avg, q = 2 s, q = 3 Avg^2, ...). avg, perf: N x 12 host arrays;
+ * sm_frac: N host values; coef_out: 12 x (degree+1)(degree+2)/2. 0 <=
+ * degree <= 4, N >= the number of terms. Host function.
+ */
+spc5_status spc5_poly2_fit(const double* avg, const double* sm_frac, const double* perf, int N, int degree,
+                           double* coef_out);
+
+/* spc5_poly2_select - the format with the highest spc5_poly2_fit estimate at
+ * the matrix's features (spc5_features, host, 16 values) and SM fraction
+ * sm_frac; est_out (nullable, 12) receives the estimates. Host function. */
+spc5_status spc5_poly2_select(const double* coef, int degree, const double* features, double sm_frac, int* r_out,
+                              int* c_out, double* est_out);
+
 typedef enum { SPC5_SELECT_EXHAUSTIVE = 0, SPC5_SELECT_POLY = 1, SPC5_SELECT_MLP = 2 } spc5_select_method;
 
 typedef struct {

@@ -11,6 +11,10 @@ TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
 * The paper-style predictor (section "Performance polynomial interpolation"):
   per format, a least-squares polynomial of the performance in Avg(r,c);
   the format with the highest estimate is chosen.
+* The paper's parallel predictor (same section, parallel part): per format a
+  least-squares polynomial of the performance in two variables, Avg(r,c) and
+  the amount of parallel hardware (the fraction of the SMs here), over the
+  monomials Avg^a s^b with a + b <= degree; the highest estimate wins.
 * A multilayer perceptron 16 -> 64 -> 64 -> 12 with ReLU, in float64, that
   maps standardised features to a score per format (centred log time); its
   forward and backward passes written out layer by layer.
@@ -56,6 +60,33 @@ def poly_eval(coef: np.ndarray, avg) -> np.ndarray:
 def poly_select(coefs: list[np.ndarray], feats: np.ndarray) -> int:
     """Index of the format with the highest estimated performance."""
     est = [poly_eval(coefs[q], feats[q]) for q in range(NFMT)]
+    return int(np.argmax(est))
+
+
+# ------------------------------------------------------------- 2D regression
+
+def poly2_exponents(degree: int):
+    """(a, b) of the monomials Avg^a s^b, a + b <= degree: by total degree, then by b."""
+    return [(t - b, b) for t in range(degree + 1) for b in range(t + 1)]
+
+
+def poly2_fit(avg: np.ndarray, sfrac: np.ndarray, perf: np.ndarray, degree: int) -> np.ndarray:
+    """Least-squares coefficients of perf ~ sum_q c_q avg^a_q s^b_q for one format."""
+    avg = np.asarray(avg, dtype=np.float64)
+    sfrac = np.asarray(sfrac, dtype=np.float64)
+    V = np.stack([avg**a * sfrac**b for a, b in poly2_exponents(degree)], axis=1)
+    coef, *_ = np.linalg.lstsq(V, np.asarray(perf, dtype=np.float64), rcond=None)
+    return coef
+
+
+def poly2_eval(coef: np.ndarray, degree: int, avg, sfrac) -> np.ndarray:
+    avg = np.asarray(avg, dtype=np.float64)
+    return sum(c * avg**a * np.asarray(sfrac, dtype=np.float64)**b for c, (a, b) in zip(coef, poly2_exponents(degree)))
+
+
+def poly2_select(coefs, degree: int, feats: np.ndarray, sfrac: float) -> int:
+    """Index of the format with the highest 2D-regression estimate."""
+    est = [poly2_eval(coefs[q], degree, feats[q], sfrac) for q in range(NFMT)]
     return int(np.argmax(est))
 
 

@@ -213,6 +213,26 @@ spc5_status spc5_export(spc5_handle h, spc5_arrays* v) {
   return SPC5_OK;
 }
 
+spc5_status spc5_poly2_fit(const double* avg, const double* sm_frac, const double* perf, int N, int degree,
+                           double* coef_out) {
+  if (!avg || !sm_frac || !perf || !coef_out) return fail(SPC5_EINVAL, "poly2_fit: NULL array");
+  return poly2_fit_impl(avg, sm_frac, perf, N, degree, coef_out);
+}
+
+spc5_status spc5_poly2_select(const double* coef, int degree, const double* features, double sm_frac, int* r_out,
+                              int* c_out, double* est_out) {
+  if (!coef || !features || !r_out || !c_out) return fail(SPC5_EINVAL, "poly2_select: NULL argument");
+  if (degree < 0 || degree > 4) return fail(SPC5_EINVAL, "poly2_select: need 0 <= degree <= 4");
+  double est[SPC5_NFORMATS];
+  const int q = poly2_select_impl(coef, degree, features, sm_frac, est);
+  const int rs[4] = {1, 2, 4, 8}, cs[3] = {4, 8, 16};
+  *r_out = rs[q / 3];
+  *c_out = cs[q % 3];
+  if (est_out)
+    for (int f = 0; f < SPC5_NFORMATS; ++f) est_out[f] = est[f];
+  return SPC5_OK;
+}
+
 spc5_status spc5_pool_trim(void) {
   cudaError_t e = trim_pools();
   if (e != cudaSuccess) return cuda_fail(e, "pool_trim");

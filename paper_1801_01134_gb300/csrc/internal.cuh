@@ -155,6 +155,10 @@ spc5_status mlp_grad_impl(const float* P, const float* X, const float* Y, const 
 spc5_status mlp_infer_impl(const float* P, const float* X, int N, float* out, cudaStream_t s);
 spc5_status poly_fit_impl(const double* avg, const double* perf, int N, int degree, double* coef);
 int poly_select_impl(const double* coef, int degree, const double* feat, double* est);
+int poly2_terms(int degree);
+spc5_status poly2_fit_impl(const double* avg, const double* sfrac, const double* perf, int N, int degree,
+                           double* coef);
+int poly2_select_impl(const double* coef, int degree, const double* feat, double sfrac, double* est);
 int mlp_param_count();
 
 // conjugate gradients (cg.cu)

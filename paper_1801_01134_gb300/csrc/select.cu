@@ -336,6 +336,54 @@ int poly_select_impl(const double* coef, int degree, const double* feat, double*
   return best;
 }
 
+// The paper's parallel predictor: per format, a least-squares polynomial of
+// the performance in two variables, Avg(r,c) and the amount of parallel
+// hardware (threads there, the fraction of the SMs here): every monomial
+// Avg^a s^b with a + b <= degree, ordered by total degree t = a + b, then by b.
+int poly2_terms(int degree) { return (degree + 1) * (degree + 2) / 2; }
+
+static void poly2_row(double avg, double s, int degree, double* row) {
+  int q = 0;
+  for (int t = 0; t <= degree; ++t)
+    for (int b = 0; b <= t; ++b) {
+      const int a = t - b;
+      double v = 1.0;
+      for (int k = 0; k < a; ++k) v *= avg;
+      for (int k = 0; k < b; ++k) v *= s;
+      row[q++] = v;
+    }
+}
+
+spc5_status poly2_fit_impl(const double* avg, const double* sfrac, const double* perf, int N, int degree,
+                           double* coef) {
+  if (degree < 0 || degree > 4) return fail(SPC5_EINVAL, "poly2_fit: need 0 <= degree <= 4");
+  const int k = poly2_terms(degree);
+  if (N < k) return fail(SPC5_EINVAL, "poly2_fit: fewer samples than terms");
+  for (int f = 0; f < kNO; ++f) {
+    std::vector<double> V((size_t)N * k), y((size_t)N);
+    for (int i = 0; i < N; ++i) {
+      poly2_row(avg[(size_t)i * kNO + f], sfrac[i], degree, &V[(size_t)i * k]);
+      y[(size_t)i] = perf[(size_t)i * kNO + f];
+    }
+    if (!lstsq(V, y, N, k, coef + (size_t)f * k)) return fail(SPC5_EINVAL, "poly2_fit: rank-deficient data");
+  }
+  return SPC5_OK;
+}
+
+int poly2_select_impl(const double* coef, int degree, const double* feat, double sfrac, double* est) {
+  const int k = poly2_terms(degree);
+  std::vector<double> row((size_t)k);
+  int best = 0;
+  for (int f = 0; f < kNO; ++f) {
+    poly2_row(feat[f], sfrac, degree, row.data());
+    double v = 0.0;
+    for (int j = 0; j < k; ++j) v += coef[(size_t)f * k + j] * row[(size_t)j];
+    est[f] = v;
+    if (v > est[best]) best = f;
+  }
+  return best;
+}
+
 int mlp_param_count() { return kNP; }
 
 }  // namespace spc5

@@ -14,6 +14,15 @@ the polynomial fit run in libspc5; this module drives them and computes the
 input standardisation and the regret statistics.
 
     python -m paper_1801_01134_gb300.selector --train 2000 --test 300 --out <file.npz>
+
+The SM-count axis (the paper's parallel predictor, a 2D regression over the
+thread count and Avg(r,c)): the timings are recorded again on SM-limited
+streams (spc5_sm_stream_create) and the 2D regression (spc5_poly2_fit) is
+fitted over (Avg(r,c), SM fraction); its held-out regret is reported per SM
+count beside the SM-unaware predictors:
+
+    python -m paper_1801_01134_gb300.selector --sm-counts 16,40,80,152 --train 400 --test 120 \
+        --mlp-model <selector.npz> --out <sm.npz>
 """
 from __future__ import annotations
 
@@ -62,6 +71,94 @@ def record(indices, seed: int = 3, dtype=torch.float64, reps: int = 5, n_max: fl
             log(f"recorded {len(F)} matrices in {time.time() - t0:.0f} s")
     th.join()
     return np.array(F), np.array(T, dtype=np.float64), np.array(NNZ, dtype=np.int64), fam
+
+
+def record_sm(indices, sm_counts, seed: int = 3, dtype=torch.float64, reps: int = 5, n_max: float = 1e6, log=None):
+    """Features, nnz, and per-SM-count per-shape SpMV milliseconds (N x S x 12):
+    the timing recorder run on SM-limited streams."""
+    streams = [spc5.SmStream(k) for k in sm_counts]
+    got = [st.sms for st in streams]
+    F, T, NNZ = [], [], []
+    t0 = time.time()
+    for i in indices:
+        A = inputs.corpus_matrix(i, seed=seed, n_max=n_max)
+        d = spc5.upload_csr(A, dtype, "cuda")
+        F.append(spc5.features(d))
+        T.append([spc5.time_formats(d, reps=reps, stream=st.stream) for st in streams])
+        NNZ.append(A.nnz)
+        del d
+        if log and len(F) % 100 == 0:
+            log(f"recorded {len(F)} matrices x {len(streams)} SM counts in {time.time() - t0:.0f} s")
+    for st in streams:
+        st.destroy()
+    return np.array(F), np.array(T, dtype=np.float64), np.array(NNZ, dtype=np.int64), got
+
+
+def fit_poly2(F, T, nnz, sfrac, degree):
+    """The paper's 2D regression over (Avg(r,c), SM fraction) on GFLOP/s, all SM counts pooled.
+    T: N x S x 12, sfrac: S values."""
+    N, S, _ = T.shape
+    avg = np.repeat(F[:, None, :12], S, axis=1).reshape(N * S, 12)
+    sf = np.tile(np.asarray(sfrac, dtype=np.float64), N)
+    gflops = (2.0 * nnz[:, None, None] / (T * 1e-3) / 1e9).reshape(N * S, 12)
+    return spc5.poly2_fit(avg, sf, gflops, degree)
+
+
+def poly2_choices(coef, degree, F, sfrac_one: float) -> np.ndarray:
+    return np.array([SHAPES.index(spc5.poly2_select(coef, degree, f, sfrac_one)[:2]) for f in F])
+
+
+def sm_axis_main(args, log):
+    """Record the SM-axis corpus, fit the 2D regression, report held-out regret per SM count."""
+    sm_req = [int(v) for v in args.sm_counts.split(",")]
+    Ftr, Ttr, Ntr, sms = record_sm(range(args.train), sm_req, args.seed, n_max=args.n_max, reps=args.reps, log=log)
+    Fte, Tte, Nte, _ = record_sm(range(args.train, args.train + args.test), sm_req, args.seed, n_max=args.n_max,
+                                 reps=args.reps, log=log)
+    full = max(sms)
+    sfrac = [k / full for k in sms]
+    # degree of the 2D regression by cross-validation over the training matrices
+    best = None
+    idx = np.arange(Ftr.shape[0])
+    for deg in (1, 2, 3):
+        regs = []
+        for k in range(5):
+            va = idx % 5 == k
+            coef = fit_poly2(Ftr[~va], Ttr[~va], Ntr[~va], sfrac, deg)
+            for j, sf in enumerate(sfrac):
+                regs.append(regret(Ttr[va, j], poly2_choices(coef, deg, Ftr[va], sf)))
+        m = float(np.concatenate(regs).mean())
+        if best is None or m < best[0]:
+            best = (m, deg)
+    deg2 = best[1]
+    coef2 = fit_poly2(Ftr, Ttr, Ntr, sfrac, deg2)
+    # SM-unaware yardsticks: the 1D polynomial fitted on the whole-GPU timings,
+    # the committed whole-GPU MLP, the best single shape on the whole GPU
+    jf = sms.index(full)
+    deg1 = choose_poly_degree(Ftr, Ttr[:, jf], Ntr)
+    coef1 = fit_poly(Ftr, Ttr[:, jf], Ntr, deg1)
+    fixed = int(np.argmin(np.log(Ttr[:, jf]).mean(axis=0)))
+    mlp = None
+    if args.mlp_model:
+        z = np.load(args.mlp_model)
+        mlp = (torch.from_numpy(z["mlp_params"]).cuda(), z["feat_mean"], z["feat_scale"])
+    per = {}
+    for j, k in enumerate(sms):
+        row = {"sm_fraction": round(sfrac[j], 4),
+               "poly2": summary(regret(Tte[:, j], poly2_choices(coef2, deg2, Fte, sfrac[j]))),
+               "poly_whole_gpu": summary(regret(Tte[:, j], poly_choices(coef1, Fte))),
+               "fixed_whole_gpu": summary(regret(Tte[:, j], np.full(Tte.shape[0], fixed)))}
+        if mlp is not None:
+            row["mlp_whole_gpu"] = summary(regret(Tte[:, j], mlp_choices(mlp[0], Fte, mlp[1], mlp[2])))
+        # how often the best shape on k SMs differs from the best on the whole GPU
+        row["best_differs_from_whole_gpu"] = float((Tte[:, j].argmin(axis=1) != Tte[:, jf].argmin(axis=1)).mean())
+        per[str(k)] = row
+    res = {"train": args.train, "test": args.test, "sm_counts": sms, "poly2_degree": deg2, "poly_degree": deg1,
+           "fixed_shape": f"{SHAPES[fixed][0]}x{SHAPES[fixed][1]}", "regret_by_sm_count": per}
+    log(json.dumps(res))
+    if args.out:
+        np.savez(args.out, Ftr=Ftr.astype(np.float32), Ttr=Ttr.astype(np.float32), Ntr=Ntr,
+                 Fte=Fte.astype(np.float32), Tte=Tte.astype(np.float32), Nte=Nte, sm_counts=np.array(sms),
+                 poly2_coef=coef2, poly2_degree=deg2, result=json.dumps(res))
 
 
 def mlp_inputs(F: np.ndarray, mean=None, scale=None):
@@ -151,9 +248,13 @@ def main():
     ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--epochs", type=int, default=400)
     ap.add_argument("--out", default=None, help="npz with the corpus table, the models and the evaluation")
+    ap.add_argument("--sm-counts", default=None, help="SM-count axis: comma list of SM counts (2D regression)")
+    ap.add_argument("--mlp-model", default=None, help="SM-count axis: the whole-GPU model to evaluate beside it")
     args = ap.parse_args()
     spc5.load()
     log = lambda m: print(m, flush=True)  # noqa: E731
+    if args.sm_counts:
+        return sm_axis_main(args, log)
     t0 = time.time()
     Ftr, Ttr, Ntr, famtr = record(range(args.train), args.seed, n_max=args.n_max, reps=args.reps, log=log)
     Fte, Tte, Nte, famte = record(range(args.train, args.train + args.test), args.seed, n_max=args.n_max,

@@ -112,6 +112,8 @@ def load(build_if_missing: bool = False):
     lib.spc5_spmv_noalloc.argtypes = [vp, vp, vp, vp]
     lib.spc5_launch_count.argtypes = [vp, ctypes.POINTER(i32)]
     lib.spc5_pool_trim.argtypes = []
+    lib.spc5_poly2_fit.argtypes = [vp, vp, vp, i32, i32, vp]
+    lib.spc5_poly2_select.argtypes = [vp, i32, vp, ctypes.c_double, ctypes.POINTER(i32), ctypes.POINTER(i32), vp]
     lib.spc5_sm_stream_create.argtypes = [i32, ctypes.POINTER(vp), ctypes.POINTER(i32)]
     lib.spc5_sm_stream_destroy.argtypes = [vp]
     lib.spc5_csr_plan_create.argtypes = [i64, i64, vp, i32, i32, i64, i64, vp, ctypes.POINTER(vp)]
@@ -144,7 +146,7 @@ def load(build_if_missing: bool = False):
               lib.spc5_spmv_noalloc, lib.spc5_launch_count, lib.spc5_device_peaks, lib.spc5_tune,
               lib.spc5_tune_cache_clear, lib.spc5_convert_rows, lib.spc5_pool_trim, lib.spc5_csr_plan_create,
               lib.spc5_csr_spmv_plan, lib.spc5_csr_plan_info, lib.spc5_csr_plan_destroy, lib.spc5_sm_stream_create,
-              lib.spc5_sm_stream_destroy, lib.spc5_cg, lib.spc5_spmm, lib.spc5_features,
+              lib.spc5_sm_stream_destroy, lib.spc5_poly2_fit, lib.spc5_poly2_select, lib.spc5_cg, lib.spc5_spmm, lib.spc5_features,
               lib.spc5_time_formats, lib.spc5_mlp_train, lib.spc5_mlp_grad, lib.spc5_mlp_infer, lib.spc5_poly_fit,
               lib.spc5_select, lib.spc5_batch_create, lib.spc5_batch_spmv, lib.spc5_batch_spmv_direct,
               lib.spc5_batch_destroy, lib.spc5_partition):
@@ -537,6 +539,28 @@ def poly_fit(avg: np.ndarray, perf: np.ndarray, degree: int) -> np.ndarray:
     _check(load().spc5_poly_fit(avg.ctypes.data, perf.ctypes.data, avg.shape[0], degree, coef.ctypes.data),
            "spc5_poly_fit")
     return coef
+
+
+def poly2_fit(avg: np.ndarray, sm_frac: np.ndarray, perf: np.ndarray, degree: int) -> np.ndarray:
+    """The paper's 2D regression per format over (Avg(r,c), SM fraction); (12, nterms) coefficients."""
+    avg = np.ascontiguousarray(avg, dtype=np.float64)
+    sf = np.ascontiguousarray(sm_frac, dtype=np.float64)
+    perf = np.ascontiguousarray(perf, dtype=np.float64)
+    coef = np.zeros((NFORMATS, (degree + 1) * (degree + 2) // 2), dtype=np.float64)
+    _check(load().spc5_poly2_fit(avg.ctypes.data, sf.ctypes.data, perf.ctypes.data, avg.shape[0], degree,
+                                 coef.ctypes.data), "spc5_poly2_fit")
+    return coef
+
+
+def poly2_select(coef: np.ndarray, degree: int, features: np.ndarray, sm_frac: float):
+    """(r, c, estimates) of the 2D regression at one matrix and SM fraction."""
+    coef = np.ascontiguousarray(coef, dtype=np.float64)
+    f = np.ascontiguousarray(features, dtype=np.float64)
+    est = np.zeros(NFORMATS, dtype=np.float64)
+    r, c = ctypes.c_int(), ctypes.c_int()
+    _check(load().spc5_poly2_select(coef.ctypes.data, degree, f.ctypes.data, sm_frac, ctypes.byref(r),
+                                    ctypes.byref(c), est.ctypes.data), "spc5_poly2_select")
+    return r.value, c.value, est
 
 
 def select(d: "DeviceCSR", method: int, poly_coef: np.ndarray | None = None, mlp_params: torch.Tensor | None = None,

@@ -142,3 +142,30 @@ def test_binding_checks_vectors_before_calling_the_library():
     M._h = None
     with pytest.raises(ValueError):  # a destroyed matrix
         M.spmv_acc(torch.zeros(7, dtype=torch.float64), torch.zeros(10, dtype=torch.float64))
+
+
+def test_library_poly2_fit_and_select_match_the_oracle():
+    # the library's 2D regression (host code) against the oracle's, and its choice
+    from oracle import select as osel
+    from paper_1801_01134_gb300 import spc5
+
+    rng = np.random.default_rng(7)
+    N, deg = 80, 2
+    avg = rng.uniform(1.0, 24.0, (N, 12))
+    s = rng.choice([16 / 152, 40 / 152, 80 / 152, 1.0], N)
+    perf = rng.uniform(50.0, 900.0, (N, 12))
+    got = spc5.poly2_fit(avg, s, perf, deg)
+    for q in range(12):
+        want = osel.poly2_fit(avg[:, q], s, perf[:, q], deg)
+        assert np.allclose(got[q], want, rtol=1e-9, atol=1e-9)
+    for i in range(10):
+        f = np.concatenate([avg[i], np.zeros(4)])
+        r, c, est = spc5.poly2_select(got, deg, f, float(s[i]))
+        q = osel.poly2_select(list(got), deg, f, float(s[i]))
+        assert (r, c) == oracle_shapes()[q]
+
+
+def oracle_shapes():
+    import oracle
+
+    return oracle.SHAPES

@@ -112,3 +112,29 @@ def test_adam_minimises_a_quadratic_and_regret_definition():
     assert np.allclose(osel.regret(times, np.array([0, 0])), [0.0, 1.0])
     c = osel.centred_log_times(times)
     assert np.allclose(c.sum(axis=1), 0.0)
+
+
+def test_poly2_fit_recovers_exact_2d_polynomials():
+    # data drawn from a known polynomial in (Avg, s): the fit returns it
+    rng = np.random.default_rng(5)
+    for deg in (1, 2, 3):
+        terms = osel.poly2_exponents(deg)
+        assert len(terms) == (deg + 1) * (deg + 2) // 2 and terms[:3] == [(0, 0), (1, 0), (0, 1)][:len(terms)]
+        c = rng.standard_normal(len(terms))
+        avg = rng.uniform(1.0, 20.0, 60)
+        s = rng.choice([8 / 152, 40 / 152, 80 / 152, 1.0], 60)
+        y = sum(ci * avg**a * s**b for ci, (a, b) in zip(c, terms))
+        got = osel.poly2_fit(avg, s, y, deg)
+        assert np.allclose(got, c, rtol=1e-7, atol=1e-7)
+
+
+def test_poly2_select_takes_the_highest_estimate_at_the_sm_fraction():
+    # format 3: 10 + 20 s (gains with SMs); format 5: 20 (flat); others 1.
+    # At s = 0.25 the flat format wins (15 < 20), at s = 1 format 3 (30 > 20).
+    deg = 1
+    coefs = [np.array([1.0, 0.0, 0.0]) for _ in range(osel.NFMT)]
+    coefs[3] = np.array([10.0, 0.0, 20.0])
+    coefs[5] = np.array([20.0, 0.0, 0.0])
+    f = np.full(osel.NFEAT, 2.0)
+    assert osel.poly2_select(coefs, deg, f, 0.25) == 5
+    assert osel.poly2_select(coefs, deg, f, 1.0) == 3
