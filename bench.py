@@ -441,6 +441,18 @@ def run_selector_section(prep, dev):
                           "mlp_regret": round(best / sweep[f"{rm}x{cm}"] - 1.0, 4),
                           "poly": f"{rp}x{cp}", "poly_regret": round(best / sweep[f"{rp}x{cp}"] - 1.0, 4)}
     out["bench_matrices"] = per
+    smp = os.path.join(ROOT, "paper_1801_01134_gb300", "models", "selector_sm_gb300.npz")
+    if os.path.exists(smp):
+        zs = np.load(smp)
+        rs = json.loads(str(zs["result"]))
+        out["sm_axis"] = {"model": "paper_1801_01134_gb300/models/selector_sm_gb300.npz",
+                          "what": "held-out mean regret per SM count (green-context partitions): the paper's 2D "
+                                  "regression over (Avg, SM fraction) beside the SM-unaware whole-GPU predictors",
+                          "poly2_degree": rs["poly2_degree"],
+                          "mean_regret": {k: {m: round(v[m]["mean"], 4) for m in v if isinstance(v[m], dict)}
+                                          for k, v in rs["regret_by_sm_count"].items()},
+                          "best_differs_from_whole_gpu": {k: v["best_differs_from_whole_gpu"]
+                                                          for k, v in rs["regret_by_sm_count"].items()}}
     return out
 
 

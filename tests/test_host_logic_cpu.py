@@ -169,3 +169,27 @@ def oracle_shapes():
     import oracle
 
     return oracle.SHAPES
+
+
+def test_committed_sm_axis_model_refits_and_its_axis_limits_the_gpu():
+    # the committed SM-axis corpus: the stored 2D-regression coefficients come
+    # back from the stored timings through the library's fit, and fewer SMs
+    # make the larger products slower
+    import json
+    import os
+
+    from paper_1801_01134_gb300 import selector, spc5
+
+    path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_1801_01134_gb300",
+                        "models", "selector_sm_gb300.npz")
+    z = np.load(path)
+    sms = [int(v) for v in z["sm_counts"]]
+    sf = [k / max(sms) for k in sms]
+    deg = int(z["poly2_degree"])
+    coef = selector.fit_poly2(z["Ftr"].astype(np.float64), z["Ttr"].astype(np.float64), z["Ntr"], sf, deg)
+    assert np.allclose(coef, z["poly2_coef"], rtol=1e-6, atol=1e-6)
+    T = z["Ttr"].astype(np.float64)
+    big = z["Ntr"] > np.quantile(z["Ntr"], 0.75)
+    assert np.median(T[big, 0].min(axis=1) / T[big, -1].min(axis=1)) > 2.0  # 16 SMs vs all
+    res = json.loads(str(z["result"]))
+    assert set(res["regret_by_sm_count"]) == {str(k) for k in sms}
