@@ -189,6 +189,7 @@ class Matrix:
     def __init__(self, handle: int, n: int, m: int, nnz: int, r: int, c: int, vt: int):
         self._h = handle
         self.n, self.m, self.nnz, self.r, self.c, self.vt = n, m, nnz, r, c, vt
+        self.variant = 0
 
     @property
     def vector_dtype(self) -> torch.dtype:
@@ -311,7 +312,9 @@ def convert(rowptr: torch.Tensor, colidx: torch.Tensor, values: torch.Tensor, n:
     h = ctypes.c_void_p()
     _check(load().spc5_convert(n, m, nnz, _ptr(rowptr), _ptr(colidx), _ptr(values), vt, r, c, ctypes.byref(opts),
                                _stream_ptr(stream), ctypes.byref(h)), "spc5_convert")
-    return Matrix(h.value, n, m, nnz, r, c, vt)
+    M = Matrix(h.value, n, m, nnz, r, c, vt)
+    M.variant = variant
+    return M
 
 
 def convert_rows(rowptr: torch.Tensor, colidx: torch.Tensor, values: torch.Tensor, n: int, m: int, r: int, c: int,

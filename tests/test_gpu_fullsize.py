@@ -138,3 +138,59 @@ def test_low_precision_convert_and_spmv(full, kind):
         bad = err > bound + 1e-45
         assert not bad.any(), f"{kind} beta({r},{c}) variant {v}: {bad.sum()} rows over gamma_(L+1) (|A||x|)_i"
         M.destroy()
+
+
+def test_spmm_full_size_stencil_k32(cuda_device):
+    # the bench's SpMM workload: 27-point stencil 128^3, float32, k = 32, the
+    # block-row tiles and the lane-per-row tiles; sampled columns against the oracle
+    A = _make("stencil27_128^3")
+    A = inputs.CSR(A.n, A.m, A.rowptr, A.colidx, oracle.round_f32(A.values))
+    k = 32
+    X = oracle.round_f32(inputs.vec_uniform(A.m * k, seed=7).reshape(A.m, k))
+    d = spc5.upload_csr(A, torch.float32, "cuda")
+    Xd = torch.from_numpy(X).float().cuda()
+    L = np.diff(A.rowptr).astype(np.float64)
+    cols = (0, 13, 31)
+    refs = {j: oracle.csr_spmv_dot2(A, np.ascontiguousarray(X[:, j])) for j in cols}
+    for r, c, kt in ((2, 4, 32), (4, 8, 16), (8, 4, -32)):
+        M = spc5.convert(d.rowptr, d.colidx, d.values, A.n, A.m, r, c)
+        Y = M.spmm(Xd, ktile=kt).double().cpu().numpy()
+        for j in cols:
+            y_ref, absy = refs[j]
+            assert np.all(np.abs(Y[:, j] - y_ref) <= (L + 1) * U32 / (1 - (L + 1) * U32) * absy + 1e-45), (r, c, kt, j)
+        M.destroy()
+
+
+def test_batch_full_size_256_matrices(cuda_device):
+    # the bench's batched workload: 256 uneven float32 matrices in the shape and
+    # variant the tuner picks; bit for bit against one product per matrix
+    mats, keep, xs, ys, As = [], [], [], [], []
+    for j in range(256):
+        A = inputs.batch_matrix(j, seed=2)
+        A = inputs.CSR(A.n, A.m, A.rowptr, A.colidx, oracle.round_f32(A.values))
+        As.append(A)
+        d = spc5.upload_csr(A, torch.float32, "cuda")
+        t = spc5.tune(d, reps=2)
+        mats.append(spc5.convert(d.rowptr, d.colidx, d.values, A.n, A.m, t["r"], t["c"], variant=t["variant"]))
+        keep.append(d)
+        xs.append(torch.rand(A.m, dtype=torch.float32, device="cuda"))
+        ys.append(torch.full((A.n,), float("nan"), dtype=torch.float32, device="cuda"))
+    B = spc5.Batch(mats, xs, ys)
+    B.run()
+    torch.cuda.synchronize()
+    for j, M in enumerate(mats):
+        single = M.spmv(xs[j])
+        if M.variant in (22, 23) or 24 <= M.variant <= 29:
+            # these variants sum in another order than the batch's one-lane
+            # decode: both within the float32 bound of the oracle
+            A = As[j]
+            y_ref, absy = oracle.csr_spmv_dot2(A, xs[j].double().cpu().numpy())
+            L = np.diff(A.rowptr).astype(np.float64)
+            bound = (L + 1) * U32 / (1 - (L + 1) * U32) * absy + 1e-45
+            assert np.all(np.abs(ys[j].double().cpu().numpy() - y_ref) <= bound), j
+            assert np.all(np.abs(single.double().cpu().numpy() - y_ref) <= bound), j
+        else:
+            assert torch.equal(ys[j], single), j
+    B.destroy()
+    for M in mats:
+        M.destroy()
