@@ -562,6 +562,31 @@ spc5_status spc5_mlp_grad(const float* params_d, const float* X_d, const float* 
 spc5_status spc5_mlp_infer(const float* params_d, const float* X_d, int N, float* out_d, spc5_stream_t stream);
 
 /*
+ * Richer selection inputs (the paper's conclusion asks for statistics beyond
+ * Avg(r,c) and hardware properties; its interpolation section names the
+ * block distribution's effect on the x accesses as what Avg cannot tell).
+ * spc5_features_ext fills 20 host doubles: [0..15] as spc5_features, [16] the
+ * mean distance |col - row| of the entries from the diagonal divided by n,
+ * [17] log10(1 + that mean distance), [18] the fraction of rows with at most
+ * two entries, [19] sm_frac (the fraction of the SMs the products will use,
+ * in (0, 1]: the hardware input). Synchronises `stream`.
+ */
+spc5_status spc5_features_ext(int64_t n, int64_t m, int64_t nnz, const int64_t* rowptr_d, const int32_t* colidx_d,
+                              double sm_frac, double* features_out, spc5_stream_t stream);
+
+/* The MLP with nfeat = 16 or 20 inputs (W1 is 64 x nfeat, the rest as above):
+ * parameter count (-1 for another nfeat), training, gradient and inference as
+ * spc5_mlp_train / spc5_mlp_grad / spc5_mlp_infer. */
+int spc5_mlp_nparams_n(int nfeat);
+spc5_status spc5_mlp_train_n(float* params_d, const float* X_d, const float* Y_d, const float* M_d, int N, int nfeat,
+                             int epochs, int batch, float lr, uint64_t seed, float* loss_history,
+                             spc5_stream_t stream);
+spc5_status spc5_mlp_grad_n(const float* params_d, const float* X_d, const float* Y_d, const float* M_d, int B,
+                            int nfeat, float* loss_out, float* grad_d, spc5_stream_t stream);
+spc5_status spc5_mlp_infer_n(const float* params_d, const float* X_d, int N, int nfeat, float* out_d,
+                             spc5_stream_t stream);
+
+/*
  * spc5_poly_fit - the paper's per-kernel polynomial interpolation: for each
  * format f, least-squares coefficients c_0..c_d of perf[:, f] ~ sum_j c_j
  * avg[:, f]^j (Householder QR). avg, perf: N x 12 host arrays; coef_out:

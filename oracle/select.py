@@ -15,9 +15,13 @@ TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
   least-squares polynomial of the performance in two variables, Avg(r,c) and
   the amount of parallel hardware (the fraction of the SMs here), over the
   monomials Avg^a s^b with a + b <= degree; the highest estimate wins.
-* A multilayer perceptron 16 -> 64 -> 64 -> 12 with ReLU, in float64, that
-  maps standardised features to a score per format (centred log time); its
-  forward and backward passes written out layer by layer.
+* A multilayer perceptron 16 (or 20) -> 64 -> 64 -> 12 with ReLU, in float64,
+  that maps standardised features to a score per format (centred log time);
+  its forward and backward passes written out layer by layer.
+* Extended features (the conclusion's richer inputs): the 16 plus the mean
+  distance |col - row| of the entries from the diagonal (over n, and as
+  log10(1 + d)), the fraction of rows of at most two entries, and the
+  fraction of the SMs used.
 """
 from __future__ import annotations
 
@@ -41,6 +45,23 @@ def features(A) -> np.ndarray:
     f[13] = lens.std() if lens.size else 0.0
     f[14] = lens.max() if lens.size else 0.0
     f[15] = np.log10(max(A.n, 1))
+    return f
+
+
+def features_ext(A, sm_frac: float) -> np.ndarray:
+    """The 20 extended features: the 16, then mean |col - row| / n,
+    log10(1 + mean |col - row|), the fraction of rows with <= 2 entries, sm_frac."""
+    f = np.zeros(20)
+    f[:16] = features(A)
+    rowptr = np.asarray(A.rowptr, dtype=np.int64)
+    lens = np.diff(rowptr)
+    rows = np.repeat(np.arange(A.n, dtype=np.int64), lens)
+    dist = np.abs(np.asarray(A.colidx, dtype=np.int64) - rows)
+    mean = float(dist.sum()) / A.nnz if A.nnz else 0.0
+    f[16] = mean / A.n if A.n else 0.0
+    f[17] = np.log10(1.0 + mean)
+    f[18] = float((lens <= 2).sum()) / A.n if A.n else 0.0
+    f[19] = sm_frac
     return f
 
 
@@ -92,22 +113,24 @@ def poly2_select(coefs, degree: int, feats: np.ndarray, sfrac: float) -> int:
 
 # ----------------------------------------------------------------------- MLP
 
-def mlp_shapes():
-    return [(HIDDEN, NFEAT), (HIDDEN,), (HIDDEN, HIDDEN), (HIDDEN,), (NFMT, HIDDEN), (NFMT,)]
+def mlp_shapes(nfeat: int = NFEAT):
+    return [(HIDDEN, nfeat), (HIDDEN,), (HIDDEN, HIDDEN), (HIDDEN,), (NFMT, HIDDEN), (NFMT,)]
+
+
+def mlp_nparams(nfeat: int = NFEAT) -> int:
+    return sum(int(np.prod(s)) for s in mlp_shapes(nfeat))
 
 
 def mlp_unpack(theta: np.ndarray):
-    """Split the flat parameter vector: W1, b1, W2, b2, W3, b3 (row-major)."""
+    """Split the flat parameter vector: W1, b1, W2, b2, W3, b3 (row-major); the
+    input width follows from the vector's length."""
+    nfeat = next(k for k in (NFEAT, 20) if mlp_nparams(k) == len(theta))
     out, o = [], 0
-    for s in mlp_shapes():
+    for s in mlp_shapes(nfeat):
         k = int(np.prod(s))
         out.append(np.asarray(theta[o:o + k], dtype=np.float64).reshape(s))
         o += k
     return out
-
-
-def mlp_nparams() -> int:
-    return sum(int(np.prod(s)) for s in mlp_shapes())
 
 
 def mlp_forward(theta: np.ndarray, X: np.ndarray):

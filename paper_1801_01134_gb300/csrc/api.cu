@@ -466,6 +466,38 @@ spc5_status spc5_autotune(spc5_handle h, const void* x_d, void* y_d, int reps, i
 
 int spc5_mlp_nparams(void) { return mlp_param_count(); }
 
+int spc5_mlp_nparams_n(int nfeat) { return nfeat == 16 || nfeat == 20 ? mlp_param_count(nfeat) : -1; }
+
+spc5_status spc5_features_ext(int64_t n, int64_t m, int64_t nnz, const int64_t* rowptr_d, const int32_t* colidx_d,
+                              double sm_frac, double* features_out, spc5_stream_t stream) {
+  if (!features_out) return fail(SPC5_EINVAL, "features_ext: NULL output");
+  if (!(sm_frac > 0.0 && sm_frac <= 1.0)) return fail(SPC5_EINVAL, "features_ext: sm_frac must be in (0, 1]");
+  spc5_status st = check_csr_args(n, m, nnz, rowptr_d, colidx_d, (const void*)colidx_d);
+  if (st != SPC5_OK) return st;
+  return features_ext_impl(n, nnz, rowptr_d, colidx_d, sm_frac, features_out, (cudaStream_t)stream);
+}
+
+spc5_status spc5_mlp_train_n(float* params_d, const float* X_d, const float* Y_d, const float* M_d, int N, int nfeat,
+                             int epochs, int batch, float lr, uint64_t seed, float* loss_history,
+                             spc5_stream_t stream) {
+  if (!params_d || N < 1 || epochs < 0 || !X_d || !Y_d || !M_d || !(lr >= 0.f))
+    return fail(SPC5_EINVAL, "mlp_train: bad argument");
+  return mlp_train_impl(params_d, X_d, Y_d, M_d, N, epochs, batch, lr, seed, loss_history, (cudaStream_t)stream,
+                        nfeat);
+}
+
+spc5_status spc5_mlp_grad_n(const float* params_d, const float* X_d, const float* Y_d, const float* M_d, int B,
+                            int nfeat, float* loss_out, float* grad_d, spc5_stream_t stream) {
+  if (!params_d || !X_d || !Y_d || !M_d || !loss_out || !grad_d) return fail(SPC5_EINVAL, "mlp_grad: NULL argument");
+  return mlp_grad_impl(params_d, X_d, Y_d, M_d, B, loss_out, grad_d, (cudaStream_t)stream, nfeat);
+}
+
+spc5_status spc5_mlp_infer_n(const float* params_d, const float* X_d, int N, int nfeat, float* out_d,
+                             spc5_stream_t stream) {
+  if (!params_d || N < 0 || (N > 0 && (!X_d || !out_d))) return fail(SPC5_EINVAL, "mlp_infer: bad argument");
+  return mlp_infer_impl(params_d, X_d, N, out_d, (cudaStream_t)stream, nfeat);
+}
+
 spc5_status spc5_mlp_train(float* params_d, const float* X_d, const float* Y_d, const float* M_d, int N, int epochs,
                            int batch, float lr, uint64_t seed, float* loss_history, spc5_stream_t stream) {
   if (!params_d || N < 1 || epochs < 0 || !X_d || !Y_d || !M_d || !(lr >= 0.f))

@@ -149,17 +149,20 @@ int spmm_auto_tile(int k);
 spc5_status features_impl(int64_t n, int64_t nnz, const int64_t* rowptr, const int32_t* colidx, double* f,
                           cudaStream_t s);
 spc5_status mlp_train_impl(float* P, const float* X, const float* Y, const float* M, int N, int epochs, int batch,
-                           float lr, uint64_t seed, float* loss_hist, cudaStream_t s);
+                           float lr, uint64_t seed, float* loss_hist, cudaStream_t s, int nfeat = 16);
 spc5_status mlp_grad_impl(const float* P, const float* X, const float* Y, const float* M, int B, float* loss,
-                          float* grad, cudaStream_t s);
-spc5_status mlp_infer_impl(const float* P, const float* X, int N, float* out, cudaStream_t s);
+                          float* grad, cudaStream_t s, int nfeat = 16);
+spc5_status mlp_infer_impl(const float* P, const float* X, int N, float* out, cudaStream_t s, int nfeat = 16);
+// extended selection features (16 + x-access locality, short rows, SM fraction)
+spc5_status features_ext_impl(int64_t n, int64_t nnz, const int64_t* rowptr, const int32_t* colidx,
+                              double sm_frac, double* f, cudaStream_t s);
 spc5_status poly_fit_impl(const double* avg, const double* perf, int N, int degree, double* coef);
 int poly_select_impl(const double* coef, int degree, const double* feat, double* est);
 int poly2_terms(int degree);
 spc5_status poly2_fit_impl(const double* avg, const double* sfrac, const double* perf, int N, int degree,
                            double* coef);
 int poly2_select_impl(const double* coef, int degree, const double* feat, double sfrac, double* est);
-int mlp_param_count();
+int mlp_param_count(int nfeat = 16);
 
 // conjugate gradients (cg.cu)
 spc5_status cg_impl(const spc5_matrix* A, const spc5_matrix* L, const double* b, double* x, const spc5_cg_opts* o,

@@ -30,27 +30,35 @@
 namespace spc5 {
 namespace {
 
-constexpr int kNF = SPC5_NFEATURES;  // 16
 constexpr int kNO = SPC5_NFORMATS;   // 12
 constexpr int kH = 64;
-constexpr int kNP = kH * kNF + kH + kH * kH + kH + kNO * kH + kNO;  // 6028 parameters
 
 // ----------------------------------------------------------------- MLP
-// Parameter layout (float32, flat): W1[64][16], b1[64], W2[64][64], b2[64],
-// W3[12][64], b3[12].
-constexpr int oW1 = 0, ob1 = oW1 + kH * kNF, oW2 = ob1 + kH, ob2 = oW2 + kH * kH, oW3 = ob2 + kH,
-              ob3 = oW3 + kNO * kH;
+// Parameter layout (float32, flat) for NF inputs: W1[64][NF], b1[64],
+// W2[64][64], b2[64], W3[12][64], b3[12]. NF = 16 (the selection features)
+// or 20 (the extended features: plus x-access locality, short rows and the
+// SM fraction, see spc5_features_ext).
+template <int NF>
+struct Mlp {
+  static constexpr int oW1 = 0, ob1 = oW1 + kH * NF, oW2 = ob1 + kH, ob2 = oW2 + kH * kH, oW3 = ob2 + kH,
+                       ob3 = oW3 + kNO * kH, NP = ob3 + kNO;
+};
+constexpr int kNF = SPC5_NFEATURES;  // 16
+constexpr int kNP = Mlp<kNF>::NP;    // 6028 parameters
 constexpr int kMaxBatch = 32;  // keeps the step's activations in static shared memory
 constexpr int kStepThreads = 1024;
 
 // One training step on a minibatch of B <= 32 samples (rows idx[0..B) of X and
 // Y, with the 0/1 mask M saying which targets exist): forward, mean squared
 // error gradient, backward, Adam update of the parameters, all in one CTA.
+template <int NF>
 __global__ void __launch_bounds__(kStepThreads) k_mlp_step(float* __restrict__ P, float* __restrict__ mom,
                                                            float* __restrict__ vel, const float* __restrict__ X,
                                                            const float* __restrict__ Y, const float* __restrict__ Mk,
                                                            const int32_t* __restrict__ idx, int B, int t, float lr,
                                                            float* __restrict__ loss_out, float* __restrict__ grad_out) {
+  constexpr int oW1 = Mlp<NF>::oW1, ob1 = Mlp<NF>::ob1, oW2 = Mlp<NF>::oW2, ob2 = Mlp<NF>::ob2, oW3 = Mlp<NF>::oW3,
+                ob3 = Mlp<NF>::ob3, kNP = Mlp<NF>::NP, kNF = NF;
   __shared__ float xs[kMaxBatch][kNF];
   __shared__ float z1[kMaxBatch][kH], z2[kMaxBatch][kH];  // pre-activations, then reused for gradients
   __shared__ float h1[kMaxBatch][kH], h2[kMaxBatch][kH];
@@ -153,8 +161,11 @@ __global__ void __launch_bounds__(kStepThreads) k_mlp_step(float* __restrict__ P
 // scores of N samples: one thread per (sample, output); hidden layers of a
 // sample recomputed per output is wasteful but N is small; instead one thread
 // per sample with the activations in local arrays
+template <int NF>
 __global__ void __launch_bounds__(128) k_mlp_infer(const float* __restrict__ P, const float* __restrict__ X, int N,
                                                    float* __restrict__ out) {
+  constexpr int oW1 = Mlp<NF>::oW1, ob1 = Mlp<NF>::ob1, oW2 = Mlp<NF>::oW2, ob2 = Mlp<NF>::ob2, oW3 = Mlp<NF>::oW3,
+                ob3 = Mlp<NF>::ob3, kNF = NF;
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= N) return;
   float a1[kH], a2[kH];
@@ -237,9 +248,65 @@ spc5_status features_impl(int64_t n, int64_t nnz, const int64_t* rowptr, const i
   return SPC5_OK;
 }
 
+// Matrix statistics beyond Avg(r,c) for the extended features: the summed
+// distance |col - row| of the entries from the diagonal (how far the x
+// gathers of a row stray from it; the paper names the block distribution's
+// effect on the x accesses as what Avg alone cannot tell) and the number of
+// rows of at most two entries. A warp per 32 rows, its lanes splitting each
+// row's entries; integer sums, so the result does not depend on the order.
+__global__ void k_matrix_stats(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
+                               unsigned long long* __restrict__ acc) {
+  const int lane = threadIdx.x & 31;
+  const int64_t r0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32;
+  if (r0 >= n) return;  // whole warp
+  unsigned long long dist = 0, shortrows = 0;
+  const int64_t r1 = r0 + 32 < n ? r0 + 32 : n;
+  for (int64_t i = r0; i < r1; ++i) {
+    const int64_t a = rowptr[i], b = rowptr[i + 1];
+    if (lane == 0 && b - a <= 2) ++shortrows;
+    for (int64_t p = a + lane; p < b; p += 32) {
+      const int64_t d = (int64_t)colidx[p] - i;
+      dist += (unsigned long long)(d < 0 ? -d : d);
+    }
+  }
+#pragma unroll
+  for (int d = 16; d >= 1; d >>= 1) dist += __shfl_xor_sync(0xffffffffu, dist, d);
+  if (lane == 0) {
+    atomicAdd(acc, dist);
+    atomicAdd(acc + 1, shortrows);
+  }
+}
+
+spc5_status features_ext_impl(int64_t n, int64_t nnz, const int64_t* rowptr, const int32_t* colidx,
+                              double sm_frac, double* f, cudaStream_t s) {
+  spc5_status st = features_impl(n, nnz, rowptr, colidx, f, s);
+  if (st != SPC5_OK) return st;
+  DBuf acc;
+  cudaError_t e = cudaMalloc(&acc.p, sizeof(unsigned long long) * 2);
+  if (e == cudaSuccess) e = cudaMemsetAsync(acc.p, 0, sizeof(unsigned long long) * 2, s);
+  if (e == cudaSuccess && n > 0) {
+    const int64_t warps = (n + 31) / 32;
+    k_matrix_stats<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(n, rowptr, colidx,
+                                                                       (unsigned long long*)acc.p);
+    e = cudaGetLastError();
+  }
+  unsigned long long h[2] = {0ull, 0ull};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h, acc.p, sizeof(h), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "features_ext");
+  const double mean_dist = nnz > 0 ? (double)h[0] / (double)nnz : 0.0;
+  f[16] = n > 0 ? mean_dist / (double)n : 0.0;
+  f[17] = std::log10(1.0 + mean_dist);
+  f[18] = n > 0 ? (double)h[1] / (double)n : 0.0;
+  f[19] = sm_frac;
+  return SPC5_OK;
+}
+
 spc5_status mlp_train_impl(float* P, const float* X, const float* Y, const float* M, int N, int epochs, int batch,
-                           float lr, uint64_t seed, float* loss_hist, cudaStream_t s) {
+                           float lr, uint64_t seed, float* loss_hist, cudaStream_t s, int nfeat) {
   if (batch < 1 || batch > kMaxBatch) return fail(SPC5_EINVAL, "mlp_train: batch must be in [1, 32]");
+  if (nfeat != 16 && nfeat != 20) return fail(SPC5_EINVAL, "mlp_train: nfeat must be 16 or 20");
+  const int kNP = mlp_param_count(nfeat);
   const int steps_per_epoch = (N + batch - 1) / batch;
   DBuf mom, vel, idx, loss;
   cudaError_t e = cudaMalloc(&mom.p, sizeof(float) * kNP);
@@ -262,8 +329,12 @@ spc5_status mlp_train_impl(float* P, const float* X, const float* Y, const float
       const int b0 = st * batch;
       const int B = N - b0 < batch ? N - b0 : batch;
       ++t;
-      k_mlp_step<<<1, kStepThreads, 0, s>>>(P, (float*)mom.p, (float*)vel.p, X, Y, M, (const int32_t*)idx.p + b0, B,
-                                            t, lr, (float*)loss.p + st, nullptr);
+      if (nfeat == 16)
+        k_mlp_step<16><<<1, kStepThreads, 0, s>>>(P, (float*)mom.p, (float*)vel.p, X, Y, M, (const int32_t*)idx.p + b0,
+                                                  B, t, lr, (float*)loss.p + st, nullptr);
+      else
+        k_mlp_step<20><<<1, kStepThreads, 0, s>>>(P, (float*)mom.p, (float*)vel.p, X, Y, M, (const int32_t*)idx.p + b0,
+                                                  B, t, lr, (float*)loss.p + st, nullptr);
     }
     e = cudaMemcpyAsync(lh.data(), loss.p, sizeof(float) * (size_t)steps_per_epoch, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -278,8 +349,10 @@ spc5_status mlp_train_impl(float* P, const float* X, const float* Y, const float
 }
 
 spc5_status mlp_grad_impl(const float* P, const float* X, const float* Y, const float* M, int B, float* loss,
-                          float* grad, cudaStream_t s) {
+                          float* grad, cudaStream_t s, int nfeat) {
   if (B < 1 || B > kMaxBatch) return fail(SPC5_EINVAL, "mlp_grad: batch must be in [1, 32]");
+  if (nfeat != 16 && nfeat != 20) return fail(SPC5_EINVAL, "mlp_grad: nfeat must be 16 or 20");
+  const int kNP = mlp_param_count(nfeat);
   std::vector<int32_t> order((size_t)B);
   for (int i = 0; i < B; ++i) order[(size_t)i] = i;
   DBuf idx, l, Pc;
@@ -291,8 +364,12 @@ spc5_status mlp_grad_impl(const float* P, const float* X, const float* Y, const 
     e = cudaMemcpyAsync(idx.p, order.data(), sizeof(int32_t) * (size_t)B, cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return cuda_fail(e, "mlp_grad: workspace");
   // lr = 0: gradient only, the parameter copy is left as it is
-  k_mlp_step<<<1, kStepThreads, 0, s>>>((float*)Pc.p, nullptr, nullptr, X, Y, M, (const int32_t*)idx.p, B, 1, 0.f,
-                                        (float*)l.p, grad);
+  if (nfeat == 16)
+    k_mlp_step<16><<<1, kStepThreads, 0, s>>>((float*)Pc.p, nullptr, nullptr, X, Y, M, (const int32_t*)idx.p, B, 1,
+                                              0.f, (float*)l.p, grad);
+  else
+    k_mlp_step<20><<<1, kStepThreads, 0, s>>>((float*)Pc.p, nullptr, nullptr, X, Y, M, (const int32_t*)idx.p, B, 1,
+                                              0.f, (float*)l.p, grad);
   e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaMemcpyAsync(loss, l.p, sizeof(float), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -300,8 +377,10 @@ spc5_status mlp_grad_impl(const float* P, const float* X, const float* Y, const 
   return SPC5_OK;
 }
 
-spc5_status mlp_infer_impl(const float* P, const float* X, int N, float* out, cudaStream_t s) {
-  if (N > 0) k_mlp_infer<<<(unsigned)((N + 127) / 128), 128, 0, s>>>(P, X, N, out);
+spc5_status mlp_infer_impl(const float* P, const float* X, int N, float* out, cudaStream_t s, int nfeat) {
+  if (nfeat != 16 && nfeat != 20) return fail(SPC5_EINVAL, "mlp_infer: nfeat must be 16 or 20");
+  if (N > 0 && nfeat == 16) k_mlp_infer<16><<<(unsigned)((N + 127) / 128), 128, 0, s>>>(P, X, N, out);
+  if (N > 0 && nfeat == 20) k_mlp_infer<20><<<(unsigned)((N + 127) / 128), 128, 0, s>>>(P, X, N, out);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "mlp_infer");
   return SPC5_OK;
@@ -384,6 +463,6 @@ int poly2_select_impl(const double* coef, int degree, const double* feat, double
   return best;
 }
 
-int mlp_param_count() { return kNP; }
+int mlp_param_count(int nfeat) { return nfeat == 20 ? Mlp<20>::NP : Mlp<16>::NP; }
 
 }  // namespace spc5

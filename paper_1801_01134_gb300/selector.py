@@ -83,7 +83,7 @@ def record_sm(indices, sm_counts, seed: int = 3, dtype=torch.float64, reps: int 
     for i in indices:
         A = inputs.corpus_matrix(i, seed=seed, n_max=n_max)
         d = spc5.upload_csr(A, dtype, "cuda")
-        F.append(spc5.features(d))
+        F.append(spc5.features_ext(d, 1.0))  # the SM fraction (last input) is set per SM count later
         T.append([spc5.time_formats(d, reps=reps, stream=st.stream) for st in streams])
         NNZ.append(A.nnz)
         del d
@@ -106,6 +106,30 @@ def fit_poly2(F, T, nnz, sfrac, degree):
 
 def poly2_choices(coef, degree, F, sfrac_one: float) -> np.ndarray:
     return np.array([SHAPES.index(spc5.poly2_select(coef, degree, f, sfrac_one)[:2]) for f in F])
+
+
+def ext_samples(F, T, sfrac):
+    """(matrix, SM count) samples for the 20-input MLP: the extended features with
+    the SM fraction as the last input, targets the centred log times."""
+    N, S, _ = T.shape
+    X = np.repeat(F[:, None, :], S, axis=1).copy()
+    X[:, :, 19] = np.asarray(sfrac)[None, :]
+    return X.reshape(N * S, 20), T.reshape(N * S, 12)
+
+
+def train_mlp_ext(X, T, epochs: int, seed: int = 0, lr: float = 2e-3, batch: int = 32):
+    Xn, mean, scale = mlp_inputs(X)
+    Y = centred_log(T).astype(np.float32)
+    g = torch.Generator().manual_seed(seed)
+    parts = []
+    for fan_out, fan_in in ((64, 20), (64, 64), (12, 64)):
+        parts.append(torch.randn(fan_out * fan_in, generator=g) * np.sqrt(2.0 / fan_in))
+        parts.append(torch.zeros(fan_out))
+    params = torch.cat(parts).float().cuda().contiguous()
+    assert params.numel() == spc5.mlp_nparams(20)
+    Xd, Yd, Md = (torch.from_numpy(a).cuda().contiguous() for a in (Xn, Y, np.ones_like(Y)))
+    hist = spc5.mlp_train(params, Xd, Yd, Md, epochs=epochs, batch=batch, lr=lr, seed=seed)
+    return params, mean, scale, hist
 
 
 def sm_axis_main(args, log):
@@ -141,24 +165,46 @@ def sm_axis_main(args, log):
     if args.mlp_model:
         z = np.load(args.mlp_model)
         mlp = (torch.from_numpy(z["mlp_params"]).cuda(), z["feat_mean"], z["feat_scale"])
+    # the MLP with the richer inputs (x-access locality, short rows, SM fraction),
+    # epochs and seed chosen on a validation split of the training matrices
+    va = np.arange(Ftr.shape[0]) % 7 == 0
+    Xtr_v, Ttr_v = ext_samples(Ftr[~va], Ttr[~va], sfrac)
+    best_m = None
+    for ep in (50, 100, 200, 400):
+        for sd in (0, 1):
+            p_, m_, s_, _ = train_mlp_ext(Xtr_v, Ttr_v, ep, sd)
+            rv = []
+            for j, sf in enumerate(sfrac):
+                Xv, _ = ext_samples(Ftr[va], Ttr[va][:, j:j + 1], [sf])
+                rv.append(regret(Ttr[va, j], mlp_choices(p_, Xv, m_, s_)))
+            rv = float(np.concatenate(rv).mean())
+            log(f"extended MLP epochs {ep} seed {sd}: validation mean regret {rv:.4f}")
+            if best_m is None or rv < best_m[0]:
+                best_m = (rv, ep, sd)
+    Xall, Tall = ext_samples(Ftr, Ttr, sfrac)
+    pe, me, se, he = train_mlp_ext(Xall, Tall, best_m[1], best_m[2])
     per = {}
     for j, k in enumerate(sms):
+        Xte_j, _ = ext_samples(Fte, Tte[:, j:j + 1], [sfrac[j]])
         row = {"sm_fraction": round(sfrac[j], 4),
+               "mlp_ext": summary(regret(Tte[:, j], mlp_choices(pe, Xte_j, me, se))),
                "poly2": summary(regret(Tte[:, j], poly2_choices(coef2, deg2, Fte, sfrac[j]))),
                "poly_whole_gpu": summary(regret(Tte[:, j], poly_choices(coef1, Fte))),
                "fixed_whole_gpu": summary(regret(Tte[:, j], np.full(Tte.shape[0], fixed)))}
         if mlp is not None:
-            row["mlp_whole_gpu"] = summary(regret(Tte[:, j], mlp_choices(mlp[0], Fte, mlp[1], mlp[2])))
+            row["mlp_whole_gpu"] = summary(regret(Tte[:, j], mlp_choices(mlp[0], Fte[:, :16], mlp[1], mlp[2])))
         # how often the best shape on k SMs differs from the best on the whole GPU
         row["best_differs_from_whole_gpu"] = float((Tte[:, j].argmin(axis=1) != Tte[:, jf].argmin(axis=1)).mean())
         per[str(k)] = row
     res = {"train": args.train, "test": args.test, "sm_counts": sms, "poly2_degree": deg2, "poly_degree": deg1,
+           "mlp_ext_epochs": best_m[1], "mlp_ext_seed": best_m[2], "mlp_ext_validation_regret": best_m[0],
            "fixed_shape": f"{SHAPES[fixed][0]}x{SHAPES[fixed][1]}", "regret_by_sm_count": per}
     log(json.dumps(res))
     if args.out:
         np.savez(args.out, Ftr=Ftr.astype(np.float32), Ttr=Ttr.astype(np.float32), Ntr=Ntr,
                  Fte=Fte.astype(np.float32), Tte=Tte.astype(np.float32), Nte=Nte, sm_counts=np.array(sms),
-                 poly2_coef=coef2, poly2_degree=deg2, result=json.dumps(res))
+                 poly2_coef=coef2, poly2_degree=deg2, mlp_ext_params=pe.cpu().numpy(), mlp_ext_mean=me,
+                 mlp_ext_scale=se, mlp_ext_loss=he, result=json.dumps(res))
 
 
 def mlp_inputs(F: np.ndarray, mean=None, scale=None):

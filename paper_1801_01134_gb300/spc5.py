@@ -135,6 +135,12 @@ def load(build_if_missing: bool = False):
     lib.spc5_time_formats.argtypes = [i64, i64, i64, vp, vp, vp, i32, vp, vp, i32, vp, vp]
     lib.spc5_mlp_nparams.argtypes = []
     lib.spc5_mlp_nparams.restype = i32
+    lib.spc5_mlp_nparams_n.argtypes = [i32]
+    lib.spc5_mlp_nparams_n.restype = i32
+    lib.spc5_features_ext.argtypes = [i64, i64, i64, vp, vp, ctypes.c_double, vp, vp]
+    lib.spc5_mlp_train_n.argtypes = [vp, vp, vp, vp, i32, i32, i32, i32, ctypes.c_float, ctypes.c_uint64, vp, vp]
+    lib.spc5_mlp_grad_n.argtypes = [vp, vp, vp, vp, i32, i32, vp, vp, vp]
+    lib.spc5_mlp_infer_n.argtypes = [vp, vp, i32, i32, vp, vp]
     lib.spc5_mlp_train.argtypes = [vp, vp, vp, vp, i32, i32, i32, ctypes.c_float, ctypes.c_uint64, vp, vp]
     lib.spc5_mlp_grad.argtypes = [vp, vp, vp, vp, i32, vp, vp, vp]
     lib.spc5_mlp_infer.argtypes = [vp, vp, i32, vp, vp]
@@ -146,7 +152,8 @@ def load(build_if_missing: bool = False):
               lib.spc5_spmv_noalloc, lib.spc5_launch_count, lib.spc5_device_peaks, lib.spc5_tune,
               lib.spc5_tune_cache_clear, lib.spc5_convert_rows, lib.spc5_pool_trim, lib.spc5_csr_plan_create,
               lib.spc5_csr_spmv_plan, lib.spc5_csr_plan_info, lib.spc5_csr_plan_destroy, lib.spc5_sm_stream_create,
-              lib.spc5_sm_stream_destroy, lib.spc5_poly2_fit, lib.spc5_poly2_select, lib.spc5_cg, lib.spc5_spmm, lib.spc5_features,
+              lib.spc5_sm_stream_destroy, lib.spc5_poly2_fit, lib.spc5_poly2_select, lib.spc5_features_ext,
+              lib.spc5_mlp_train_n, lib.spc5_mlp_grad_n, lib.spc5_mlp_infer_n, lib.spc5_cg, lib.spc5_spmm, lib.spc5_features,
               lib.spc5_time_formats, lib.spc5_mlp_train, lib.spc5_mlp_grad, lib.spc5_mlp_infer, lib.spc5_poly_fit,
               lib.spc5_select, lib.spc5_batch_create, lib.spc5_batch_spmv, lib.spc5_batch_spmv_direct,
               lib.spc5_batch_destroy, lib.spc5_partition):
@@ -498,31 +505,41 @@ def time_formats(d: "DeviceCSR", reps: int = 5, stream=None) -> np.ndarray:
     return out
 
 
-def mlp_nparams() -> int:
-    return int(load().spc5_mlp_nparams())
+def mlp_nparams(nfeat: int = 16) -> int:
+    return int(load().spc5_mlp_nparams_n(nfeat))
+
+
+def features_ext(d: "DeviceCSR", sm_frac: float = 1.0, stream=None) -> np.ndarray:
+    """The 20 extended selection features (spc5_features_ext)."""
+    out = np.zeros(20, dtype=np.float64)
+    _check(load().spc5_features_ext(d.n, d.m, d.nnz, _ptr(d.rowptr), _ptr(d.colidx), sm_frac, out.ctypes.data,
+                                    _stream_ptr(stream)), "spc5_features_ext")
+    return out
 
 
 def mlp_train(params: torch.Tensor, X: torch.Tensor, Y: torch.Tensor, M: torch.Tensor, epochs: int, batch: int = 32,
               lr: float = 1e-3, seed: int = 0, stream=None) -> np.ndarray:
-    """Train the format-scoring MLP in place on the GPU; returns the per-epoch mean loss."""
+    """Train the format-scoring MLP (16 or 20 inputs: X.shape[1]) in place on the GPU;
+    returns the per-epoch mean loss."""
     hist = np.zeros(max(epochs, 1), dtype=np.float32)
-    _check(load().spc5_mlp_train(_ptr(params), _ptr(X), _ptr(Y), _ptr(M), X.shape[0], epochs, batch, lr, seed,
-                                 hist.ctypes.data, _stream_ptr(stream)), "spc5_mlp_train")
+    _check(load().spc5_mlp_train_n(_ptr(params), _ptr(X), _ptr(Y), _ptr(M), X.shape[0], X.shape[1], epochs, batch,
+                                   lr, seed, hist.ctypes.data, _stream_ptr(stream)), "spc5_mlp_train")
     return hist[:epochs]
 
 
 def mlp_grad(params: torch.Tensor, X: torch.Tensor, Y: torch.Tensor, M: torch.Tensor, stream=None):
     """(loss, gradient) of the first X.shape[0] <= 32 samples."""
-    g = torch.empty(mlp_nparams(), dtype=torch.float32, device=params.device)
+    g = torch.empty(mlp_nparams(X.shape[1]), dtype=torch.float32, device=params.device)
     loss = ctypes.c_float()
-    _check(load().spc5_mlp_grad(_ptr(params), _ptr(X), _ptr(Y), _ptr(M), X.shape[0], ctypes.byref(loss), _ptr(g),
-                                _stream_ptr(stream)), "spc5_mlp_grad")
+    _check(load().spc5_mlp_grad_n(_ptr(params), _ptr(X), _ptr(Y), _ptr(M), X.shape[0], X.shape[1],
+                                  ctypes.byref(loss), _ptr(g), _stream_ptr(stream)), "spc5_mlp_grad")
     return float(loss.value), g
 
 
 def mlp_infer(params: torch.Tensor, X: torch.Tensor, stream=None) -> torch.Tensor:
     out = torch.empty(X.shape[0], NFORMATS, dtype=torch.float32, device=params.device)
-    _check(load().spc5_mlp_infer(_ptr(params), _ptr(X), X.shape[0], _ptr(out), _stream_ptr(stream)), "spc5_mlp_infer")
+    _check(load().spc5_mlp_infer_n(_ptr(params), _ptr(X), X.shape[0], X.shape[1], _ptr(out), _stream_ptr(stream)),
+           "spc5_mlp_infer")
     return out
 
 

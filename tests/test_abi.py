@@ -89,6 +89,11 @@ def test_host_side_argument_checks(lib):
     assert lib.spc5_sm_stream_create(0, ctypes.byref(st), None) == spc5.EINVAL
     assert lib.spc5_sm_stream_create(8, None, None) == spc5.EINVAL
     assert lib.spc5_sm_stream_destroy(None) == spc5.OK
+    assert lib.spc5_mlp_nparams_n(16) == 6028 and lib.spc5_mlp_nparams_n(20) == 6028 + 4 * 64
+    assert lib.spc5_mlp_nparams_n(17) == -1
+    f20 = (ctypes.c_double * 20)()
+    assert lib.spc5_features_ext(4, 4, 0, 1, None, ctypes.c_double(0.0), f20, None) == spc5.EINVAL  # sm_frac
+    assert lib.spc5_mlp_infer_n(None, None, 1, 16, None, None) == spc5.EINVAL
     assert lib.spc5_convert_rows(4, 4, 0, 1, None, None, 0, 2, 8, 1, 4, None, None, ctypes.byref(h)) == spc5.EINVAL
     assert lib.spc5_autotune(None, None, None, 3, None, None, None) == spc5.EINVAL
 

@@ -129,3 +129,39 @@ def test_committed_model_beats_the_paper_predictor_on_held_out(cuda_device):
     assert r_mlp.mean() < r_poly.mean()
     rec = json.loads(str(z["result"]))
     assert abs(rec["regret_mlp"]["mean"] - r_mlp.mean()) <= 0.005
+
+
+@pytest.mark.parametrize("make", [
+    lambda: inputs.stencil3d(13, 11, 7, points=27, seed=4),
+    lambda: inputs.rmat(11, seed=2),
+    lambda: inputs.random_csr(301, 517, 0.03, seed=3),
+    lambda: inputs.uniform(3001, 2500, 8, seed=5),
+])
+def test_features_ext_match_oracle(cuda_device, make):
+    A = make()
+    d = spc5.upload_csr(A, torch.float64, "cuda")
+    got = spc5.features_ext(d, 0.5)
+    want = osel.features_ext(A, 0.5)
+    assert np.array_equal(got[:12], want[:12]) and np.array_equal(got[18:], want[18:])
+    assert np.allclose(got[12:18], want[12:18], rtol=1e-12, atol=1e-15)
+
+
+def test_mlp_20_inputs_forward_and_gradient_match_float64_oracle(cuda_device):
+    rng = np.random.default_rng(4)
+    th = (rng.standard_normal(spc5.mlp_nparams(20)) * 0.2).astype(np.float32)
+    X = rng.standard_normal((23, 20)).astype(np.float32)
+    Y = rng.standard_normal((23, 12)).astype(np.float32)
+    M = (rng.random((23, 12)) > 0.3).astype(np.float32)
+    P = torch.from_numpy(th).cuda()
+    out = spc5.mlp_infer(P, torch.from_numpy(X).cuda()).cpu().numpy()
+    ref, _ = osel.mlp_forward(th.astype(np.float64), X.astype(np.float64))
+    assert np.abs(out - ref).max() <= 1e-4 * max(1.0, np.abs(ref).max())
+    loss, g = spc5.mlp_grad(P, torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda(), torch.from_numpy(M).cuda())
+    gref = osel.mlp_grad(th.astype(np.float64), X.astype(np.float64), Y.astype(np.float64), M.astype(np.float64))
+    assert np.abs(g.cpu().numpy() - gref).max() <= 1e-4 * np.abs(gref).max()
+    # training on it lowers the loss
+    Xs = rng.standard_normal((300, 20)).astype(np.float32)
+    Ys = np.tanh(Xs[:, :12]).astype(np.float32)
+    hist = spc5.mlp_train(P, torch.from_numpy(Xs).cuda(), torch.from_numpy(Ys).cuda(),
+                          torch.ones(300, 12, device="cuda"), epochs=30)
+    assert hist[-1] < 0.5 * hist[0]

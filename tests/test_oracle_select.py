@@ -138,3 +138,30 @@ def test_poly2_select_takes_the_highest_estimate_at_the_sm_fraction():
     f = np.full(osel.NFEAT, 2.0)
     assert osel.poly2_select(coefs, deg, f, 0.25) == 5
     assert osel.poly2_select(coefs, deg, f, 1.0) == 3
+
+
+def test_features_ext_hand_worked():
+    # rows: [0: cols 0, 3], [1: col 1], [2: cols 0, 2, 4, 5]; distances |col - row|:
+    # 0, 3 | 0 | 2, 0, 2, 3 -> sum 10 over 7 entries; rows with <= 2 entries: 2 of 3
+    D = np.zeros((3, 6))
+    D[0, [0, 3]] = 1.0
+    D[1, 1] = 1.0
+    D[2, [0, 2, 4, 5]] = 1.0
+    f = osel.features_ext(inputs.CSR.from_dense(D), 0.25)
+    assert abs(f[16] - (10 / 7) / 3) < 1e-15 and abs(f[17] - np.log10(1 + 10 / 7)) < 1e-15
+    assert abs(f[18] - 2 / 3) < 1e-15 and f[19] == 0.25
+    assert np.array_equal(f[:16], osel.features(inputs.CSR.from_dense(D)))
+
+
+def test_mlp_with_20_inputs_gradient_matches_central_differences():
+    rng = np.random.default_rng(11)
+    theta = rng.standard_normal(osel.mlp_nparams(20)) * 0.3
+    X = rng.standard_normal((5, 20))
+    Y = rng.standard_normal((5, osel.NFMT))
+    g = osel.mlp_grad(theta, X, Y)
+    h = 1e-6
+    for i in rng.choice(theta.size, 80, replace=False):
+        e = np.zeros_like(theta)
+        e[i] = h
+        fd = (osel.mlp_loss(theta + e, X, Y) - osel.mlp_loss(theta - e, X, Y)) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(fd))
