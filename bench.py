@@ -40,8 +40,9 @@ FP64_PEAK_GFLOPS = 1250.0  # nominal GB300 float64 rate (2 FMA lanes/clk/SM x 15
 # short-interval kernel variants the tuner tries per shape: float64 keeps to the
 # flattened decodes (16's unrolled positions cost float64 pipe slots when empty)
 VARIANTS = {"f64": (5, 10, 13, 15, 24), "f32": (5, 10, 13, 15, 16, 18, 24, 28)}
-# beta(1,c) only: two lanes per row (natural, sorted order), Algorithm 2's single-value test (sorted, natural)
-GROUP_VARIANTS = (22, 23, 30, 31)
+# beta(1,c) only: two lanes per row (natural, sorted order), Algorithm 2's single-value test (sorted, natural),
+# the warp streaming its rows' blocks (float32 / bfloat16 only)
+GROUP_VARIANTS = (22, 23, 30, 31, 32)
 CG_INNER_VARIANT = 18  # decode of the float32 / bfloat16 inner CG handle (unrolled positions, two blocks a trip)
 
 
@@ -104,7 +105,8 @@ def profile_matrices():
 
 
 # sources that decide the SpMV kernels and the layout they read
-SPMV_SOURCES = ("internal.cuh", "spmv_beta.cuh", "spmv_f64.cu", "spmv_f32.cu", "spmv_bf16.cu", "convert.cu")
+SPMV_SOURCES = ("internal.cuh", "spmv_beta.cuh", "spmv_group.cuh", "spmv_stream.cuh", "spmv_f64.cu", "spmv_f32.cu",
+                "spmv_bf16.cu", "spmv_group_f64.cu", "spmv_group_f32.cu", "spmv_group_bf16.cu", "convert.cu")
 
 
 def kernel_source_hash() -> str:
@@ -782,7 +784,8 @@ def main():
             for (r, c) in shapes:
                 M = spc5.convert(d.rowptr, d.colidx, d.values, A.n, A.m, r, c)
                 tv = {}
-                for v in VARIANTS["f64" if dtype == torch.float64 else "f32"] + (GROUP_VARIANTS if r == 1 else ()):
+                group = tuple(v for v in GROUP_VARIANTS if dtype != torch.float64 or v != 32)
+                for v in VARIANTS["f64" if dtype == torch.float64 else "f32"] + (group if r == 1 else ()):
                     M.set_variant(v)
                     tv[v] = time_call(lambda: M.spmv(xd, yd), 5)
                 v = min(tv, key=tv.get)

@@ -95,6 +95,15 @@ typedef struct {
    *           whose blocks all hold one value is read like CSR (no mask
    *           decode), other rows with the mask windows; sorted / natural
    *           order. Same sums as 0-19.
+   *   32      r = 1 only: the warp streams the blocks of its 32 rows, two
+   *           adjacent blocks per lane whatever row they belong to; a scan of
+   *           the popcounts places the values, a segmented scan over the
+   *           lanes adds each row's blocks, a row running past a trip carries
+   *           its partial sum. Mask, column and value reads are consecutive
+   *           over the warp and no lane idles on a shorter row; warps that
+   *           hold a long interval take one lane per row instead. Sums differ
+   *           from 0-19 by rounding only. A float32 / bfloat16 form (its
+   *           float64 cost is set by the busiest lane's block).
    * spc5_cg uses the decode of 16 or 18 when its handle has that variant,
    * the flattened one otherwise.
    * Variants 0-19, 30 and 31 compute the same sums in the same order per
@@ -203,7 +212,7 @@ spc5_status spc5_spmv_acc(spc5_handle h, const void* x_d, void* y_d, spc5_stream
  * builds the sorted work order, and 30 or 31 the single-value class bits, if
  * the handle has none yet (synchronises `stream`); the other values take
  * effect with no device work. SPC5_EINVAL for an unknown variant,
- * SPC5_EUNSUPPORTED for 22, 23, 30 or 31 on a handle with r > 1.
+ * SPC5_EUNSUPPORTED for 22, 23, 30, 31 or 32 on a handle with r > 1.
  */
 spc5_status spc5_set_variant(spc5_handle h, int variant, spc5_stream_t stream);
 
@@ -213,8 +222,8 @@ spc5_status spc5_set_variant(spc5_handle h, int variant, spc5_stream_t stream);
  * overwritten) and keep the fastest; the GPU form of the paper's choice of
  * the best kernel for a matrix (section "Performance prediction and optimal
  * kernel selection"). Candidates: variants 5, 10, 13, 15, plus 16 and 18 for
- * float32 / bfloat16 values and 22, 23 for r = 1 (the ones that win on some
- * matrix). Writes the
+ * float32 / bfloat16 values and 22, 23, 30 for r = 1, and 32 for r = 1 with
+ * float32 / bfloat16 values (the ones that win on some matrix). Writes the
  * chosen variant and its median milliseconds (either pointer may be NULL).
  * Synchronises `stream`. On error the handle keeps its previous variant.
  */
@@ -399,7 +408,8 @@ typedef struct {
 /*
  * spc5_tune - the library's autotuner: times every block shape (twelve) x the
  * kernel variants that win on some matrix (float64: 5, 10, 13, 15, 24;
- * float32 / bfloat16 also 16, 18; r = 1 also 22, 23, 30, 31) and, when
+ * float32 / bfloat16 also 16, 18; r = 1 also 22, 23, 30, 31, and 32 for
+ * float32 / bfloat16) and, when
  * k_spmm > 0, every shape x SpMM column tile for k_spmm right-hand sides, on
  * this GPU (median of `reps` products after one untimed product, no cache
  * flush between them), and returns the fastest choices - the GPU form of the

@@ -23,10 +23,10 @@ constexpr int kOrderWindow = 1024;  // rows per sorting window of the work order
 // short-interval kernel variants (spc5_opts.variant)
 inline bool valid_variant(int v) {
   return v == 0 || v == 1 || v == 3 || v == 5 || v == 9 || v == 10 || (v >= 12 && v <= 19) || v == 22 || v == 23 ||
-         (v >= 24 && v <= 31);
+         (v >= 24 && v <= 32);
 }
-// variants that need r = 1 (two lanes per row)
-inline bool r1_variant(int v) { return v == 22 || v == 23 || v == 30 || v == 31; }
+// variants that need r = 1 (two lanes per row, Algorithm 2's test, block streaming)
+inline bool r1_variant(int v) { return v == 22 || v == 23 || v == 30 || v == 31 || v == 32; }
 // variants that take intervals in the sorted work order
 inline bool ordered_variant(int v) {
   return v == 9 || v == 10 || v == 13 || v == 15 || v == 17 || v == 19 || v == 23 || v == 28 || v == 29 || v == 30;
@@ -35,6 +35,8 @@ inline bool ordered_variant(int v) {
 inline bool group_variant(int v) { return v >= 24 && v <= 29; }
 // variants that read the single-value class bits (Algorithm 2's test)
 inline bool single_variant(int v) { return v == 30 || v == 31; }
+// the warp streams the blocks of its 32 rows, lane = block (spmv_stream.cuh)
+inline bool stream_variant(int v) { return v == 32; }
 
 struct Segment {  // one warp task of a long interval
   int32_t interval;

@@ -5,7 +5,7 @@ namespace spc5 {
 
 cudaError_t launch_spmv_bf16(const spc5_matrix* h, const void* x, void* y, bool acc, cudaStream_t s, void* partials) {
   void* part = partials ? partials : h->partials;
-  if (group_variant(h->variant)) return launch_group_bf16(h, x, y, acc, s, part);
+  if (group_variant(h->variant) || stream_variant(h->variant)) return launch_group_bf16(h, x, y, acc, s, part);
   return dispatch_beta<BF16>(h, x, y, acc, part, s);
 }
 

@@ -255,6 +255,77 @@ def test_single_value_test_variants(cuda_device, name, c, lb):
         M.destroy()
 
 
+def _wide_rows():
+    # rows of 80 to 600 entries in runs of 1 to 5 columns: blocks of one row
+    # cover several 32-block trips of the streaming warp (carry between trips)
+    rng = np.random.default_rng(11)
+    n, m = 70, 4000
+    rows, cols = [], []
+    for i in range(n):
+        if i % 9 == 4:
+            continue  # an empty row now and then
+        cs = set()
+        target = int(rng.integers(80, 600))
+        while len(cs) < target:
+            start = int(rng.integers(0, m - 5))
+            cs.update(range(start, start + int(rng.integers(1, 6))))
+        cs = sorted(cs)[:target]
+        rows += [i] * len(cs)
+        cols += cs
+    vals = inputs.vec_normal(len(cols), seed=12)
+    dense = np.zeros((n, m))
+    dense[np.array(rows), np.array(cols)] = vals
+    return inputs.CSR.from_dense(dense)
+
+
+@pytest.mark.parametrize("name", ["lap128", "rand_ragged", "st27_ragged", "rmat11", "uniform", "fem", "dense64",
+                                  "sparse_rows", "wide_rows"])
+@pytest.mark.parametrize("c", [4, 8, 16])
+@pytest.mark.parametrize("lb", [0, 2, 100000])
+def test_stream_variant(cuda_device, name, c, lb):
+    # variant 32: the warp streams the blocks of its 32 rows, lane = block, a
+    # segmented scan adds each row's run; warps holding a long row fall back
+    # to one lane per row (long_blocks 2 sends most rows there), and with
+    # long_blocks 100000 every row streams, carried across trips
+    A = _wide_rows() if name == "wide_rows" else get(name)
+    x = inputs.vec_uniform(A.m, seed=0)
+    y_ref, absy = oracle.csr_spmv_dot2(A, x)
+    d = dev_csr(A)
+    xd = torch.from_numpy(x).cuda()
+    M = spc5.convert(d.rowptr, d.colidx, d.values, A.n, A.m, 1, c, variant=32, long_blocks=lb)
+    buf, y = guarded(A.n, torch.float64)
+    M.spmv(xd, y)
+    check64(y.cpu().numpy(), y_ref, absy)
+    assert torch.isnan(buf[A.n:]).all(), "wrote past the end of y"
+    assert torch.equal(M.spmv(xd), y)
+    y0 = inputs.vec_uniform(A.n, seed=1)
+    yd = torch.from_numpy(y0.copy()).cuda()
+    M.spmv_acc(xd, yd)
+    assert np.all(np.abs(yd.cpu().numpy() - (y0 + y_ref)) <= TOL64 * (absy + np.abs(y0)) + 1e-300)
+    M.destroy()
+    L = np.diff(A.rowptr).astype(np.float64)
+    u = 2.0**-24
+    for kind in ("f32", "bf16"):
+        Ar = rounded_case(A, kind)
+        xr = oracle.round_f32(x)
+        yr_ref, absr = oracle.csr_spmv_dot2(Ar, xr)
+        vals = torch.from_numpy(Ar.values).to(torch.float32 if kind == "f32" else torch.bfloat16).cuda()
+        M = spc5.convert(d.rowptr, d.colidx, vals, A.n, A.m, 1, c, variant=32, long_blocks=lb)
+        buf, y = guarded(A.n, torch.float32)
+        M.spmv(torch.from_numpy(xr).float().cuda(), y)
+        assert np.all(np.abs(y.double().cpu().numpy() - yr_ref) <= (L + 1) * u / (1 - (L + 1) * u) * absr + 1e-45)
+        assert torch.isnan(buf[A.n:]).all()
+        M.destroy()
+
+
+def test_stream_variant_needs_r1(cuda_device):
+    A = get("fem")
+    d = dev_csr(A)
+    with pytest.raises(spc5.Spc5Error) as ei:
+        spc5.convert(d.rowptr, d.colidx, d.values, A.n, A.m, 2, 4, variant=32)
+    assert ei.value.status == spc5.EUNSUPPORTED
+
+
 def test_single_value_class_needs_r1(cuda_device):
     A = get("rmat11")
     d = dev_csr(A)
@@ -360,12 +431,12 @@ def test_autotune_keeps_a_candidate_and_the_result(cuda_device, dtype):
     ref = M.spmv(xd).clone()
     y = torch.empty_like(ref)
     v, ms = M.autotune(xd, y, reps=3)
-    cands = ((5, 10, 13, 15) if dtype == torch.float64 else (5, 10, 13, 15, 16, 18)) + (22,)
+    cands = ((5, 10, 13, 15) if dtype == torch.float64 else (5, 10, 13, 15, 16, 18, 32)) + (22, 23, 30)
     assert v in cands and ms > 0
     got = M.spmv(xd)
-    if v < 20:
-        assert torch.equal(got, ref)  # variants 0-19 add in the same order
-    else:  # two lanes per row add in their own fixed order
+    if v < 20 or v == 30:
+        assert torch.equal(got, ref)  # variants 0-19 and 30 add in the same order
+    else:  # two lanes per row, the streaming warp: their own fixed orders
         Ar = inputs.CSR(A.n, A.m, A.rowptr, A.colidx, vals)
         y_ref, absy = oracle.csr_spmv_dot2(Ar, xd.double().cpu().numpy())
         L = np.diff(A.rowptr).astype(np.float64)
