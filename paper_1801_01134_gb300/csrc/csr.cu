@@ -142,7 +142,7 @@ cudaError_t csr_dispatch(int G, int64_t n, const int64_t* rowptr, const int32_t*
   const V* val = static_cast<const V*>(values);
   const X* x = static_cast<const X*>(xv);
   X* y = static_cast<X*>(yv);
-  const int threads = 256;
+  const int threads = kSpmvThreads;
   const unsigned grid = (unsigned)((n * G + threads - 1) / threads);
   if (n == 0) return cudaSuccess;
   switch (G) {
@@ -187,7 +187,7 @@ cudaError_t csr_plan_launch(int G, int64_t n, int64_t long_len, const int64_t* r
   const X* x = static_cast<const X*>(xv);
   X* y = static_cast<X*>(yv);
   A* part = static_cast<A*>(partials);
-  const int threads = 256;
+  const int threads = kSpmvThreads;
   const int64_t seg_ctas = (nseg * 32 + threads - 1) / threads;
   const unsigned grid = (unsigned)(seg_ctas + (n * G + threads - 1) / threads);
   if (grid == 0) return cudaSuccess;

@@ -900,7 +900,7 @@ cudaError_t launch_beta(const spc5_matrix* h, const void* xv, void* yv, bool acc
   X* y = static_cast<X*>(yv);
   const V* val = static_cast<const V*>(h->values);
   constexpr int S = kWarp / R;
-  const int threads = 256;
+  const int threads = kSpmvThreads;
   const int v = h->variant;
   const bool ordered = ordered_variant(v) && h->norder > 0;
   A* part = static_cast<A*>(partials);

@@ -186,7 +186,7 @@ cudaError_t launch_grp_g(const spc5_matrix* h, const void* xv, void* yv, bool ac
   X* y = static_cast<X*>(yv);
   const typename T::V* val = static_cast<const typename T::V*>(h->values);
   A* part = static_cast<A*>(partials);
-  const int threads = 256;
+  const int threads = kSpmvThreads;
   const int64_t slots = ORDER ? h->norder : h->I;
   const int64_t seg_ctas = (h->nseg * kWarp + threads - 1) / threads;
   const unsigned grid = (unsigned)((slots * G + threads - 1) / threads);

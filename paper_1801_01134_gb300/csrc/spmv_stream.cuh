@@ -219,7 +219,7 @@ cudaError_t launch_stream_c(const spc5_matrix* h, const void* xv, void* yv, bool
   X* y = static_cast<X*>(yv);
   const typename T::V* val = static_cast<const typename T::V*>(h->values);
   A* part = static_cast<A*>(partials);
-  const int threads = 256;
+  const int threads = kSpmvThreads;
   const int64_t seg_ctas = (h->nseg * kWarp + threads - 1) / threads;
   const int64_t warps = (h->I + kWarp - 1) / kWarp;
   const unsigned grid = (unsigned)((warps * kWarp + threads - 1) / threads);
