@@ -41,8 +41,8 @@ FP64_PEAK_GFLOPS = 1250.0  # nominal GB300 float64 rate (2 FMA lanes/clk/SM x 15
 # flattened decodes (16's unrolled positions cost float64 pipe slots when empty)
 VARIANTS = {"f64": (5, 10, 13, 15, 24), "f32": (5, 10, 13, 15, 16, 18, 24, 28)}
 # beta(1,c) only: two lanes per row (natural, sorted order), Algorithm 2's single-value test (sorted, natural),
-# the warp streaming its rows' blocks (float32 / bfloat16 only)
-GROUP_VARIANTS = (22, 23, 30, 31, 32)
+# the warp streaming its rows' blocks (float32 / bfloat16 only), two lanes per row with Algorithm 2's test
+GROUP_VARIANTS = (22, 23, 30, 31, 32, 33)
 CG_INNER_VARIANT = 18  # decode of the float32 / bfloat16 inner CG handle (unrolled positions, two blocks a trip)
 
 

@@ -104,10 +104,15 @@ typedef struct {
    *           hold a long interval take one lane per row instead. Sums differ
    *           from 0-19 by rounding only. A float32 / bfloat16 form (its
    *           float64 cost is set by the busiest lane's block).
+   *   33      r = 1 only: 22 with Algorithm 2's single-value test (class bits
+   *           built when the variant is selected): a row whose blocks all
+   *           hold one value is read like a two-lane CSR row (no mask read);
+   *           the same sums as 22, bit for bit.
    * spc5_cg uses the decode of 16 or 18 when its handle has that variant,
    * the flattened one otherwise.
    * Variants 0-19, 30 and 31 compute the same sums in the same order per
-   * row; every variant repeats its own results bit for bit. */
+   * row, and so do 22 and 33; every variant repeats its own results bit for
+   * bit. */
   int32_t variant;
   /* Rows per sorting window of the work order of the sorted variants:
    * 0 selects 1024; a negative value sorts all intervals together. */
@@ -209,10 +214,10 @@ spc5_status spc5_spmv_acc(spc5_handle h, const void* x_d, void* y_d, spc5_stream
 /*
  * spc5_set_variant - switch the short-interval kernel variant of a handle
  * (values as in spc5_opts.variant). Selecting 9, 10, 13, 15, 17, 19, 23, 28, 29 or 30
- * builds the sorted work order, and 30 or 31 the single-value class bits, if
+ * builds the sorted work order, and 30, 31 or 33 the single-value class bits, if
  * the handle has none yet (synchronises `stream`); the other values take
  * effect with no device work. SPC5_EINVAL for an unknown variant,
- * SPC5_EUNSUPPORTED for 22, 23, 30, 31 or 32 on a handle with r > 1.
+ * SPC5_EUNSUPPORTED for 22, 23 or 30 to 33 on a handle with r > 1.
  */
 spc5_status spc5_set_variant(spc5_handle h, int variant, spc5_stream_t stream);
 
@@ -222,8 +227,8 @@ spc5_status spc5_set_variant(spc5_handle h, int variant, spc5_stream_t stream);
  * overwritten) and keep the fastest; the GPU form of the paper's choice of
  * the best kernel for a matrix (section "Performance prediction and optimal
  * kernel selection"). Candidates: variants 5, 10, 13, 15, plus 16 and 18 for
- * float32 / bfloat16 values and 22, 23, 30 for r = 1, and 32 for r = 1 with
- * float32 / bfloat16 values (the ones that win on some matrix). Writes the
+ * float32 / bfloat16 values and 22, 23, 30, 33 for r = 1, and 32 for r = 1
+ * with float32 / bfloat16 values (the ones that win on some matrix). Writes the
  * chosen variant and its median milliseconds (either pointer may be NULL).
  * Synchronises `stream`. On error the handle keeps its previous variant.
  */
@@ -408,8 +413,8 @@ typedef struct {
 /*
  * spc5_tune - the library's autotuner: times every block shape (twelve) x the
  * kernel variants that win on some matrix (float64: 5, 10, 13, 15, 24;
- * float32 / bfloat16 also 16, 18; r = 1 also 22, 23, 30, 31, and 32 for
- * float32 / bfloat16) and, when
+ * float32 / bfloat16 also 16, 18; r = 1 also 22, 23, 30, 31, 33, and 32
+ * for float32 / bfloat16) and, when
  * k_spmm > 0, every shape x SpMM column tile for k_spmm right-hand sides, on
  * this GPU (median of `reps` products after one untimed product, no cache
  * flush between them), and returns the fastest choices - the GPU form of the

@@ -133,9 +133,9 @@ spc5_status spc5_convert(int64_t n, int64_t m, int64_t nnz, const int64_t* rowpt
   if (vt != SPC5_F64 && vt != SPC5_F32 && vt != SPC5_BF16) return fail(SPC5_EUNSUPPORTED, "convert: value type");
   if (opt && (opt->long_blocks < 0 || opt->seg_blocks < 0 || opt->long_values < 0)) return fail(SPC5_EINVAL, "convert: negative option");
   if (opt && !valid_variant(opt->variant))
-    return fail(SPC5_EINVAL, "convert: variant must be 0, 1, 3, 5, 9, 10, 12..19 or 22..32");
+    return fail(SPC5_EINVAL, "convert: variant must be 0, 1, 3, 5, 9, 10, 12..19 or 22..33");
   if (opt && r1_variant(opt->variant) && r != 1)
-    return fail(SPC5_EUNSUPPORTED, "convert: variants 22, 23, 30, 31 and 32 need r = 1");
+    return fail(SPC5_EUNSUPPORTED, "convert: variants 22, 23 and 30 to 33 need r = 1");
   spc5_matrix* h = nullptr;
   st = convert_impl(n, m, nnz, rowptr_d, colidx_d, values_d, vt, r, c, opt, (cudaStream_t)stream, &h);
   if (st != SPC5_OK) return st;
@@ -157,9 +157,9 @@ spc5_status spc5_assemble(int64_t n, int64_t m, int64_t nnz, int64_t nblocks, co
     return fail(SPC5_EINVAL, "assemble: NULL array");
   if (opt && (opt->long_blocks < 0 || opt->seg_blocks < 0 || opt->long_values < 0)) return fail(SPC5_EINVAL, "assemble: negative option");
   if (opt && !valid_variant(opt->variant))
-    return fail(SPC5_EINVAL, "assemble: variant must be 0, 1, 3, 5, 9, 10, 12..19 or 22..32");
+    return fail(SPC5_EINVAL, "assemble: variant must be 0, 1, 3, 5, 9, 10, 12..19 or 22..33");
   if (opt && r1_variant(opt->variant) && r != 1)
-    return fail(SPC5_EUNSUPPORTED, "assemble: variants 22, 23, 30, 31 and 32 need r = 1");
+    return fail(SPC5_EUNSUPPORTED, "assemble: variants 22, 23 and 30 to 33 need r = 1");
   spc5_matrix* h = nullptr;
   spc5_status st = assemble_impl(n, m, nnz, nblocks, r, c, vt, block_rowptr_d, block_colidx_d, block_masks_d, values_d,
                                  opt, (cudaStream_t)stream, &h);
@@ -179,13 +179,13 @@ spc5_status spc5_spmv_acc(spc5_handle h, const void* x_d, void* y_d, spc5_stream
 spc5_status spc5_set_variant(spc5_handle h, int variant, spc5_stream_t stream) {
   if (!h) return fail(SPC5_EINVAL, "set_variant: NULL handle");
   if (!valid_variant(variant))
-    return fail(SPC5_EINVAL, "set_variant: variant must be 0, 1, 3, 5, 9, 10, 12..19 or 22..32");
-  if (r1_variant(variant) && h->r != 1) return fail(SPC5_EUNSUPPORTED, "set_variant: variants 22, 23, 30, 31 and 32 need r = 1");
+    return fail(SPC5_EINVAL, "set_variant: variant must be 0, 1, 3, 5, 9, 10, 12..19 or 22..33");
+  if (r1_variant(variant) && h->r != 1) return fail(SPC5_EUNSUPPORTED, "set_variant: variants 22, 23 and 30 to 33 need r = 1");
   if (ordered_variant(variant)) {
     spc5_status st = build_order(h, (cudaStream_t)stream);
     if (st != SPC5_OK) return st;
   }
-  if (single_variant(variant)) {
+  if (uses_single_bits(variant)) {
     spc5_status st = build_single_bits(h, (cudaStream_t)stream);
     if (st != SPC5_OK) return st;
   }
@@ -423,6 +423,7 @@ spc5_status spc5_autotune(spc5_handle h, const void* x_d, void* y_d, int reps, i
     cand.push_back(22);
     cand.push_back(23);
     cand.push_back(30);
+    cand.push_back(33);
     if (h->vt != SPC5_F64) cand.push_back(32);
   }
   const int ncand = (int)cand.size();

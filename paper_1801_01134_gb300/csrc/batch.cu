@@ -44,12 +44,12 @@ constexpr int kGrab = 8;
 
 // The decode of a matrix's short intervals, from its variant: 1 mask
 // windows (also for the block-streaming variant 32, whose one-lane fallback
-// they are), 4 Algorithm 2's single-value test (r = 1) with the mask windows
-// for the other rows, 0 the flattened decode for every other variant (the
-// batch maps one lane to one row).
+// they are), 4 Algorithm 2's single-value test (r = 1: variants 30, 31 and
+// the two-lane 33) with the mask windows for the other rows, 0 the flattened
+// decode for every other variant (the batch maps one lane to one row).
 inline int decode_of(int v, int r) {
   if (v == 12 || v == 13 || v == 14 || v == 15 || v == 32) return 1;
-  if ((v == 30 || v == 31) && r == 1) return 4;
+  if ((v == 30 || v == 31 || v == 33) && r == 1) return 4;
   return 0;
 }
 

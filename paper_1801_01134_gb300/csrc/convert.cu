@@ -1312,7 +1312,7 @@ spc5_status assemble_impl(int64_t n, int64_t m, int64_t nnz, int64_t nb, int r, 
     spc5_status st2 = build_order(h, s);
     if (st2 != SPC5_OK) return bail(st2);
   }
-  if (single_variant(h->variant)) {
+  if (uses_single_bits(h->variant)) {
     spc5_status st2 = build_single_bits(h, s);
     if (st2 != SPC5_OK) return bail(st2);
   }
@@ -1521,7 +1521,7 @@ spc5_status convert_impl(int64_t n, int64_t m, int64_t nnz, const int64_t* rowpt
     spc5_status st2 = build_order(h, s);
     if (st2 != SPC5_OK) return bail(st2);
   }
-  if (single_variant(h->variant)) {
+  if (uses_single_bits(h->variant)) {
     spc5_status st2 = build_single_bits(h, s);
     if (st2 != SPC5_OK) return bail(st2);
   }

@@ -30,10 +30,10 @@ constexpr int kOrderWindow = 1024;  // rows per sorting window of the work order
 // short-interval kernel variants (spc5_opts.variant)
 inline bool valid_variant(int v) {
   return v == 0 || v == 1 || v == 3 || v == 5 || v == 9 || v == 10 || (v >= 12 && v <= 19) || v == 22 || v == 23 ||
-         (v >= 24 && v <= 32);
+         (v >= 24 && v <= 33);
 }
 // variants that need r = 1 (two lanes per row, Algorithm 2's test, block streaming)
-inline bool r1_variant(int v) { return v == 22 || v == 23 || v == 30 || v == 31 || v == 32; }
+inline bool r1_variant(int v) { return v == 22 || v == 23 || v == 30 || v == 31 || v == 32 || v == 33; }
 // variants that take intervals in the sorted work order
 inline bool ordered_variant(int v) {
   return v == 9 || v == 10 || v == 13 || v == 15 || v == 17 || v == 19 || v == 23 || v == 28 || v == 29 || v == 30;
@@ -42,6 +42,8 @@ inline bool ordered_variant(int v) {
 inline bool group_variant(int v) { return v >= 24 && v <= 29; }
 // variants that read the single-value class bits (Algorithm 2's test)
 inline bool single_variant(int v) { return v == 30 || v == 31; }
+// variants that need the single-value class bits (30, 31 and the two-lane 33)
+inline bool uses_single_bits(int v) { return single_variant(v) || v == 33; }
 // the warp streams the blocks of its 32 rows, lane = block (spmv_stream.cuh)
 inline bool stream_variant(int v) { return v == 32; }
 

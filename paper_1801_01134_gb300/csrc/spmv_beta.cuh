@@ -541,15 +541,19 @@ __device__ __forceinline__ uint32_t rank_class_bits(uint32_t m, int cls) {
 }
 
 // With ORDER, row slot q of the warp takes row order[q] (the sorted work
-// order, short rows only) instead of row q.
-template <int C, class T, bool ACCUM, int G, int U, bool ORDER = false>
+// order, short rows only) instead of row q. With SGL (variant 33), a row whose
+// single-value class bit is set (Algorithm 2's test: every block holds one
+// value, at its first column) skips the masks: value j belongs to block
+// b0 + j, so lane g reads blocks g, g + 2, ... and their values like a
+// two-lane CSR kernel - the same values in the same order as the parity path.
+template <int C, class T, bool ACCUM, int G, int U, bool ORDER = false, bool SGL = false>
 __device__ __forceinline__ void rows_g_body(int64_t bid, int64_t n, int64_t I, int32_t long_blocks,
                                             int64_t long_values, const int32_t* __restrict__ brp,
                                             const int32_t* __restrict__ bcol, const uint8_t* __restrict__ bmask,
                                             const typename T::V* __restrict__ val,
                                             const int64_t* __restrict__ valptr, const typename T::X* __restrict__ x,
                                             typename T::X* __restrict__ y, const int32_t* __restrict__ order = nullptr,
-                                            int64_t norder = 0) {
+                                            int64_t norder = 0, const uint32_t* __restrict__ single = nullptr) {
   constexpr int MB = (C + 7) / 8;
   constexpr int S = kWarp / G;  // rows per warp
   using A = typename T::A;
@@ -571,10 +575,32 @@ __device__ __forceinline__ void rows_g_body(int64_t bid, int64_t n, int64_t I, i
     vp = v0 + g;
   }
   if (!have) bend = b;  // no work, but the group still meets at the shuffle below
+  A acc = 0;
+  if constexpr (SGL) {
+    if (have && ((__ldg(single + (it >> 5)) >> (it & 31)) & 1u)) {
+      const typename T::V* __restrict__ vrow = val + (vp - g);
+      const int32_t len = bend - b;
+      int32_t j = g;
+      for (; j + G * (U - 1) < len; j += G * U) {
+        int32_t cc[U];
+        A v[U], xx[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          cc[u] = __ldg(bcol + b + j + G * u);
+          v[u] = T::val(vrow, j + G * u);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) xx[u] = T::xv(x, cc[u]);
+#pragma unroll
+        for (int u = 0; u < U; ++u) acc = fmadd<T>(v[u], xx[u], acc);
+      }
+      for (; j < len; j += G) acc = fmadd<T>(T::val(vrow, j), T::xv(x, __ldg(bcol + b + j)), acc);
+      bend = b;  // the parity walk below has nothing left
+    }
+  }
   uint32_t sel = 0, nm = b < bend ? load_mask<MB>(bmask, b).w[0] : 0u;
   int32_t col0 = 0, ncol = b < bend ? __ldg(bcol + b) : 0;
   int before = 0;  // values of the row in the blocks already entered
-  A acc = 0;
   for (;;) {
     int64_t vi[U];
     int32_t xi[U];
@@ -631,6 +657,20 @@ __global__ void __launch_bounds__(256) k_spmv_rows_g(int64_t n, int64_t I, int32
                                                      int64_t norder) {
   rows_g_body<C, T, ACCUM, G, U, ORDER>(blockIdx.x, n, I, long_blocks, long_values, brp, bcol, bmask, val, valptr, x,
                                         y, order, norder);
+}
+
+// variant 33: two lanes per row with Algorithm 2's test (natural order)
+template <int C, class T, bool ACCUM, int U>
+__global__ void __launch_bounds__(256) k_spmv_rows_g1(int64_t n, int64_t I, int32_t long_blocks, int64_t long_values,
+                                                      const int32_t* __restrict__ brp, const int32_t* __restrict__ bcol,
+                                                      const uint8_t* __restrict__ bmask,
+                                                      const typename T::V* __restrict__ val,
+                                                      const int64_t* __restrict__ valptr,
+                                                      const typename T::X* __restrict__ x,
+                                                      typename T::X* __restrict__ y,
+                                                      const uint32_t* __restrict__ single) {
+  rows_g_body<C, T, ACCUM, 2, U, false, true>(blockIdx.x, n, I, long_blocks, long_values, brp, bcol, bmask, val, valptr,
+                                              x, y, nullptr, 0, single);
 }
 
 // ------------------------------------- Algorithm 2's test (beta(1,c))
@@ -792,6 +832,25 @@ __global__ void __launch_bounds__(256) k_spmv_rows_segs(int64_t seg_ctas, int64_
                                           bmask, val, valptr, x, y, order, norder);
 }
 
+// segments and the two-lane single-value test kernel in one grid (variant 33)
+template <int C, class T, bool ACCUM, int U>
+__global__ void __launch_bounds__(256) k_spmv_g1_segs(int64_t seg_ctas, int64_t n, int64_t I, int32_t long_blocks,
+                                                      int64_t long_values, const int32_t* __restrict__ brp,
+                                                      const int32_t* __restrict__ bcol,
+                                                      const uint8_t* __restrict__ bmask,
+                                                      const typename T::V* __restrict__ val,
+                                                      const int64_t* __restrict__ valptr,
+                                                      const typename T::X* __restrict__ x, typename T::X* __restrict__ y,
+                                                      const uint32_t* __restrict__ single, int64_t nseg,
+                                                      const Segment* __restrict__ segs,
+                                                      typename T::A* __restrict__ partials) {
+  if ((int64_t)blockIdx.x < seg_ctas)
+    segments_body<1, C, T, 4, 1>(blockIdx.x, nseg, segs, bcol, bmask, val, x, partials);
+  else
+    rows_g_body<C, T, ACCUM, 2, U, false, true>((int64_t)blockIdx.x - seg_ctas, n, I, long_blocks, long_values, brp,
+                                                bcol, bmask, val, valptr, x, y, nullptr, 0, single);
+}
+
 // segments and the single-value test kernel in one grid (variants 30 / 31)
 template <int C, class T, bool ACCUM, int U, bool ORDER>
 __global__ void __launch_bounds__(256) k_spmv_t_segs(int64_t seg_ctas, int64_t n, int64_t I, int32_t long_blocks,
@@ -886,7 +945,8 @@ __global__ void __launch_bounds__(256) k_spmv_fixup(int64_t n, int64_t nlong, co
 // windows, U=4/U=2; 13/15 sorted order, mask windows, U=4/U=2; 16/17
 // natural / sorted order, bit positions unrolled (row_sum_e); 18/19 the same
 // two blocks per trip (row_sum_e2); 22 (r = 1) two lanes per row taking
-// alternate stored values (rows_g_body), 23 the same in the sorted order;
+// alternate stored values (rows_g_body), 23 the same in the sorted order,
+// 33 the same in natural order with Algorithm 2's single-value test;
 // 30 / 31 (r = 1) Algorithm 2's single-value test in sorted / natural order
 // (rows_t_body). (Measured:
 // 8 nonzeros per trip is slower than 2 or 4 on every test matrix.)
@@ -940,7 +1000,23 @@ cudaError_t launch_beta(const spc5_matrix* h, const void* xv, void* yv, bool acc
       }
       rows_done = true;
     }
-    if (!rows_done && (v == 22 || v == 23) && h->I > 0) {
+    if (!rows_done && v == 33 && h->I > 0 && h->single_bits) {
+      constexpr int U = 2;
+      const int64_t warps = (h->I + kWarp / 2 - 1) / (kWarp / 2);
+      const unsigned grid = (unsigned)((warps * kWarp + threads - 1) / threads);
+      if (fused) {
+        auto kern = acc ? k_spmv_g1_segs<C, T, true, U> : k_spmv_g1_segs<C, T, false, U>;
+        kern<<<(unsigned)(seg_ctas + grid), threads, 0, s>>>(seg_ctas, h->n, h->I, h->long_blocks, h->long_values,
+                                                             h->block_rowptr, h->block_colidx, h->block_masks, val,
+                                                             h->valptr, x, y, h->single_bits, h->nseg, h->segs, part);
+      } else {
+        auto kern = acc ? k_spmv_rows_g1<C, T, true, U> : k_spmv_rows_g1<C, T, false, U>;
+        kern<<<grid, threads, 0, s>>>(h->n, h->I, h->long_blocks, h->long_values, h->block_rowptr, h->block_colidx,
+                                      h->block_masks, val, h->valptr, x, y, h->single_bits);
+      }
+      rows_done = true;
+    }
+    if (!rows_done && (v == 22 || v == 23 || v == 33) && h->I > 0) {
       constexpr int U = 2;
       const int64_t slots = ordered ? h->norder : h->I;
       const int64_t warps = (slots + kWarp / 2 - 1) / (kWarp / 2);

@@ -53,6 +53,7 @@ std::vector<int> tune_candidates(spc5_dtype vt, int r) {
     v.push_back(23);
     v.push_back(30);
     v.push_back(31);
+    v.push_back(33);
     if (vt != SPC5_F64) v.push_back(32);  // float64: the busiest lane's block sets the cost
   }
   return v;

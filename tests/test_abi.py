@@ -62,10 +62,10 @@ def test_host_side_argument_checks(lib):
     out = (ctypes.c_int64 * 12)()
     assert lib.spc5_count_blocks(4, 4, 0, None, None, out, None) == spc5.EINVAL
     # kernel variants: unknown numbers, and the two-lane form on r > 1, refused before any device work
-    for v, r, code in ((2, 1, spc5.EINVAL), (11, 1, spc5.EINVAL), (20, 1, spc5.EINVAL), (33, 1, spc5.EINVAL),
+    for v, r, code in ((2, 1, spc5.EINVAL), (11, 1, spc5.EINVAL), (20, 1, spc5.EINVAL), (34, 1, spc5.EINVAL),
                        (22, 2, spc5.EUNSUPPORTED), (22, 8, spc5.EUNSUPPORTED), (23, 4, spc5.EUNSUPPORTED),
                        (30, 2, spc5.EUNSUPPORTED), (31, 8, spc5.EUNSUPPORTED),
-                       (32, 2, spc5.EUNSUPPORTED), (32, 4, spc5.EUNSUPPORTED)):
+                       (32, 2, spc5.EUNSUPPORTED), (32, 4, spc5.EUNSUPPORTED), (33, 8, spc5.EUNSUPPORTED)):
         opts = spc5.Opts(0, 0, v, 0)
         assert lib.spc5_convert(4, 4, 0, 1, None, None, 0, r, 8, ctypes.byref(opts), None, ctypes.byref(h)) == code, v
     assert lib.spc5_set_variant(None, 22, None) == spc5.EINVAL

@@ -326,10 +326,39 @@ def test_stream_variant_needs_r1(cuda_device):
     assert ei.value.status == spc5.EUNSUPPORTED
 
 
+@pytest.mark.parametrize("name", ["lap128", "rand_ragged", "rmat11", "uniform", "fem", "sparse_rows", "dense64"])
+@pytest.mark.parametrize("c", [4, 8, 16])
+@pytest.mark.parametrize("lb", [0, 6])
+def test_two_lane_single_value_variant(cuda_device, name, c, lb):
+    # variant 33: two lanes per row, rows whose blocks all hold one value read
+    # like a two-lane CSR kernel (Algorithm 2's test); lane g still takes the
+    # values of rank g, g + 2, ..., so the bits equal variant 22's
+    A = get(name)
+    x = inputs.vec_uniform(A.m, seed=0)
+    y_ref, absy = oracle.csr_spmv_dot2(A, x)
+    for vdt, xdt in ((torch.float64, torch.float64), (torch.float32, torch.float32), (torch.bfloat16, torch.float32)):
+        d = dev_csr(A, vdt)
+        xd = torch.from_numpy(x).to(xdt).cuda()
+        M = spc5.convert(d.rowptr, d.colidx, d.values, A.n, A.m, 1, c, variant=22, long_blocks=lb)
+        ref = M.spmv(xd).clone()
+        M.set_variant(33)
+        buf, y = guarded(A.n, xdt)
+        M.spmv(xd, y)
+        assert torch.equal(y, ref), vdt
+        assert torch.isnan(buf[A.n:]).all()
+        if vdt == torch.float64:
+            check64(y.cpu().numpy(), y_ref, absy)
+            y0 = inputs.vec_uniform(A.n, seed=1)
+            yd = torch.from_numpy(y0.copy()).cuda()
+            M.spmv_acc(xd, yd)
+            assert np.all(np.abs(yd.cpu().numpy() - (y0 + y_ref)) <= TOL64 * (absy + np.abs(y0)) + 1e-300)
+        M.destroy()
+
+
 def test_single_value_class_needs_r1(cuda_device):
     A = get("rmat11")
     d = dev_csr(A)
-    for v in (30, 31):
+    for v in (30, 31, 33):
         with pytest.raises(spc5.Spc5Error) as ei:
             spc5.convert(d.rowptr, d.colidx, d.values, A.n, A.m, 2, 8, variant=v)
         assert ei.value.status == spc5.EUNSUPPORTED
@@ -431,7 +460,7 @@ def test_autotune_keeps_a_candidate_and_the_result(cuda_device, dtype):
     ref = M.spmv(xd).clone()
     y = torch.empty_like(ref)
     v, ms = M.autotune(xd, y, reps=3)
-    cands = ((5, 10, 13, 15) if dtype == torch.float64 else (5, 10, 13, 15, 16, 18, 32)) + (22, 23, 30)
+    cands = ((5, 10, 13, 15) if dtype == torch.float64 else (5, 10, 13, 15, 16, 18, 32)) + (22, 23, 30, 33)
     assert v in cands and ms > 0
     got = M.spmv(xd)
     if v < 20 or v == 30:

@@ -9,7 +9,7 @@ from paper_1801_01134_gb300 import inputs, spc5
 
 pytestmark = pytest.mark.gpu
 
-VALID_VARIANTS = {5, 10, 13, 15, 16, 18, 22, 23, 24, 30, 31, 32}
+VALID_VARIANTS = {5, 10, 13, 15, 16, 18, 22, 23, 24, 30, 31, 32, 33}
 
 
 def test_tune_choice_is_valid_correct_and_cached(cuda_device):
