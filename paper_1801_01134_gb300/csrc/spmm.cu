@@ -382,6 +382,112 @@ __global__ void k_spmm_fixup(int64_t n, int64_t nseg, int r, const Segment* __re
   if (row < n) Y[row * ldy + j] = s;
 }
 
+// Long intervals of beta(1,c) with column groups (k >= 8): a warp per
+// segment walks its blocks 32 at a time - lane t reads block t's mask and
+// column (consecutive over the warp) and a shuffle scan of the popcounts
+// places the blocks' values - and the warp's 32/G groups of G lanes then take
+// the trip's blocks in turn (group q: blocks q, q + 32/G, ...). Lane g of a
+// group owns the 4 columns j0 + 4 g .. + 3: per stored value it reads that
+// stretch of the X row (one 16-byte load when aligned), so a group reads a
+// whole row slice of 4 G values as one coalesced request, where one lane per
+// block run would read it as 4 G scalar or 16-byte pieces of its own. All
+// blocks belong to the segment's row: after the last trip an xor tree adds
+// the groups' sums, and group 0 writes the segment's partials. The order of
+// the sums depends only on the structure (results repeat bit for bit).
+template <class T, int G>
+__global__ void __launch_bounds__(256) k_spmm_seg_cols(int64_t nseg, int c, int mb, const Segment* __restrict__ segs,
+                                                       const int32_t* __restrict__ bcol,
+                                                       const uint8_t* __restrict__ bmask,
+                                                       const typename T::V* __restrict__ val,
+                                                       const typename T::X* __restrict__ X, int64_t ldx,
+                                                       typename T::A* __restrict__ part, int k, bool vec) {
+  using A = typename T::A;
+  constexpr int V = 4;
+  constexpr int NG = kWarp / G;  // groups per warp
+  const int lane = threadIdx.x & 31;
+  const int64_t seg = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (seg >= nseg) return;  // whole warp
+  const int grp = lane / G, gl = lane % G;
+  const int j = blockIdx.y * (G * V) + gl * V;
+  const int nv = k - j < V ? (k - j > 0 ? k - j : 0) : V;
+  const bool full = vec && nv == V;
+  const Segment sg = segs[seg];
+  int64_t vbase = sg.v_begin;
+  A acc[V];
+#pragma unroll
+  for (int q = 0; q < V; ++q) acc[q] = A(0);
+  for (int32_t b0 = sg.b_begin; b0 < sg.b_end; b0 += kWarp) {
+    const int32_t b = b0 + lane;
+    const bool valid = b < sg.b_end;
+    const uint32_t m = valid ? load_mask_rt(bmask, b, mb).w[0] : 0u;  // r = 1: c <= 16 bits
+    const int32_t col = valid ? __ldg(bcol + b) : 0;
+    const int cnt = __popc(m);
+    int incl = cnt;
+#pragma unroll
+    for (int d = 1; d < kWarp; d <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, d);
+      if (lane >= d) incl += t;
+    }
+    const int excl = incl - cnt;
+#pragma unroll 2
+    for (int q0 = 0; q0 < kWarp; q0 += NG) {
+      const int q = q0 + grp;
+      uint32_t mq = __shfl_sync(0xffffffffu, m, q);
+      const int64_t cq = __shfl_sync(0xffffffffu, col, q);
+      int64_t vo = vbase + __shfl_sync(0xffffffffu, excl, q);
+      while (mq) {
+        const int kb = __ffs(mq) - 1;
+        mq &= mq - 1;
+        const A v = T::val(val, vo++);
+        if (nv > 0) {
+          const XQuad<T, V> xq = load_xq<T, V>(X + (cq + kb) * ldx + j, nv, full);
+#pragma unroll
+          for (int t = 0; t < V; ++t) acc[t] = fma(v, xq.v[t], acc[t]);
+        }
+      }
+    }
+    vbase += __shfl_sync(0xffffffffu, incl, kWarp - 1);
+  }
+#pragma unroll
+  for (int t = 0; t < V; ++t)
+#pragma unroll
+    for (int d = G; d < kWarp; d <<= 1) acc[t] += __shfl_xor_sync(0xffffffffu, acc[t], d);
+  if (grp == 0) {
+#pragma unroll
+    for (int t = 0; t < V; ++t)
+      if (t < nv) part[seg * (int64_t)k + j + t] = acc[t];
+  }
+}
+
+// the long intervals' segments and fix-up; beta(1,c) with k >= 8 takes the
+// column groups above (G = 2, 4 or 8 lanes: 8, 16 or 32 columns per tile),
+// other shapes a lane per (block run, row) with KT columns
+template <class T, int KT>
+void spmm_long(const spc5_matrix* h, int k, const typename T::X* Xm, int64_t ldx, typename T::X* Ym, int64_t ldy,
+               typename T::A* part, cudaStream_t s) {
+  const typename T::V* val = static_cast<const typename T::V*>(h->values);
+  if (h->r == 1 && k >= 8) {
+    const bool vec = sizeof(typename T::X) == 4 && ldx % 4 == 0 && (reinterpret_cast<uintptr_t>(Xm) & 15u) == 0;
+    const unsigned gx = (unsigned)((h->nseg * kWarp + 255) / 256);
+    if (k >= 32) {
+      k_spmm_seg_cols<T, 8><<<dim3(gx, (unsigned)((k + 31) / 32)), 256, 0, s>>>(
+          h->nseg, h->c, h->mb, h->segs, h->block_colidx, h->block_masks, val, Xm, ldx, part, k, vec);
+    } else if (k >= 16) {
+      k_spmm_seg_cols<T, 4><<<dim3(gx, (unsigned)((k + 15) / 16)), 256, 0, s>>>(
+          h->nseg, h->c, h->mb, h->segs, h->block_colidx, h->block_masks, val, Xm, ldx, part, k, vec);
+    } else {
+      k_spmm_seg_cols<T, 2><<<dim3(gx, (unsigned)((k + 7) / 8)), 256, 0, s>>>(
+          h->nseg, h->c, h->mb, h->segs, h->block_colidx, h->block_masks, val, Xm, ldx, part, k, vec);
+    }
+  } else {
+    dim3 grid((unsigned)((h->nseg * kWarp + 255) / 256), (unsigned)((k + KT - 1) / KT));
+    k_spmm_segments<T, KT><<<grid, 256, 0, s>>>(h->nseg, h->r, h->c, h->mb, h->segs, h->block_colidx, h->block_masks,
+                                                val, Xm, ldx, part, k);
+  }
+  const int64_t nt = h->nseg * h->r * (int64_t)k;
+  k_spmm_fixup<T><<<(unsigned)((nt + 255) / 256), 256, 0, s>>>(h->n, h->nseg, h->r, h->segs, part, Ym, ldy, k);
+}
+
 template <class T, int KT>
 cudaError_t spmm_launch(const spc5_matrix* h, int k, const void* Xv, int64_t ldx, void* Yv, int64_t ldy, void* part,
                         cudaStream_t s) {
@@ -402,19 +508,12 @@ cudaError_t spmm_launch(const spc5_matrix* h, int k, const void* Xv, int64_t ldx
                                             h->block_rowptr, h->block_colidx, h->block_masks, val, h->valptr, Xm, ldx,
                                             Ym, ldy, k, vec);
   }
-  if (h->nseg > 0) {
-    dim3 grid((unsigned)((h->nseg * kWarp + 255) / 256), tiles);
-    k_spmm_segments<T, KT><<<grid, 256, 0, s>>>(h->nseg, h->r, h->c, h->mb, h->segs, h->block_colidx, h->block_masks,
-                                                val, Xm, ldx, static_cast<A*>(part), k);
-    const int64_t nt = h->nseg * h->r * (int64_t)k;
-    k_spmm_fixup<T><<<(unsigned)((nt + 255) / 256), 256, 0, s>>>(h->n, h->nseg, h->r, h->segs,
-                                                                 static_cast<const A*>(part), Ym, ldy, k);
-  }
+  if (h->nseg > 0) spmm_long<T, KT>(h, k, Xm, ldx, Ym, ldy, static_cast<A*>(part), s);
   return cudaGetLastError();
 }
 
-// ktile columns per interval for the short intervals; the long ones keep the
-// segment path with 8 columns per lane
+// ktile columns per interval for the short intervals; the long ones take
+// spmm_long
 template <class T, int G>
 cudaError_t spmm_launch_cols(const spc5_matrix* h, int k, const void* Xv, int64_t ldx, void* Yv, int64_t ldy,
                              void* part, cudaStream_t s) {
@@ -424,15 +523,7 @@ cudaError_t spmm_launch_cols(const spc5_matrix* h, int k, const void* Xv, int64_
   X* Ym = static_cast<X*>(Yv);
   const typename T::V* val = static_cast<const typename T::V*>(h->values);
   if (h->I > 0) launch_spmm_blk<T, G / 4>(h, k, Xm, ldx, Ym, ldy, s);
-  if (h->nseg > 0) {
-    constexpr int KT = 8;
-    dim3 grid((unsigned)((h->nseg * kWarp + 255) / 256), (unsigned)((k + KT - 1) / KT));
-    k_spmm_segments<T, KT><<<grid, 256, 0, s>>>(h->nseg, h->r, h->c, h->mb, h->segs, h->block_colidx, h->block_masks,
-                                                val, Xm, ldx, static_cast<A*>(part), k);
-    const int64_t nt = h->nseg * h->r * (int64_t)k;
-    k_spmm_fixup<T><<<(unsigned)((nt + 255) / 256), 256, 0, s>>>(h->n, h->nseg, h->r, h->segs,
-                                                                 static_cast<const A*>(part), Ym, ldy, k);
-  }
+  if (h->nseg > 0) spmm_long<T, 8>(h, k, Xm, ldx, Ym, ldy, static_cast<A*>(part), s);
   return cudaGetLastError();
 }
 

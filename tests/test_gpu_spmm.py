@@ -94,6 +94,48 @@ def test_spmm_row_tiles_vector_and_scalar_loads(cuda_device, dtype, ktile, pad):
     M.destroy()
 
 
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32, torch.bfloat16])
+@pytest.mark.parametrize("k", [8, 17, 32, 45])
+@pytest.mark.parametrize("pad", [0, 1])
+@pytest.mark.parametrize("ktile", [0, -32, 16])
+def test_spmm_long_rows_column_groups(cuda_device, dtype, k, pad, ktile):
+    # beta(1,c) long intervals with k >= 8 go to the column-group segment
+    # kernel (2, 4 or 8 lanes of 4 columns per stored value); most R-MAT rows
+    # are long here (long_blocks 2); aligned X rows (pad 0: 16-byte loads) and
+    # unaligned ones (pad 1: scalar loads), partial last tiles
+    A = get("rmat11")
+    vals = A.values if dtype == torch.float64 else (oracle.round_f32(A.values) if dtype == torch.float32
+                                                    else oracle.round_bf16(A.values))
+    Ar = inputs.CSR(A.n, A.m, A.rowptr, A.colidx, vals)
+    X = inputs.vec_uniform(A.m * k, seed=3).reshape(A.m, k)
+    xdt = torch.float64 if dtype == torch.float64 else torch.float32
+    if xdt == torch.float32:
+        X = oracle.round_f32(X)
+    Yref, S = oracle.csr_spmm_dot2(Ar, X)
+    d = spc5.upload_csr(Ar, dtype, "cuda")
+    M = spc5.convert(d.rowptr, d.colidx, d.values, A.n, A.m, 1, 4, long_blocks=2)
+    assert M.arrays().nsegments > 0
+    ld = k + pad if pad else ((k + 3) // 4) * 4
+    Xd = torch.zeros(A.m, ld, dtype=xdt, device="cuda")
+    Xd[:, :k] = torch.from_numpy(X).to(xdt)
+    Yd = torch.full((A.n, ld), float("nan"), dtype=xdt, device="cuda")
+    M.spmm(Xd[:, :k], Yd[:, :k], ktile=ktile)
+    Y = Yd.double().cpu().numpy()
+    if dtype == torch.float64:
+        assert np.all(np.abs(Y[:, :k] - Yref) <= 1e-13 * S)
+    else:
+        L = np.diff(A.rowptr).astype(np.float64)[:, None]
+        u = 2.0**-24
+        assert np.all(np.abs(Y[:, :k] - Yref) <= (L + 1) * u / (1 - (L + 1) * u) * S + 1e-45)
+    if ld > k:
+        assert np.isnan(Y[:, k:]).all()
+    # repeated products give the same bits
+    Y2 = torch.full_like(Yd, float("nan"))
+    M.spmm(Xd[:, :k], Y2[:, :k], ktile=ktile)
+    assert torch.equal(Y2[:, :k], Yd[:, :k])
+    M.destroy()
+
+
 def test_spmm_rejects_bad_arguments(cuda_device):
     A = get("uniform")
     d = spc5.upload_csr(A, torch.float32, "cuda")
