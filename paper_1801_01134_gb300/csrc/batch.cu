@@ -1,19 +1,21 @@
-// Batched SpMV: y_j = A_j x_j for many uneven matrices in one persistent,
-// graph-replayed launch.
+// Batched SpMV: y_j = A_j x_j for many uneven matrices in one graph launch.
 //
 // Many small products launched one by one leave the GPU idle between tiny
 // kernels. Here every short interval of every matrix belongs to a work item
 // of 32/r consecutive intervals (one warp's worth, lane per row as in the
-// single-matrix kernel); persistent warps take kGrab items at a time from a
-// global counter with one atomicAdd (no waiting on other warps), so uneven
-// matrices balance themselves. Each matrix keeps its own block shape and the
-// row decode of its tuned variant (both run-time arguments here, chosen per
-// matrix by spc5_tune or the caller's selector). Long
-// intervals are items of a second kind - one warp per segment, partials into
-// the matrix's scratch - followed by one fix-up kernel over the long
-// intervals.
-// The counter reset, the persistent kernel and the fix-up are captured once
-// into a CUDA graph at batch creation; a batched SpMV is one graph launch.
+// single-matrix kernel). The items are grouped by (block shape, row decode):
+// each matrix keeps its own shape and the decode of its tuned variant
+// (chosen per matrix by spc5_tune or the caller's selector), and each group
+// runs one kernel compiled for its shape and decode - one warp per item - so
+// no group pays for the registers another decode needs. Long intervals are
+// items of a second kind - one warp per segment, partials into the matrix's
+// scratch - taken by persistent warps from a global counter (kGrab items per
+// atomic), followed by one fix-up kernel over the long intervals. The group
+// kernels and the segment kernel run on parallel branches (side streams
+// joined by events); the whole product is captured once into a CUDA graph at
+// batch creation, so a batched SpMV is one graph launch.
+#include <algorithm>
+#include <map>
 #include <vector>
 
 #include "spmv_beta.cuh"
@@ -42,14 +44,21 @@ struct MatDesc {  // one matrix of the batch (device copy)
 // batch on 256 matrices of ~3 M rows in total
 constexpr int kGrab = 8;
 
-// The decode of a matrix's short intervals, from its variant: 1 mask
-// windows (also for the block-streaming variant 32, whose one-lane fallback
-// they are), 4 Algorithm 2's single-value test (r = 1: variants 30, 31 and
-// the two-lane 33) with the mask windows for the other rows, 0 the flattened
-// decode for every other variant (the batch maps one lane to one row).
-inline int decode_of(int v, int r) {
-  if (v == 12 || v == 13 || v == 14 || v == 15 || v == 32) return 1;
+// The decode of a matrix's short intervals, from its variant (the batch maps
+// one lane to one row): 1 mask windows, 4 Algorithm 2's single-value test
+// (r = 1: variants 30, 31 and the two-lane 33) with the mask windows for the
+// other rows, 2 / 3 the unrolled bit positions one / two blocks per trip
+// (variants 16/17, 18/19), 0 the flattened decode (variants 0-10).
+inline int decode_of(int v, int r, int c, spc5_dtype vt) {
+  if (v == 12 || v == 13 || v == 14 || v == 15) return 1;
   if ((v == 30 || v == 31 || v == 33) && r == 1) return 4;
+  const int unrolled = c <= 8 ? 3 : 2;  // row_sum_e2 holds two blocks of at most 8 positions
+  if (v == 16 || v == 17) return 2;
+  if (v == 18 || v == 19) return unrolled;
+  // the many-lane forms (two lanes per row, lanes per interval, the streaming
+  // warp): the unrolled one-lane decode for the 4-byte types, the mask
+  // windows for float64 (unrolled positions there cost float64 issue slots)
+  if (v == 22 || v == 23 || (v >= 24 && v <= 29) || v == 32) return vt == SPC5_F64 ? 1 : unrolled;
   return 0;
 }
 
@@ -138,6 +147,63 @@ __device__ __forceinline__ typename T::A batch_row_any(const MatDesc& d, int64_t
   SPC5_BCASE(8, 4) SPC5_BCASE(8, 8)
 #undef SPC5_BCASE
   return batch_row_dec<8, 16, T>(d, it, i, b, bend, v0);
+}
+
+// One group: items of matrices with block shape R x C and row decode DEC,
+// one warp per item (items[0 .. nitems) of this group).
+template <class T, int R, int C, int DEC>
+__global__ void __launch_bounds__(256) k_batch_rows(const MatDesc* __restrict__ mats, const Item* __restrict__ items,
+                                                    int64_t nitems) {
+  using X = typename T::X;
+  using A = typename T::A;
+  const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (w >= nitems) return;  // whole warp
+  const int lane = threadIdx.x & 31;
+  const Item itm = items[w];
+  const MatDesc& d = mats[itm.mat];
+  const int64_t it = (int64_t)itm.i0 + lane / R;
+  const int i = lane % R;
+  if (it >= d.I) return;
+  const int32_t b = __ldg(d.brp + it);
+  const int32_t bend = __ldg(d.brp + it + 1);
+  const int64_t v0 = __ldg(d.valptr + it);
+  if (bend - b > d.long_blocks || __ldg(d.valptr + it + 1) - v0 > d.long_values) return;  // the segment path's
+  const A acc = batch_row<R, C, T, DEC>(d, it, i, b, bend, v0);
+  const int64_t row = it * R + i;
+  if (row < d.n) static_cast<X*>(d.y)[row] = acc;
+}
+
+// launch of one group's kernel (shape and decode from the group's key)
+template <class T>
+cudaError_t launch_group(int r, int c, int dec, const MatDesc* mats, const Item* items, int64_t nitems,
+                         cudaStream_t s) {
+  if (nitems <= 0) return cudaSuccess;
+  const int threads = kSpmvThreads;
+  const unsigned grid = (unsigned)((nitems * kWarp + threads - 1) / threads);
+#define SPC5_GKERN(RR, CC, DD) k_batch_rows<T, RR, CC, DD><<<grid, threads, 0, s>>>(mats, items, nitems)
+#define SPC5_GSHAPE(RR, CC)                                     \
+  if (r == RR && c == CC) {                                     \
+    if (dec == 1) {                                             \
+      SPC5_GKERN(RR, CC, 1);                                    \
+    } else if (dec == 2 || (dec == 3 && CC > 8)) {              \
+      SPC5_GKERN(RR, CC, 2);                                    \
+    } else if (dec == 3) {                                      \
+      if constexpr (CC <= 8) SPC5_GKERN(RR, CC, 3);             \
+    } else if (dec == 4) {                                      \
+      if constexpr (RR == 1) SPC5_GKERN(RR, CC, 4);             \
+      else SPC5_GKERN(RR, CC, 0);                               \
+    } else {                                                    \
+      SPC5_GKERN(RR, CC, 0);                                    \
+    }                                                           \
+    return cudaGetLastError();                                  \
+  }
+  SPC5_GSHAPE(1, 4) SPC5_GSHAPE(1, 8) SPC5_GSHAPE(1, 16)
+  SPC5_GSHAPE(2, 4) SPC5_GSHAPE(2, 8) SPC5_GSHAPE(2, 16)
+  SPC5_GSHAPE(4, 4) SPC5_GSHAPE(4, 8) SPC5_GSHAPE(4, 16)
+  SPC5_GSHAPE(8, 4) SPC5_GSHAPE(8, 8) SPC5_GSHAPE(8, 16)
+#undef SPC5_GSHAPE
+#undef SPC5_GKERN
+  return cudaErrorInvalidValue;
 }
 
 template <class T>
@@ -245,14 +311,29 @@ __global__ void __launch_bounds__(256) k_batch_fixup(const MatDesc* __restrict__
 }  // namespace
 }  // namespace spc5
 
+namespace spc5 {
+namespace {
+constexpr int kSide = 4;  // side streams the group kernels are spread over
+struct Group {  // the items of one (block shape, decode): items_d[off .. off + cnt)
+  int r, c, dec;
+  int64_t off, cnt;
+};
+}  // namespace
+}  // namespace spc5
+
 struct spc5_batch_s {
   spc5_dtype vt = SPC5_F32;
   int count = 0;
   int64_t nitems = 0, nfirst = 0;
+  int64_t seg_off = 0, nseg_items = 0;  // the segment items: items_d[seg_off .. seg_off + nseg_items)
+  std::vector<spc5::Group> groups;
   spc5::MatDesc* mats_d = nullptr;
   spc5::Item* items_d = nullptr;
   int2* firsts_d = nullptr;  // (matrix, first segment) of every long interval
   unsigned long long* counter_d = nullptr;
+  cudaStream_t side[spc5::kSide] = {};
+  cudaEvent_t ev_fork = nullptr;
+  cudaEvent_t ev_join[spc5::kSide] = {};
   cudaGraphExec_t exec = nullptr;
   int blocks = 0;
 };
@@ -262,6 +343,11 @@ namespace spc5 {
 static void batch_free(spc5_batch_s* b) {
   if (!b) return;
   if (b->exec) cudaGraphExecDestroy(b->exec);
+  for (int q = 0; q < kSide; ++q) {
+    if (b->side[q]) cudaStreamDestroy(b->side[q]);
+    if (b->ev_join[q]) cudaEventDestroy(b->ev_join[q]);
+  }
+  if (b->ev_fork) cudaEventDestroy(b->ev_fork);
   cudaFree(b->mats_d);
   cudaFree(b->items_d);
   cudaFree(b->firsts_d);
@@ -269,14 +355,28 @@ static void batch_free(spc5_batch_s* b) {
   delete b;
 }
 
+// the segments (persistent kernel, then the fix-up) on s, the groups on the
+// side streams, forked from and joined back into s
 template <class T>
 cudaError_t batch_enqueue(spc5_batch_s* b, cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(b->counter_d, 0, sizeof(unsigned long long), s);
+  cudaError_t e = cudaEventRecord(b->ev_fork, s);
+  for (int q = 0; q < kSide && e == cudaSuccess; ++q) e = cudaStreamWaitEvent(b->side[q], b->ev_fork, 0);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->counter_d, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
-  if (b->nitems > 0) k_batch<T><<<b->blocks, 256, 0, s>>>(b->mats_d, b->items_d, b->nitems, b->counter_d);
+  if (b->nseg_items > 0)
+    k_batch<T><<<b->blocks, 256, 0, s>>>(b->mats_d, b->items_d + b->seg_off, b->nseg_items, b->counter_d);
   if (b->nfirst > 0)
     k_batch_fixup<T><<<(unsigned)((b->nfirst + 255) / 256), 256, 0, s>>>(b->mats_d, b->firsts_d, b->nfirst);
-  return cudaGetLastError();
+  e = cudaGetLastError();
+  for (size_t g = 0; g < b->groups.size() && e == cudaSuccess; ++g) {
+    const Group& gr = b->groups[g];
+    e = launch_group<T>(gr.r, gr.c, gr.dec, b->mats_d, b->items_d + gr.off, gr.cnt, b->side[g % kSide]);
+  }
+  for (int q = 0; q < kSide && e == cudaSuccess; ++q) {
+    e = cudaEventRecord(b->ev_join[q], b->side[q]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b->ev_join[q], 0);
+  }
+  return e;
 }
 
 cudaError_t batch_enqueue_any(spc5_batch_s* b, cudaStream_t s) {
@@ -293,7 +393,8 @@ spc5_status batch_create_impl(const spc5_handle* mats, const void* const* xs, vo
   b->count = count;
   b->vt = mats[0]->vt;
   std::vector<MatDesc> md((size_t)count);
-  std::vector<Item> items;
+  std::vector<Item> items, seg_items;
+  std::map<int, std::vector<Item>> by_key;  // (r, c, decode) -> short-interval items
   std::vector<int2> firsts;
   std::vector<Segment> hsegs;
   for (int j = 0; j < count; ++j) {
@@ -321,10 +422,11 @@ spc5_status batch_create_impl(const spc5_handle* mats, const void* const* xs, vo
     d.mb = h->mb;
     d.long_blocks = h->long_blocks;
     d.log2r = h->r == 1 ? 0 : h->r == 2 ? 1 : h->r == 4 ? 2 : 3;
-    d.dec = decode_of(h->variant, h->r);
+    d.dec = decode_of(h->variant, h->r, h->c, h->vt);
     d.single = d.dec == 4 ? h->single_bits : nullptr;
     const int S = kWarp / h->r;
-    for (int64_t i0 = 0; i0 < h->I; i0 += S) items.push_back(Item{j, (int32_t)i0, 0, 0});
+    auto& list = by_key[(h->r * 32 + h->c) * 8 + d.dec];
+    for (int64_t i0 = 0; i0 < h->I; i0 += S) list.push_back(Item{j, (int32_t)i0, 0, 0});
     if (h->nseg > 0) {
       hsegs.resize((size_t)h->nseg);
       cudaError_t e = cudaMemcpy(hsegs.data(), h->segs, sizeof(Segment) * (size_t)h->nseg, cudaMemcpyDeviceToHost);
@@ -333,10 +435,23 @@ spc5_status batch_create_impl(const spc5_handle* mats, const void* const* xs, vo
         return cuda_fail(e, "batch: segment table");
       }
     }
-    for (int64_t q = 0; q < h->nseg; ++q) items.push_back(Item{j, (int32_t)q, 1, 0});
+    for (int64_t q = 0; q < h->nseg; ++q) seg_items.push_back(Item{j, (int32_t)q, 1, 0});
     for (int64_t q = 0; q < h->nseg; ++q)
       if (hsegs[(size_t)q].count > 0) firsts.push_back(make_int2(j, (int)q));
   }
+  // groups, largest first (the side streams start on the big ones), then the segments
+  std::vector<std::pair<int, std::vector<Item>*>> keys;
+  for (auto& kv : by_key) keys.push_back({kv.first, &kv.second});
+  std::stable_sort(keys.begin(), keys.end(),
+                   [](const auto& a, const auto& c) { return a.second->size() > c.second->size(); });
+  for (auto& kv : keys) {
+    const int key = kv.first;
+    b->groups.push_back(Group{key / 256, (key / 8) % 32, key % 8, (int64_t)items.size(), (int64_t)kv.second->size()});
+    items.insert(items.end(), kv.second->begin(), kv.second->end());
+  }
+  b->seg_off = (int64_t)items.size();
+  b->nseg_items = (int64_t)seg_items.size();
+  items.insert(items.end(), seg_items.begin(), seg_items.end());
   b->nitems = (int64_t)items.size();
   b->nfirst = (int64_t)firsts.size();
   cudaError_t e = cudaMalloc((void**)&b->mats_d, sizeof(MatDesc) * (size_t)count);
@@ -365,9 +480,18 @@ spc5_status batch_create_impl(const spc5_handle* mats, const void* const* xs, vo
     if (oe == cudaSuccess && v > 0) per_sm = v;
   }
   int64_t blocks = (int64_t)sm_count() * per_sm;
-  const int64_t need = (b->nitems + 8 * kGrab - 1) / (8 * kGrab);
+  const int64_t need = (b->nseg_items + 8 * kGrab - 1) / (8 * kGrab);
   if (blocks > need) blocks = need > 0 ? need : 1;
   b->blocks = (int)blocks;
+  for (int q = 0; q < kSide && e == cudaSuccess; ++q) {
+    e = cudaStreamCreateWithFlags(&b->side[q], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_join[q], cudaEventDisableTiming);
+  }
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    batch_free(b);
+    return cuda_fail(e, "batch: streams");
+  }
   // capture the whole batched product once; replays reuse it
   cudaStream_t cs = nullptr;
   cudaGraph_t g = nullptr;

@@ -77,11 +77,12 @@ def test_batch_rejects_mixed_types(cuda_device):
 
 
 def test_batch_keeps_each_matrix_decode_bitwise(cuda_device):
-    # per-matrix tuned variants: the batch uses the matrix's mask-window or
-    # single-value decode, which add in storage order like the single product
+    # per-matrix tuned variants: the batch groups the matrices by shape and
+    # decode and runs each with its mask-window, single-value, unrolled or
+    # flattened decode, which add in storage order like the single product
     As, mats, hs, xs, ys = build(36, torch.float32, seed=7)
     for j, M in enumerate(mats):
-        choices = (13, 15, 30, 31, 12, 5) if M.r == 1 else (12, 13, 15, 5)
+        choices = (13, 15, 30, 31, 12, 5, 16, 18) if M.r == 1 else (12, 13, 15, 5)
         M.set_variant(choices[j % len(choices)])
     B = spc5.Batch(mats, xs, ys)
     B.run()
