@@ -395,7 +395,8 @@ def run_spmm_section(mats, dev, ks=(1, 4, 8, 16, 32), reps: int = 5):
         res = {}
         for k in ks:
             tn = spc5.tune(d, k_spmm=k, reps=3)
-            M = spc5.convert(d.rowptr, d.colidx, d.values, A.n, A.m, tn["spmm_r"], tn["spmm_c"])
+            M = spc5.convert(d.rowptr, d.colidx, d.values, A.n, A.m, tn["spmm_r"], tn["spmm_c"],
+                             variant=tn["spmm_variant"])
             X = torch.rand(A.m, k, dtype=torch.float32, device=dev)
             Y = torch.empty(A.n, k, dtype=torch.float32, device=dev)
             t = timed(lambda: M.spmm(X, Y, ktile=tn["ktile"]))

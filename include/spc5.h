@@ -372,9 +372,13 @@ spc5_status spc5_copy(const void* src_d, void* dst_d, int64_t bytes, spc5_stream
  *         (ktile / 4 lanes per row interval, 4 columns each: the X rows a
  *         block's columns need are read once and applied to all r rows of
  *         the block); 0 = choose from k. The grid covers ceil(k / |ktile|)
- *         tiles.
- * A handle with long intervals keeps n_segments * r * k partial sums; the first
- * call with a larger k grows that buffer (cudaMalloc, device synchronisation).
+ *         tiles. k = 1 with ldx = ldy = 1 and ktile 0 or 1 is the SpMV
+ *         (spc5_spmv, the handle's variant).
+ * Long intervals of beta(1,c) with k >= 4: a warp per segment, groups of 1, 2,
+ * 4 or 8 lanes taking its blocks in turn, 4 columns per lane (one coalesced
+ * X row slice per stored value and group). A handle with long intervals keeps
+ * n_segments * r * k partial sums; the first call with a larger k grows that
+ * buffer (cudaMalloc, device synchronisation).
  */
 spc5_status spc5_spmm(spc5_handle h, int k, const void* X_d, int64_t ldx, void* Y_d, int64_t ldy, int ktile,
                       spc5_stream_t stream);
@@ -407,6 +411,7 @@ typedef struct {
   int32_t spmm_r, spmm_c, ktile; /* SpMM (k_spmm > 0): fastest shape and column tile */
   float spmm_ms;      /* SpMM: its median milliseconds (-1 when k_spmm == 0) */
   int32_t from_cache; /* 1 when the result came from the signature cache */
+  int32_t spmm_variant; /* SpMM: the fastest SpMV variant on the SpMM shape (k = 1 runs the SpMV) */
   uint64_t signature; /* the matrix signature the cache is keyed on */
 } spc5_tune_result;
 

@@ -335,6 +335,9 @@ spc5_status spc5_spmm(spc5_handle h, int k, const void* X_d, int64_t ldx, void* 
         ktile == 16 || ktile == 32))
     return fail(SPC5_EINVAL, "spmm: ktile must be 0, 1, 4, -8, -16, -32, 8, 16 or 32");
   if ((h->m > 0 && !X_d) || (h->n > 0 && !Y_d)) return fail(SPC5_EINVAL, "spmm: NULL matrix");
+  // one right-hand side stored as a vector: the SpMV with the handle's variant
+  if (k == 1 && ldx == 1 && ldy == 1 && (ktile == 0 || ktile == 1))
+    return spmv_common(h, X_d, Y_d, false, (cudaStream_t)stream);
   return spmm_impl(h, k, X_d, ldx, Y_d, ldy, ktile, (cudaStream_t)stream);
 }
 

@@ -382,7 +382,7 @@ __global__ void k_spmm_fixup(int64_t n, int64_t nseg, int r, const Segment* __re
   if (row < n) Y[row * ldy + j] = s;
 }
 
-// Long intervals of beta(1,c) with column groups (k >= 8): a warp per
+// Long intervals of beta(1,c) with column groups (k >= 4): a warp per
 // segment walks its blocks 32 at a time - lane t reads block t's mask and
 // column (consecutive over the warp) and a shuffle scan of the popcounts
 // places the blocks' values - and the warp's 32/G groups of G lanes then take
@@ -459,17 +459,20 @@ __global__ void __launch_bounds__(256) k_spmm_seg_cols(int64_t nseg, int c, int 
   }
 }
 
-// the long intervals' segments and fix-up; beta(1,c) with k >= 8 takes the
-// column groups above (G = 2, 4 or 8 lanes: 8, 16 or 32 columns per tile),
-// other shapes a lane per (block run, row) with KT columns
+// the long intervals' segments and fix-up; beta(1,c) with k >= 4 takes the
+// column groups above (G = 1, 2, 4 or 8 lanes: 4, 8, 16 or 32 columns per
+// tile), other shapes a lane per (block run, row) with KT columns
 template <class T, int KT>
 void spmm_long(const spc5_matrix* h, int k, const typename T::X* Xm, int64_t ldx, typename T::X* Ym, int64_t ldy,
                typename T::A* part, cudaStream_t s) {
   const typename T::V* val = static_cast<const typename T::V*>(h->values);
-  if (h->r == 1 && k >= 8) {
+  if (h->r == 1 && k >= 4) {
     const bool vec = sizeof(typename T::X) == 4 && ldx % 4 == 0 && (reinterpret_cast<uintptr_t>(Xm) & 15u) == 0;
     const unsigned gx = (unsigned)((h->nseg * kWarp + 255) / 256);
-    if (k >= 32) {
+    if (k < 8) {
+      k_spmm_seg_cols<T, 1><<<dim3(gx, (unsigned)((k + 3) / 4)), 256, 0, s>>>(
+          h->nseg, h->c, h->mb, h->segs, h->block_colidx, h->block_masks, val, Xm, ldx, part, k, vec);
+    } else if (k >= 32) {
       k_spmm_seg_cols<T, 8><<<dim3(gx, (unsigned)((k + 31) / 32)), 256, 0, s>>>(
           h->nseg, h->c, h->mb, h->segs, h->block_colidx, h->block_masks, val, Xm, ldx, part, k, vec);
     } else if (k >= 16) {

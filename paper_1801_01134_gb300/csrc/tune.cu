@@ -158,11 +158,17 @@ spc5_status tune_impl(int64_t n, int64_t m, int64_t nnz, const int64_t* rowptr, 
     spc5_handle h = nullptr;
     st = spc5_convert(n, m, nnz, rowptr, colidx, values, vt, r, c, nullptr, (spc5_stream_t)s, &h);
     if (st != SPC5_OK) break;
+    int shape_v = 0;  // fastest variant on this shape
+    float shape_ms = -1.f;
     for (int v : tune_candidates(vt, r)) {
       st = spc5_set_variant(h, v, (spc5_stream_t)s);
       float ms = 0.f;
       if (st == SPC5_OK) st = tm.median([&] { return spc5_spmv(h, x, y, (spc5_stream_t)s); }, reps, &ms);
       if (st != SPC5_OK) break;
+      if (shape_ms < 0.f || ms < shape_ms) {
+        shape_ms = ms;
+        shape_v = v;
+      }
       if (best.spmv_ms < 0.f || ms < best.spmv_ms) {
         best.spmv_ms = ms;
         best.r = r;
@@ -170,6 +176,8 @@ spc5_status tune_impl(int64_t n, int64_t m, int64_t nnz, const int64_t* rowptr, 
         best.variant = v;
       }
     }
+    // the SpMM of one vector runs the SpMV: with this shape's fastest variant
+    if (st == SPC5_OK && k > 0) st = spc5_set_variant(h, shape_v, (spc5_stream_t)s);
     if (st == SPC5_OK && k > 0) {
       for (int t : tiles) {
         const int at = t < 0 ? -t : t;
@@ -182,6 +190,7 @@ spc5_status tune_impl(int64_t n, int64_t m, int64_t nnz, const int64_t* rowptr, 
           best.spmm_r = r;
           best.spmm_c = c;
           best.ktile = t;
+          best.spmm_variant = shape_v;
         }
       }
     }

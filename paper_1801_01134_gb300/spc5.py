@@ -60,7 +60,8 @@ class Selector(ctypes.Structure):
 class TuneResult(ctypes.Structure):
     _fields_ = [("r", ctypes.c_int32), ("c", ctypes.c_int32), ("variant", ctypes.c_int32), ("spmv_ms", ctypes.c_float),
                 ("spmm_r", ctypes.c_int32), ("spmm_c", ctypes.c_int32), ("ktile", ctypes.c_int32),
-                ("spmm_ms", ctypes.c_float), ("from_cache", ctypes.c_int32), ("signature", ctypes.c_uint64)]
+                ("spmm_ms", ctypes.c_float), ("from_cache", ctypes.c_int32), ("spmm_variant", ctypes.c_int32),
+                ("signature", ctypes.c_uint64)]
 
 
 TUNE_NO_CACHE = 1

@@ -50,7 +50,8 @@ def test_tune_spmm_tile(cuda_device, k):
     t = spc5.tune(d, k_spmm=k, reps=2)
     assert t["spmm_ms"] > 0 and (t["spmm_r"], t["spmm_c"]) in spc5.SHAPES
     assert t["ktile"] in ((1,) if k == 1 else (4, -8, -16, -32, 8, 16, 32)) and abs(t["ktile"]) <= 2 * k
-    M = spc5.convert(d.rowptr, d.colidx, d.values, A.n, A.m, t["spmm_r"], t["spmm_c"])
+    assert t["spmm_variant"] in VALID_VARIANTS
+    M = spc5.convert(d.rowptr, d.colidx, d.values, A.n, A.m, t["spmm_r"], t["spmm_c"], variant=t["spmm_variant"])
     X = oracle.round_f32(inputs.vec_uniform(A.m * k, seed=1).reshape(A.m, k))
     Y = M.spmm(torch.from_numpy(X).float().cuda(), ktile=t["ktile"]).double().cpu().numpy()
     Yref, S = oracle.csr_spmm_dot2(A, X)
