@@ -369,9 +369,9 @@ spc5_status spc5_copy(const void* src_d, void* dst_d, int64_t bytes, spc5_stream
  *   k     1..1024; ktile = column tile: 1, 4, -8, -16 or -32 (one lane per
  *         row holding 1 to 32 columns; X rows read as 16-byte vectors when
  *         X_d is 16-byte aligned and ldx a multiple of 16 bytes), 8, 16 or 32
- *         (ktile / 4 lanes per row interval, 4 columns each: the X rows a
- *         block's columns need are read once and applied to all r rows of
- *         the block); 0 = choose from k. The grid covers ceil(k / |ktile|)
+ *         (ktile / 4 lanes per row interval, 4 columns each: per stored value
+ *         the group reads one coalesced ktile-wide slice of its X row); 0 =
+ *         choose from k. The grid covers ceil(k / |ktile|)
  *         tiles. k = 1 with ldx = ldy = 1 and ktile 0 or 1 is the SpMV
  *         (spc5_spmv, the handle's variant).
  * Long intervals of beta(1,c) with k >= 4: a warp per segment, groups of 1, 2,

@@ -9,16 +9,18 @@
 //   ktile 1, 4, -8, -16, -32   one lane per row keeps 1 to 32 accumulators
 //                  and, per nonzero, reads one matrix value and that wide a
 //                  slice of an X row (16-byte loads when X rows are aligned);
-//   ktile 8/16/32  ktile / 4 lanes per interval, 4 columns each: the X rows
-//                  a block needs are read once (coalesced) and applied to all
-//                  of the block's rows (for large k, where X dominates).
+//   ktile 8/16/32  ktile / 4 lanes per interval, 4 columns each: per stored
+//                  value the group reads one coalesced ktile-wide slice of
+//                  its X row (for large k, where X dominates).
 // The grid's y dimension covers the column tiles. Long intervals go through
 // warp segments and a fix-up, as in the SpMV, with per-row partials per
-// segment and column.
+// segment and column (beta(1,c) with k >= 4: column groups, see
+// k_spmm_seg_cols).
 //
-// The block shape is a run-time argument here (not a template one): the
-// decode is amortised over k multiply-adds per nonzero, and it keeps the
-// number of kernel instantiations small.
+// The one-lane-per-row and segment kernels take the block shape at run time
+// (the decode is amortised over k multiply-adds per nonzero, and it keeps the
+// number of kernel instantiations small); the column-group kernel of the short
+// intervals is compiled per shape.
 #include "spmv_beta.cuh"
 
 namespace spc5 {
@@ -159,16 +161,17 @@ __global__ void __launch_bounds__(256) k_spmm_rows(int64_t n, int64_t I, int r, 
 
 // short intervals, G lanes per interval (ktile 8 / 16 / 32, G = ktile / 4):
 // lane g of a group owns the 4 columns j = tile * ktile + 4 g .. + 3 of X and
-// Y and keeps the interval's R row sums for each. Per block the group reads
-// the rows of X that the block's nonzero columns need once - 4 values per
-// lane (one 16-byte load when X rows are aligned), a coalesced stretch of
-// ktile values per group - and applies them to every row of the block, so X
-// moves (columns used per block) x ktile values instead of (nonzeros) x
-// ktile; the mask, the column index and each value are one address for the
-// whole group (broadcast loads), and each decoded value feeds 4 multiply-adds.
-// Two blocks per trip for small blocks (one for large ones), the next
-// trip's masks and columns read one trip ahead. No lane talks to another. Each (row, column) sum adds the row's products in
-// storage order, as the SpMV does.
+// Y and keeps the interval's R row sums for each. The group walks the
+// interval's blocks and each block row's set bits one by one: per stored
+// value one value read (one address for the whole group), the 4-column slice
+// of the X row of its column (one 16-byte load when X rows are aligned; the
+// group's slices form one coalesced stretch of ktile values) and 4
+// multiply-adds; the next block's mask and column are read one block ahead.
+// No lane talks to another. Each (row, column) sum adds the row's products in
+// storage order, as the SpMV does. (Measured on GB300: unrolling every bit
+// position of a block and reading the X rows of its columns once for all its
+// rows issued six times the instructions of the multiply-adds and ran 1.3 to
+// 1.5x slower: 27-point stencil 128^3, k = 32 0.74 -> 0.56 ms.)
 template <class T, int V>
 struct XQuad {
   typename T::A v[V];
@@ -194,15 +197,15 @@ __device__ __forceinline__ XQuad<T, V> load_xq(const typename T::X* __restrict__
 
 template <class T, int R, int C, int G>
 __global__ void __launch_bounds__(256) k_spmm_blk(int64_t n, int64_t I, int32_t long_blocks, int64_t long_values,
-                                                  const int32_t* __restrict__ brp, const int32_t* __restrict__ bcol,
-                                                  const uint8_t* __restrict__ bmask,
-                                                  const typename T::V* __restrict__ val,
-                                                  const int64_t* __restrict__ valptr,
-                                                  const typename T::X* __restrict__ X, int64_t ldx,
-                                                  typename T::X* __restrict__ Y, int64_t ldy, int k, bool vec) {
+                                                   const int32_t* __restrict__ brp, const int32_t* __restrict__ bcol,
+                                                   const uint8_t* __restrict__ bmask,
+                                                   const typename T::V* __restrict__ val,
+                                                   const int64_t* __restrict__ valptr,
+                                                   const typename T::X* __restrict__ X, int64_t ldx,
+                                                   typename T::X* __restrict__ Y, int64_t ldy, int k, bool vec) {
   using A = typename T::A;
   constexpr int MB = (R * C + 7) / 8;
-  constexpr int V = 4;  // columns per lane
+  constexpr int V = 4;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t it = t / G;
   const int j = blockIdx.y * (G * V) + (int)(t % G) * V;
@@ -220,60 +223,27 @@ __global__ void __launch_bounds__(256) k_spmm_blk(int64_t n, int64_t I, int32_t 
   for (int i = 0; i < R; ++i)
 #pragma unroll
     for (int q = 0; q < V; ++q) acc[i][q] = A(0);
-  int32_t vo = 0;  // first value of block b inside the interval
+  int32_t vv = 0;
   Mask<MB> m0 = b < bend ? load_mask<MB>(bmask, b) : zero_mask<MB>();
-  Mask<MB> m1 = b + 1 < bend ? load_mask<MB>(bmask, b + 1) : zero_mask<MB>();
-  int64_t c0 = b < bend ? __ldg(bcol + b) : 0, c1 = b + 1 < bend ? __ldg(bcol + b + 1) : 0;
-  // two blocks per trip while their X rows fit in registers, one otherwise
-  constexpr int NB = R * C * V * sizeof(A) <= 256 ? 2 : 1;
-  if (NB == 1) m1 = zero_mask<MB>();
-  for (; b < bend; b += NB) {
-    const Mask<MB> mk[2] = {m0, m1};
-    const int64_t cl[2] = {c0, c1};
-    if (NB == 1) {
-      if (b + 1 < bend) {
-        m0 = load_mask<MB>(bmask, b + 1);
-        c0 = __ldg(bcol + b + 1);
-      }
-    } else {
-      if (b + 2 < bend) {
-        m0 = load_mask<MB>(bmask, b + 2);
-        c0 = __ldg(bcol + b + 2);
-      }
-      if (b + 3 < bend) {
-        m1 = load_mask<MB>(bmask, b + 3);
-        c1 = __ldg(bcol + b + 3);
-      } else {  // the next pair has no second block
-        m1 = zero_mask<MB>();
-        c1 = 0;
-      }
-    }
-    XQuad<T, V> xr[NB][C];
-#pragma unroll
-    for (int h = 0; h < NB; ++h) {
-      uint32_t used = 0;  // zero for a second block past the interval
-#pragma unroll
-      for (int i = 0; i < R; ++i) used |= row_bits<C>(mk[h], i);
-#pragma unroll
-      for (int kk = 0; kk < C; ++kk)
-        xr[h][kk] = (used >> kk) & 1u ? load_xq<T, V>(xcol + (cl[h] + kk) * ldx, nv, full) : XQuad<T, V>{};
+  int64_t c0 = b < bend ? __ldg(bcol + b) : 0;
+  for (; b < bend; ++b) {
+    const Mask<MB> mk = m0;
+    const typename T::X* __restrict__ xb = xcol + c0 * ldx;
+    if (b + 1 < bend) {
+      m0 = load_mask<MB>(bmask, b + 1);
+      c0 = __ldg(bcol + b + 1);
     }
 #pragma unroll
-    for (int h = 0; h < NB; ++h) {
+    for (int i = 0; i < R; ++i) {
+      uint32_t bits = row_bits<C>(mk, i);
+      while (bits) {
+        const int kk = __ffs(bits) - 1;
+        bits &= bits - 1;
+        const A v = T::val(vrow, vv++);
+        const XQuad<T, V> xq = load_xq<T, V>(xb + kk * ldx, nv, full);
 #pragma unroll
-      for (int i = 0; i < R; ++i) {
-        const uint32_t rb = row_bits<C>(mk[h], i);
-        int32_t vv = vo + popc_below<C>(mk[h], i);
-#pragma unroll
-        for (int kk = 0; kk < C; ++kk)
-          if ((rb >> kk) & 1u) {
-            const A v = T::val(vrow, vv);
-#pragma unroll
-            for (int q = 0; q < V; ++q) acc[i][q] = fma(v, xr[h][kk].v[q], acc[i][q]);
-            ++vv;
-          }
+        for (int q = 0; q < V; ++q) acc[i][q] = fma(v, xq.v[q], acc[i][q]);
       }
-      vo += popc_all(mk[h]);
     }
   }
 #pragma unroll
