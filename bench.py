@@ -301,14 +301,23 @@ def measured_hbm_peak():
 
 def spmv_kernel_names(p):
     """The kernels one product of a prepared matrix launches (names as ncu lists them)."""
-    if p["variant"] == 22:
-        rows = "k_spmv_rows_g"
-    elif p["variant"] == 1:
-        rows = "k_spmv_rows"
+    v, fused = p["variant"], p["nseg"] > 0 and p["variant"] != 1
+    if v in (22, 23):
+        rows, both = "k_spmv_rows_g", "k_spmv_rows_segs"
+    elif v == 33:
+        rows, both = "k_spmv_rows_g1", "k_spmv_g1_segs"
+    elif v in (30, 31):
+        rows, both = "k_spmv_rows_t", "k_spmv_t_segs"
+    elif v == 32:
+        rows, both = "k_spmv_s", "k_spmv_s_segs"
+    elif 24 <= v <= 29:
+        rows, both = "k_spmv_grp", "k_spmv_grp_segs"
+    elif v == 1:
+        rows, both = "k_spmv_rows", None
     else:
-        rows = "k_spmv_rows_u"
+        rows, both = "k_spmv_rows_u", "k_spmv_rows_segs"
     if p["nseg"] > 0:
-        return ("k_spmv_rows_segs" if p["variant"] != 1 else f"{rows}+k_spmv_segments") + "+k_spmv_fixup"
+        return (both if fused else f"{rows}+k_spmv_segments") + "+k_spmv_fixup"
     return rows
 
 
