@@ -447,14 +447,20 @@ typedef struct spc5_batch_s* spc5_batch; /* opaque batched product */
 
 /*
  * spc5_batch_create - prepare y_j = A_j x_j for `count` handles of one value
- * type (each with its own block shape) as one persistent launch: the short
- * intervals of all matrices are cut into work items of 32/r intervals (the
- * long ones into their warp segments) that persistent warps take from a
- * shared counter, so uneven matrices balance themselves. x_d[j] / y_d[j]:
- * device vectors of matrix j (fixed for the batch's lifetime; refill them in
- * place between products). The counter reset, the kernel and the segment
- * fix-up are captured into a CUDA graph here. The handles must outlive the
- * batch. Synchronises the device.
+ * type (each with its own block shape and variant) as one graph launch: the
+ * short intervals of all matrices are cut into work items of 32/r intervals,
+ * grouped by (block shape, row decode of the matrix's variant), one kernel per
+ * group compiled for it (one warp per item); the long intervals become warp
+ * segments that persistent warps take from a shared counter, then a fix-up.
+ * The groups run on side streams beside the segments. The row decode: mask
+ * windows (variants 12-15), Algorithm 2's test (30, 31, 33), unrolled bit
+ * positions (16-19), flattened (0-10); the many-lane variants (22-29, 32) take
+ * the unrolled decode for float32 / bfloat16 and the mask windows for float64.
+ * A matrix whose decode sums in storage order gives the bits of its single
+ * product. x_d[j] / y_d[j]: device vectors of matrix j (fixed for the batch's
+ * lifetime; refill them in place between products). Everything is captured
+ * into a CUDA graph here. The handles must outlive the batch. Synchronises
+ * the device.
  */
 spc5_status spc5_batch_create(const spc5_handle* mats, const void* const* x_d, void* const* y_d, int count,
                               spc5_batch* out);
