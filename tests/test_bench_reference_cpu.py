@@ -68,3 +68,23 @@ def test_clock_samples_and_the_slowdown_rule():
     s = cs.summary()
     assert "hw_thermal_slowdown" in s["reasons"] and bench.throttled(s)  # measured again
     assert not bench.throttled(bench.ClockSampler(0).summary())  # no samples at all
+
+
+def test_bench_byte_counts_and_kernel_names():
+    # the roofline's algorithmic bytes (values, column indices, masks, the two
+    # interval arrays, x once, y) and the kernel names it reports per variant
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_1801_01134_gb300 import inputs
+
+    A = inputs.laplacian2d(10, 10)
+    p = {"A": A, "r": 2, "c": 8, "nblocks": 37}
+    I = (A.n + 1) // 2
+    assert bench.beta_bytes(p, 8, 8) == 8 * A.nnz + (4 + 2) * 37 + 12 * (I + 1) + 8 * A.m + 8 * A.n
+    assert bench.beta_bytes(p, 2, 4) == 2 * A.nnz + (4 + 2) * 37 + 12 * (I + 1) + 4 * A.m + 4 * A.n
+    assert bench.csr_bytes(p, 4, 4) == 4 * A.nnz + 4 * A.nnz + 8 * (A.n + 1) + 4 * A.m + 4 * A.n
+    names = {v: bench.spmv_kernel_names({"variant": v, "nseg": 0}) for v in (1, 5, 18, 22, 23, 25, 30, 32, 33)}
+    assert names == {1: "k_spmv_rows", 5: "k_spmv_rows_u", 18: "k_spmv_rows_u", 22: "k_spmv_rows_g",
+                     23: "k_spmv_rows_g", 25: "k_spmv_grp", 30: "k_spmv_rows_t", 32: "k_spmv_s", 33: "k_spmv_rows_g1"}
+    assert bench.spmv_kernel_names({"variant": 30, "nseg": 3}) == "k_spmv_t_segs+k_spmv_fixup"
+    assert bench.spmv_kernel_names({"variant": 1, "nseg": 3}) == "k_spmv_rows+k_spmv_segments+k_spmv_fixup"
