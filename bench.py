@@ -59,6 +59,8 @@ def parse():
     p.add_argument("--shape", default="4x8", help="block shape of the profiling run, e.g. 4x8, or csr")
     p.add_argument("--dtype", default="f64", choices=["f64", "f32", "bf16"], help="profiling run value type")
     p.add_argument("--reps", type=int, default=3)
+    p.add_argument("--spmm-k", type=int, default=0, help="profiling run: time Y = A X with this many columns (float32)")
+    p.add_argument("--ktile", type=int, default=0, help="profiling run: SpMM column tile (0 = from k)")
     p.add_argument("--variants", default="0", help="profiling run: comma list of kernel variants (0 = default)")
     p.add_argument("--order-window", type=int, default=0, help="profiling run: rows per work-order window "
                    "(0 = library default, negative = one window)")
@@ -660,6 +662,11 @@ def run_profile(args):
                 ar = M.arrays()
                 fmt = (f"beta({r},{c}) variant={variant} nblocks={ar.nblocks} segments={ar.nsegments}"
                        f" order_window={args.order_window} seg_blocks={args.seg_blocks} long_blocks={args.long_blocks}")
+                if args.spmm_k > 0:  # Y = A X with spmm_k columns instead
+                    X = torch.rand(A.m, args.spmm_k, dtype=xdt, device=dev)
+                    Y = torch.empty(A.n, args.spmm_k, dtype=xdt, device=dev)
+                    run = lambda: M.spmm(X, Y, ktile=args.ktile)  # noqa: E731
+                    fmt += f" spmm k={args.spmm_k} ktile={args.ktile}"
             ts = []
             for _ in range(args.reps):
                 spc5.copy(fa, fb)
@@ -670,8 +677,9 @@ def run_profile(args):
                 e1.synchronize()
                 ts.append(e0.elapsed_time(e1))
             best = min(ts)
+            kk = args.spmm_k if args.spmm_k > 0 and shape != "csr" else 1
             print(json.dumps({"profile": name, "format": fmt, "dtype": args.dtype, "n": A.n, "nnz": A.nnz,
-                              "ms": [round(t, 4) for t in ts], "gflops_best": round(2.0 * A.nnz / best / 1e6, 1)}),
+                              "ms": [round(t, 4) for t in ts], "gflops_best": round(2.0 * A.nnz * kk / best / 1e6, 1)}),
                   flush=True)
             if shape != "csr":
                 M.destroy()
